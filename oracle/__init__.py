@@ -76,11 +76,10 @@ def lib():
             L.or_alpha.restype = C.c_int; L.or_alpha.argtypes = [i64, i64, C.c_int]
             L.or_chirp.restype = C.c_int; L.or_chirp.argtypes = [i64, P]
             L.or_cmul.restype = None; L.or_cmul.argtypes = [P, P, P, i64]
-            L.or_dw_add.restype = None; L.or_dw_add.argtypes = [P, P, P]
             L.or_split.restype = C.c_int
             L.or_split.argtypes = [P, i64, C.c_int, C.c_int, C.c_int, P, P, P, P]
             L.or_garner.restype = None; L.or_garner.argtypes = [P, i64, C.c_int, P]
-            L.or_term_pair.restype = None; L.or_term_pair.argtypes = [P, i32, P]
+            L.or_exact_sum.restype = None; L.or_exact_sum.argtypes = [P, P, P, i64, P]
             L.or_schedule.restype = C.c_int
             L.or_schedule.argtypes = [C.c_int, P, C.c_int, P, C.c_int, C.c_int, C.c_int, P, P, P]
             L.or_ozfft.restype = C.c_int
@@ -153,14 +152,6 @@ def cmul(x, y):
     return z
 
 
-def dw_add(x, y):
-    x = np.ascontiguousarray(x, dtype=np.float64)
-    y = np.ascontiguousarray(y, dtype=np.float64)
-    z = np.empty(2)
-    lib().or_dw_add(_p(x), _p(y), _p(z))
-    return z
-
-
 def split(v, alpha_, K, kdim=None, want_slices=True):
     """Alg. 3: returns (slices [k][N] float64, q [k][N] int64, sexp [k], status)."""
     v = np.ascontiguousarray(v, dtype=np.float64)
@@ -192,11 +183,14 @@ def int128_to_pairs(vals):
     return out
 
 
-def term_pair(z: int, S: int):
-    z2 = int128_to_pairs([z])
-    out = np.empty(2)
-    lib().or_term_pair(_p(z2), S, _p(out))
-    return out[0], out[1]
+def exact_sum(zs, Ss, signs=None):
+    """round(sum sign_i z_i 2^-S_i) to binary64 (reading R7 of the oracle)."""
+    z2 = int128_to_pairs(list(zs))
+    S = np.ascontiguousarray(Ss, dtype=np.int32)
+    sg = np.ascontiguousarray(signs if signs is not None else np.ones(len(S)), dtype=np.int32)
+    out = np.empty(1)
+    lib().or_exact_sum(_p(z2), _p(S), _p(sg), len(S), _p(out))
+    return float(out[0])
 
 
 def schedule(sx, sy, L):

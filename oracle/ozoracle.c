@@ -16,8 +16,8 @@
  *     alpha of §4.4 (two or three primes, accumulation bound L);
  *   - the flush schedule of Alg. 8 (§4.4), the four real convolutions of §4.5,
  *     Garner's algorithm with the symmetric remainder of Eq. (1) (§3.1, §3.3);
- *   - the accumulation of the rescaled CRT integers in double-word arithmetic
- *     (the binary64 counterpart of the TSAdd of Alg. 8);
+ *   - the exact sum of the rescaled CRT integers, rounded once to binary64
+ *     (the quantity the TSAdd accumulation of Alg. 8 approximates);
  *   - the Bluestein wrapper of Alg. 1 (§3.2) with ZeroPad / ZeroPad+-;
  *   - a binary128 DFT (naive O(n^2), and radix-2 O(n log n) for large n) as
  *     the accuracy reference (the paper uses a 106-bit MPFR FFT, §5.1).
@@ -28,17 +28,19 @@
  *       not this oracle's subject.
  *   R2  chirp table: w(j) = exp(-i*pi*r/n), r = j^2 mod 2n, correctly rounded to
  *       binary64 (§4.2 assumes correctly rounded tables); evaluated in binary128
- *       after an exact octant reduction of r/n.
+ *       after an exact octant reduction of r/n; components equal to zero are +0.
  *   R3  complex products: re = fma(a,c, -(b*d)), im = fma(a,d, b*c), with b*d
  *       and b*c rounded to binary64.
  *   R4  ceil(log2(mu)) is exact: mu = m*2^E, m in [1/2,1) gives E-1 when
  *       m == 1/2 and E otherwise.
  *   R5  alpha uses n (at most n non-zero products feed any output), not N.
  *   R6  NTT roots: w_N = g^((p-1)/N) with g the smallest primitive root of p.
- *   R7  accumulation: each flush term z'/c is split exactly into a binary64 pair
- *       and added with AccurateDWPlusDW (Joldes, Muller, Popescu, ACM TOMS 2017,
- *       Alg. 6) in Alg. 8's flush order; real part = RR groups then II groups
- *       (negated), imaginary part = IR groups then RI groups (§4.5).
+ *   R7  accumulation: the rescaled CRT integers z'/c of all flush groups of
+ *       RR and -II (real part), IR and RI (imaginary part) (§4.5) are summed
+ *       exactly and the exact sum is rounded once to nearest binary64 (ties to
+ *       even).  This is the plain definition of the sum that Alg. 8's TSAdd
+ *       accumulation approximates; the oracle computes it with a two's-complement
+ *       big integer in units of 2^-max(S).
  *   R8  inverse direction: conj -> forward -> conj -> round(v / n) (Eq. (4)).
  *   R9  third prime (used only when three primes are requested): 15*2^27 + 1.
  */
@@ -242,8 +244,9 @@ int or_chirp(int64_t n, double* w)
         uint64_t r = (uint64_t)((u128)j * (u128)j % (u128)(2 * n));
         qreal s, c;
         sincospi_q(r, (uint64_t)n, &s, &c);
-        w[2 * j] = (double)c;
-        w[2 * j + 1] = (double)(-s);
+        double cd = (double)c, sd = (double)s;
+        w[2 * j] = cd == 0.0 ? 0.0 : cd;       /* zero components are +0 (R2) */
+        w[2 * j + 1] = sd == 0.0 ? 0.0 : -sd;
     }
     return OR_OK;
 }
@@ -273,38 +276,6 @@ static int ceil_log2(double mu)
     int E;
     double m = frexp(mu, &E);
     return m == 0.5 ? E - 1 : E;
-}
-
-/* TwoSum (Knuth) and FastTwoSum (Alg. 7, Dekker) */
-static void two_sum(double a, double b, double* s, double* e)
-{
-    double t = a + b;
-    double bb = t - a;
-    *e = (a - (t - bb)) + (b - bb);
-    *s = t;
-}
-static void fast_two_sum(double a, double b, double* s, double* e)
-{
-    double t = a + b;
-    *e = b - (t - a);
-    *s = t;
-}
-
-/* AccurateDWPlusDW (Joldes, Muller, Popescu 2017, Alg. 6): (zh,zl) ~ x + y */
-static void dw_add(double xh, double xl, double yh, double yl, double* zh, double* zl)
-{
-    double sh, sl, th, tl, vh, vl;
-    two_sum(xh, yh, &sh, &sl);
-    two_sum(xl, yl, &th, &tl);
-    double c = sl + th;
-    fast_two_sum(sh, c, &vh, &vl);
-    double w = tl + vl;
-    fast_two_sum(vh, w, zh, zl);
-}
-
-void or_dw_add(const double* x, const double* y, double* z)
-{
-    dw_add(x[0], x[1], y[0], y[1], &z[0], &z[1]);
 }
 
 /* ------------------------------------------------------------------------- */
@@ -396,26 +367,91 @@ void or_garner(const uint32_t* res, int64_t cnt, int nprimes, int64_t* out)
     }
 }
 
-/* exact binary64 pair (hi, lo) with hi + lo = z * 2^-S (reading R7):
-   z = zt * 2^40 + zb with 0 <= zb < 2^40 (|zt| < 2^53), TwoSum, then scale. */
-static void term_pair(i128 z, int S, double* hi, double* lo)
+/* ------------------------------------------------------------------------- */
+/* Exact accumulation (reading R7): a two's-complement big integer of nl      */
+/* 32-bit digits, little-endian.                                              */
+/* ------------------------------------------------------------------------- */
+
+/* acc += z * 2^sh  (z an i128, sh >= 0); digits beyond nl are dropped, so the */
+/* caller sizes nl to hold every partial sum. */
+static void big_add_shifted(uint32_t* acc, int nl, i128 z, int sh)
 {
-    i128 two40 = (i128)1 << 40;
-    i128 zt = z / two40;
-    i128 zb = z - zt * two40;
-    if (zb < 0) { zb += two40; zt -= 1; } /* floor division */
-    double a = ldexp((double)(int64_t)zt, 40);
-    double b = (double)(int64_t)zb;
-    double h, l;
-    two_sum(a, b, &h, &l);
-    *hi = ldexp(h, -S);
-    *lo = ldexp(l, -S);
+    /* z as 4 sign-extended 32-bit digits (|z| < 2^127) */
+    uint32_t d[4];
+    u128 uz = (u128)z;
+    for (int i = 0; i < 4; ++i) d[i] = (uint32_t)(uz >> (32 * i));
+    uint32_t ext = z < 0 ? 0xffffffffu : 0u;
+    int q = sh / 32, b = sh % 32;
+    uint64_t carry = 0;
+    for (int i = q; i < nl; ++i) {
+        /* digit i-q of (z << b), built from z's digits k = i-q and k-1 */
+        int k = i - q;
+        uint32_t hi = k < 4 ? d[k] : ext;
+        uint32_t lo = k == 0 ? 0u : (k - 1 < 4 ? d[k - 1] : ext);
+        uint32_t v = b == 0 ? hi : (uint32_t)((hi << b) | (lo >> (32 - b)));
+        uint64_t s = (uint64_t)acc[i] + v + carry;
+        acc[i] = (uint32_t)s;
+        carry = s >> 32;
+    }
 }
 
-void or_term_pair(const int64_t* z2, int32_t S, double* out)
+/* round the big integer acc * 2^unit to the nearest binary64 (ties to even) */
+static double big_to_double(const uint32_t* acc_in, int nl, int unit)
 {
-    i128 z = (i128)(((u128)(uint64_t)z2[1] << 64) | (u128)(uint64_t)z2[0]);
-    term_pair(z, S, &out[0], &out[1]);
+    uint32_t* m = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)nl);
+    memcpy(m, acc_in, sizeof(uint32_t) * (size_t)nl);
+    int neg = (m[nl - 1] >> 31) != 0;
+    if (neg) { /* magnitude = two's complement negation */
+        uint64_t c = 1;
+        for (int i = 0; i < nl; ++i) {
+            uint64_t s = (uint64_t)(uint32_t)~m[i] + c;
+            m[i] = (uint32_t)s;
+            c = s >> 32;
+        }
+    }
+    int top = -1; /* index of the leading one bit */
+    for (int i = nl - 1; i >= 0 && top < 0; --i)
+        if (m[i])
+            for (int bit = 31; bit >= 0; --bit)
+                if (m[i] >> bit & 1) { top = 32 * i + bit; break; }
+    double r = 0.0;
+    if (top >= 0) {
+        int lead = unit + top;                    /* exponent of the leading bit */
+        int eulp = lead - 52 > -1074 ? lead - 52 : -1074;
+        int drop = eulp - unit;                   /* low bits below the result's ulp */
+        uint64_t qv = 0;
+        if (drop <= 0) {
+            for (int bit = top; bit >= 0; --bit) qv = qv << 1 | (m[bit / 32] >> (bit % 32) & 1);
+            r = ldexp((double)qv, unit);
+        } else {
+            for (int bit = top; bit >= drop; --bit) qv = qv << 1 | (m[bit / 32] >> (bit % 32) & 1);
+            int rbit = m[(drop - 1) / 32] >> ((drop - 1) % 32) & 1;
+            int sticky = 0;
+            for (int bit = drop - 2; bit >= 0 && !sticky; --bit) sticky = m[bit / 32] >> (bit % 32) & 1;
+            if (rbit && (sticky || (qv & 1))) qv += 1;
+            r = ldexp((double)qv, eulp);
+        }
+    }
+    free(m);
+    return neg ? -r : r;
+}
+
+void or_exact_sum(const int64_t* z2, const int32_t* S, const int32_t* sign, int64_t cnt, double* out)
+{
+    /* exposed for the tests: round(sum sign_i z_i 2^-S_i) */
+    int smin = 0, smax = 0;
+    for (int64_t i = 0; i < cnt; ++i) {
+        if (i == 0 || S[i] < smin) smin = S[i];
+        if (i == 0 || S[i] > smax) smax = S[i];
+    }
+    int nl = (smax - smin + 128 + 16) / 32 + 2;
+    uint32_t* acc = (uint32_t*)calloc((size_t)nl, sizeof(uint32_t));
+    for (int64_t i = 0; i < cnt; ++i) {
+        i128 z = (i128)(((u128)(uint64_t)z2[2 * i + 1] << 64) | (u128)(uint64_t)z2[2 * i]);
+        big_add_shifted(acc, nl, sign[i] < 0 ? -z : z, smax - S[i]);
+    }
+    *out = big_to_double(acc, nl, -smax);
+    free(acc);
 }
 
 /* ------------------------------------------------------------------------- */
@@ -507,7 +543,9 @@ int or_ozfft(int64_t n, int64_t N, int K, int L, int nprimes, int direction,
     uint32_t* res = (uint32_t*)malloc(sizeof(uint32_t) * szN);
     uint32_t* Z = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)nprimes * szN);
     uint32_t* zr = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)nprimes * szN);
-    double* acc = (double*)calloc(4 * (size_t)n, sizeof(double)); /* [part][n][hi,lo] */
+    double* acc = (double*)calloc(2 * (size_t)n, sizeof(double)); /* y' [part][n] */
+    uint32_t* bigacc = NULL;
+    int nl = 0;
     int32_t* gS = NULL;
     int32_t* gsz = NULL;
     int32_t* gp = NULL;
@@ -545,9 +583,9 @@ int or_ozfft(int64_t n, int64_t N, int K, int L, int nprimes, int direction,
     for (int v = 0; v < 4; ++v) kq = kcount[v] > kq ? kcount[v] : kq;
     q = (int64_t*)malloc(sizeof(int64_t) * 4 * (size_t)kq * szN);
     spec = (uint32_t*)malloc(sizeof(uint32_t) * 4 * (size_t)kq * (size_t)nprimes * szN);
-    gS = (int32_t*)malloc(sizeof(int32_t) * (size_t)kq * (size_t)kq);
-    gsz = (int32_t*)malloc(sizeof(int32_t) * (size_t)kq * (size_t)kq);
-    gp = (int32_t*)malloc(sizeof(int32_t) * (size_t)kq * (size_t)kq * (size_t)kq * 2);
+    gS = (int32_t*)malloc(sizeof(int32_t) * 4 * (size_t)kq * (size_t)kq);
+    gsz = (int32_t*)malloc(sizeof(int32_t) * 4 * (size_t)kq * (size_t)kq);
+    gp = (int32_t*)malloc(sizeof(int32_t) * 4 * (size_t)kq * (size_t)kq * (size_t)kq * 2);
     if (!q || !spec || !gS || !gsz || !gp) { status = OR_ERR_ALLOC; goto done; }
     for (int v = 0; v < 4 && status == OR_OK; ++v) {
         int32_t kv;
@@ -570,21 +608,42 @@ int or_ozfft(int64_t n, int64_t N, int K, int L, int nprimes, int direction,
                 if (v < 2) ++nfr; else ++nfp;
             }
 
-    /* Alg. 8 for each of the four real convolutions */
+    /* Alg. 8 flush schedules of the four real convolutions */
+    int ngs[4];
+    const size_t gstride = (size_t)kq * (size_t)kq;
+    int smin = 0, smax = 0, any = 0;
     for (int c = 0; c < 4; ++c) {
         int vx = CONV_X[c], vw = CONV_W[c];
-        int ng = or_schedule(kcount[vx], sexp[vx], kcount[vw], sexp[vw], L, kq * kq, kq,
-                             gS, gsz, gp);
-        if (ng < 0) { status = OR_ERR_ARG; goto done; }
-        if (tr) tr->ngroups[c] = ng;
+        ngs[c] = or_schedule(kcount[vx], sexp[vx], kcount[vw], sexp[vw], L, kq * kq, kq, &gS[c * gstride],
+                             &gsz[c * gstride], &gp[c * gstride * kq * 2]);
+        if (ngs[c] < 0) { status = OR_ERR_ARG; goto done; }
+        if (tr) tr->ngroups[c] = ngs[c];
+        for (int g = 0; g < ngs[c]; ++g) {
+            int S = gS[c * gstride + g];
+            if (!any || S < smin) smin = S;
+            if (!any || S > smax) smax = S;
+            any = 1;
+        }
+    }
+    /* exact accumulators (R7): per part and output, nl digits in units of 2^-smax */
+    nl = (smax - smin + 128 + 16) / 32 + 2;
+    bigacc = (uint32_t*)calloc(2 * (size_t)n * (size_t)nl, sizeof(uint32_t));
+    if (!bigacc) { status = OR_ERR_ALLOC; goto done; }
+
+    for (int c = 0; c < 4; ++c) {
+        int vx = CONV_X[c], vw = CONV_W[c];
+        int ng = ngs[c];
+        const int32_t* cS = &gS[c * gstride];
+        const int32_t* csz = &gsz[c * gstride];
+        const int32_t* cp = &gp[c * gstride * kq * 2];
         for (int g = 0; g < ng; ++g) {
             /* NTT-domain accumulation: Z_i = sum X_s (.) Y_t mod p_i */
             for (int i = 0; i < nprimes; ++i) {
                 uint64_t p = OR_PRIMES[i];
                 uint32_t* Zi = &Z[(size_t)i * szN];
                 memset(Zi, 0, sizeof(uint32_t) * szN);
-                for (int m = 0; m < gsz[g]; ++m) {
-                    int s = gp[((size_t)g * kq + m) * 2], t = gp[((size_t)g * kq + m) * 2 + 1];
+                for (int m = 0; m < csz[g]; ++m) {
+                    int s = cp[((size_t)g * kq + m) * 2], t = cp[((size_t)g * kq + m) * 2 + 1];
                     const uint32_t* X = &spec[(((size_t)vx * kq + s) * nprimes + i) * szN];
                     const uint32_t* Y = &spec[(((size_t)vw * kq + t) * nprimes + i) * szN];
                     for (int64_t j = 0; j < N; ++j) Zi[j] = (uint32_t)((Zi[j] + mulmod(X[j], Y[j], p)) % p);
@@ -592,7 +651,7 @@ int or_ozfft(int64_t n, int64_t N, int K, int L, int nprimes, int direction,
                 or_ntt(Zi, &zr[(size_t)i * szN], N, p, 1);
                 ++ninv;
             }
-            /* Garner, rescale by 1/c, accumulate (R7) */
+            /* Garner, then z' / c added exactly (R7) */
             uint32_t z3[3];
             int part = CONV_OUT[c];
             for (int64_t j = 0; j < N; ++j) {
@@ -603,22 +662,18 @@ int or_ozfft(int64_t n, int64_t N, int K, int L, int nprimes, int direction,
                     o[0] = (int64_t)(uint64_t)(u128)zc;
                     o[1] = (int64_t)(zc >> 64);
                 }
-                if (j < n) {
-                    double th, tl;
-                    term_pair(zc, gS[g], &th, &tl);
-                    if (CONV_NEG[c]) { th = -th; tl = -tl; }
-                    double* a = &acc[((size_t)part * n + j) * 2];
-                    dw_add(a[0], a[1], th, tl, &a[0], &a[1]);
-                }
+                if (j < n)
+                    big_add_shifted(&bigacc[((size_t)part * n + j) * nl], nl, CONV_NEG[c] ? -zc : zc,
+                                    smax - cS[g]);
             }
             if (tr && g < tr->gdim) {
-                if (tr->gS) tr->gS[c * tr->gdim + g] = gS[g];
-                if (tr->gsize) tr->gsize[c * tr->gdim + g] = gsz[g];
+                if (tr->gS) tr->gS[c * tr->gdim + g] = cS[g];
+                if (tr->gsize) tr->gsize[c * tr->gdim + g] = csz[g];
                 if (tr->gpairs)
-                    for (int m = 0; m < gsz[g] && m < tr->kdim; ++m) {
-                        tr->gpairs[(((size_t)c * tr->gdim + g) * tr->kdim + m) * 2] = gp[((size_t)g * kq + m) * 2];
+                    for (int m = 0; m < csz[g] && m < tr->kdim; ++m) {
+                        tr->gpairs[(((size_t)c * tr->gdim + g) * tr->kdim + m) * 2] = cp[((size_t)g * kq + m) * 2];
                         tr->gpairs[(((size_t)c * tr->gdim + g) * tr->kdim + m) * 2 + 1] =
-                            gp[((size_t)g * kq + m) * 2 + 1];
+                            cp[((size_t)g * kq + m) * 2 + 1];
                     }
                 if (tr->zres)
                     memcpy(&tr->zres[((size_t)c * tr->gdim + g) * nprimes * szN], zr,
@@ -626,11 +681,14 @@ int or_ozfft(int64_t n, int64_t N, int K, int L, int nprimes, int direction,
             }
         }
     }
+    for (int part = 0; part < 2; ++part)
+        for (int64_t j = 0; j < n; ++j)
+            acc[(size_t)part * n + j] = any ? big_to_double(&bigacc[((size_t)part * n + j) * nl], nl, -smax) : 0.0;
 
     /* y' = rounded accumulators; Alg. 1 last step y = y' (.) w; inverse (R8) */
     for (int64_t j = 0; j < n; ++j) {
-        double yr = acc[(0 * (size_t)n + j) * 2];
-        double yi = acc[(1 * (size_t)n + j) * 2];
+        double yr = acc[j];
+        double yi = acc[(size_t)n + j];
         if (tr && tr->yprime) { tr->yprime[2 * j] = yr; tr->yprime[2 * j + 1] = yi; }
         double re, im;
         cmul(yr, yi, w[2 * j], w[2 * j + 1], &re, &im);
@@ -670,7 +728,7 @@ done:
         }
     }
     free(w); free(vec); free(q); free(spec); free(res); free(Z); free(zr); free(acc);
-    free(gS); free(gsz); free(gp);
+    free(gS); free(gsz); free(gp); free(bigacc);
     return status;
 }
 

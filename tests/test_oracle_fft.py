@@ -179,16 +179,16 @@ def test_transform_count_trends():
     assert counts[4.0] > counts[0.0]
 
 
-def test_accumulation_matches_exact_sum():
-    """Reading R7: the double-word accumulation rounds to the exact sum of the
-    rescaled CRT integers within 1 ulp (exact sum by rational arithmetic)."""
+def test_accumulation_is_the_rounded_exact_sum():
+    """Reading R7: y' is the exact sum of the rescaled CRT integers of every
+    flush group (RR - II, IR + RI), rounded once to nearest; recomputed here with
+    rational arithmetic from the oracle's CRT integers and group scales."""
     n = 128
     x = synth.complex_signal("phi", n, 8, phi=1.0)[0]
     y, info = oracle.ozfft(x, K=3, L=1, trace={"zcrt", "groups", "yprime"})
     z = info["zcrt"]
     gS = info["gS"]
-    exact_re = [Fraction(0)] * n
-    exact_im = [Fraction(0)] * n
+    exact = [[Fraction(0)] * n, [Fraction(0)] * n]
     sign = [1, -1, 1, 1]
     part = [0, 0, 1, 1]
     for c in range(4):
@@ -196,19 +196,10 @@ def test_accumulation_matches_exact_sum():
             scale = Fraction(1, 2 ** int(gS[c, g])) if gS[c, g] >= 0 else Fraction(2 ** int(-gS[c, g]))
             for j in range(n):
                 v = int(np.uint64(z[c, g, j, 0])) + (int(z[c, g, j, 1]) << 64)
-                t = sign[c] * v * scale
-                if part[c] == 0:
-                    exact_re[j] += t
-                else:
-                    exact_im[j] += t
+                exact[part[c]][j] += sign[c] * v * scale
     yp = info["yprime"]
-    equal = 0
     for j in range(n):
-        for got, ex in ((yp[j].real, exact_re[j]), (yp[j].imag, exact_im[j])):
-            rn = float(ex)  # Fraction -> float rounds to nearest
-            assert abs(got - rn) <= np.spacing(abs(rn))
-            equal += got == rn
-    assert equal >= 2 * n - 2
+        assert yp[j].real == float(exact[0][j]) and yp[j].imag == float(exact[1][j])
 
 
 def test_method_argument_errors():

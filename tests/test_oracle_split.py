@@ -153,30 +153,29 @@ def test_schedule_structure_brute_force():
             assert len(p0) == L or S0 != S1
 
 
-def test_dw_add_error_bound():
-    rng = np.random.default_rng(4)
-    u = 2.0 ** -53
-    for _ in range(2000):
-        xh = rng.standard_normal() * 2.0 ** rng.integers(-30, 30)
-        yh = -xh * (1 + rng.standard_normal() * 2.0 ** -rng.integers(1, 50))
-        xl = xh * u * rng.uniform(-1, 1)
-        yl = yh * u * rng.uniform(-1, 1)
-        xh2, xl2 = xh + xl, (xh - (xh + xl)) + xl   # normalize the pairs
-        yh2, yl2 = yh + yl, (yh - (yh + yl)) + yl
-        z = oracle.dw_add([xh2, xl2], [yh2, yl2])
-        exact = Fraction(xh2) + Fraction(xl2) + Fraction(yh2) + Fraction(yl2)
-        got = Fraction(z[0]) + Fraction(z[1])
-        if exact != 0:
-            assert abs(got - exact) <= 4 * Fraction(u) ** 2 * abs(exact)
-        assert z[0] == float(Fraction(z[0]) + Fraction(z[1]))  # normalized: hi = RN(hi + lo)
-
-
-def test_term_pair_exact():
-    rng = random.Random(5)
+def test_exact_sum_rounds_the_exact_rational():
+    """Reading R7: round-to-nearest-even of the exact sum, checked with Fractions
+    (Fraction -> float is correctly rounded), including ties, cancellation,
+    huge scale spreads and subnormal results."""
+    rng = random.Random(6)
     P3 = oracle.prime(0) * oracle.prime(1) * oracle.prime(2)
-    for _ in range(2000):
-        z = rng.randrange(-(P3 // 2), P3 // 2)
-        S = rng.randint(-100, 300)
-        h, l = oracle.term_pair(z, S)
-        assert Fraction(h) + Fraction(l) == Fraction(z) / Fraction(2) ** S
-        assert h == float(Fraction(h) + Fraction(l))
+    cases = []
+    for _ in range(400):
+        k = rng.randint(1, 12)
+        zs = [rng.randrange(-(P3 // 2), P3 // 2) for _ in range(k)]
+        base = rng.randint(-200, 1100)
+        Ss = [base + rng.choice([0, 21, 42, 63, 84, rng.randint(-60, 600)]) for _ in range(k)]
+        cases.append((zs, Ss, [rng.choice([1, -1]) for _ in range(k)]))
+    # exact ties: 2^53 + 1 (a midpoint) rounds to even, and a tiny term breaks the tie
+    cases.append(([2 ** 53 + 1], [0], [1]))
+    cases.append(([2 ** 53 + 1, 1], [0, 700], [1, 1]))
+    cases.append(([2 ** 53 + 3], [0], [1]))
+    cases.append(([5, 5], [0, 0], [1, -1]))          # exact cancellation -> +0
+    cases.append(([3], [1076], [1]))                   # subnormal with rounding
+    cases.append(([1 << 60, -(1 << 60) + 1], [10, 10], [1, 1]))
+    for zs, Ss, sg in cases:
+        exact = sum(Fraction(s * z) / Fraction(2) ** S for z, S, s in zip(zs, Ss, sg))
+        got = oracle.exact_sum(zs, Ss, sg)
+        assert got == float(exact), (zs, Ss, sg)
+        if exact == 0:
+            assert np.copysign(1.0, got) == 1.0
