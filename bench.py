@@ -1,0 +1,325 @@
+#!/usr/bin/env python3
+"""Throughput of the FP64-accurate Ozaki-scheme NTT FFT on GB300.
+
+Workload (one step): 64 complex128 signals of length n = 2^18, real and
+imaginary parts i.i.d. U[-1, 1) (seeded), forward transforms with K = 3 split
+levels, two primes and no NTT-domain accumulation (L = 1: up to 96 32-bit NTTs
+per transform, 84 at run time).  `value` is FFTs per second over all ranks,
+one ozfft_execute per step on the whole batch, inputs resident in HBM (the 256
+MiB of inputs per step exceed the 129 MB L2, so no flush is needed).  The plain
+per-transform pipeline (64 executions of a batch-1 plan per step) is reported
+beside it, and `e2e` repeats the batched measurement through
+ozfft_execute_host with pinned host buffers.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With --gpus N > 1 run under torchrun: every rank transforms its own batch on its
+own GPU (independent replicas, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FP64-accurate Ozaki-NTT FFTs/s at n=2^18 (batched); NTT GB/s; rel err"
+UNIT = "FFT/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--n", type=int, default=1 << 18)
+    ap.add_argument("--batch", type=int, default=64)
+    ap.add_argument("--K", type=int, default=3)
+    ap.add_argument("--L", type=int, default=1)
+    ap.add_argument("--nprimes", type=int, default=2)
+    ap.add_argument("--seed", type=int, default=2)
+    ap.add_argument("--skip-plain", action="store_true")
+    ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--cpu-signals", type=int, default=2, help="oracle transforms timed for cpu_baseline")
+    return ap.parse_args()
+
+
+def workload(a):
+    return {"workload": f"complex128 n=2^{a.n.bit_length() - 1} x {a.batch} signals, uniform[-1,1) parts, "
+                        f"forward, K={a.K}, L={a.L}, {a.nprimes} primes",
+            "n": a.n, "batch_per_gpu": a.batch, "K": a.K, "L": a.L, "nprimes": a.nprimes, "seed": a.seed,
+            "l2": "inputs (batch x n x 16 B) exceed L2 each step; no flush"}
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    def __init__(self, gpu_index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                       "-i", str(gpu_index), "-lms", "100"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        self.p.wait()
+        self.f.seek(0)
+        rows = [r.split(", ") for r in self.f.read().strip().splitlines() if r.count(",") >= 8]
+        os.unlink(self.f.name)
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].strip() == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        return None
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("k_ntt.cu", "oz_common.cuh", "oz_kernels.h"):
+        h.update(open(os.path.join(ROOT, "paper_2603_29129_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+# ----------------------------------------------------------------- reference arm
+def run_reference(a, rank, world):
+    """The oracle, as it stands, timed on the host cores: one signal per step."""
+    if rank != 0:
+        return
+    import oracle
+    from paper_2603_29129_gb300 import synth
+    oracle.build()
+    x = synth.complex_signal("uniform", a.n, a.seed, batch=1)[0]
+    for _ in range(a.warmup):
+        oracle.ozfft(x, K=a.K, L=a.L, nprimes=a.nprimes)
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        oracle.ozfft(x, K=a.K, L=a.L, nprimes=a.nprimes)
+    dt = time.perf_counter() - t0
+    v = a.steps / dt
+    cfg = workload(a)
+    cfg["reference_sample"] = "1 signal per step"
+    print(json.dumps({"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+                      "warmup": a.warmup, "ms_per_step": 1e3 * dt / a.steps, "higher_is_better": True,
+                      "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                      "config": cfg, "impl": "reference",
+                      "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                       "sample": f"1 transform of n={a.n} per step, single-threaded C"},
+                      "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}),
+          flush=True)
+
+
+# ----------------------------------------------------------------- our arm
+def main():
+    a = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if a.impl == "reference":
+        run_reference(a, rank, world)
+        return
+
+    import numpy as np
+    import torch
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_2603_29129_gb300 import build as bld
+    if rank == 0:
+        bld.build()
+    if dist:
+        dist.barrier()
+    from paper_2603_29129_gb300 import ozfft, synth
+
+    def barrier():
+        if dist:
+            dist.barrier()
+
+    def max_over_ranks(v):
+        if not dist:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    B, n = a.batch, a.n
+    x_host = synth.complex_signal("uniform", n, a.seed + 1000 * rank, batch=B)
+    x_pin = torch.from_numpy(x_host).pin_memory()
+    x = x_pin.to(dev)
+    y = torch.empty_like(x)
+    stream = torch.cuda.current_stream(dev)
+    plan = ozfft.Plan(n, B, ozfft.FORWARD, K=a.K, L=a.L, nprimes=a.nprimes)
+
+    # ---- batched, device-resident (the headline value), with per-kernel events
+    for _ in range(a.warmup):
+        plan.execute(x, y)
+    torch.cuda.synchronize(dev)
+    plan.profile()                      # drop anything recorded so far
+    plan.set_profiling(True)
+    clocks = ClockSampler(local)
+    time.sleep(0.25)
+    barrier()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(a.steps):
+        plan.execute(x, y)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    clk = clocks.stop()
+    plan.set_profiling(False)
+    prof = plan.profile()
+    ms = max_over_ranks(e0.elapsed_time(e1))
+    value = a.steps * B * world / (ms / 1e3)
+    stats = plan.stats()
+    if plan.status() != ozfft.OK:
+        raise RuntimeError("device status flagged the benchmark input")
+
+    # ---- plain pipeline: one execution of a batch-1 plan per transform
+    plain = None
+    if not a.skip_plain:
+        p1 = ozfft.Plan(n, 1, ozfft.FORWARD, K=a.K, L=a.L, nprimes=a.nprimes)
+        xs = [x[i:i + 1] for i in range(B)]
+        ys = [y[i:i + 1] for i in range(B)]
+        for _ in range(a.warmup):
+            for i in range(B):
+                p1.execute(xs[i], ys[i])
+        psteps = max(1, a.steps // 3)
+        barrier()
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for _ in range(psteps):
+            for i in range(B):
+                p1.execute(xs[i], ys[i])
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+        pms = max_over_ranks(e0.elapsed_time(e1))
+        plain = {"value": psteps * B * world / (pms / 1e3), "unit": UNIT, "steps": psteps,
+                 "ms_per_step": pms / psteps, "executions_per_step": B}
+        del p1
+
+    # ---- end to end through the C ABI with host buffers
+    e2e = None
+    out_pin = torch.empty_like(x_pin).pin_memory()
+    if not a.skip_e2e:
+        for _ in range(a.warmup):
+            plan.execute_host(x_pin, out_pin)
+        esteps = max(1, a.steps // 3)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(esteps):
+            plan.execute_host(x_pin, out_pin)
+        dt = max_over_ranks(time.perf_counter() - t0)
+        e2e = {"value": esteps * B * world / dt, "unit": UNIT, "h2d_bytes_per_step": B * n * 16,
+               "d2h_bytes_per_step": B * n * 16, "steps": esteps}
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    # ---- roofline of the dominant kernel (live CUDA events over the timed region)
+    N = plan.N
+    runtime_fwd = stats["ntt_forward_runtime"]        # live forward vectors per execution
+    inv_vecs = stats["ntt_inverse"]                   # live inverse vectors per execution
+    # algorithmic bytes per launch: every pass reads and writes each live vector once (4N + 4N);
+    # the fused multiply-accumulate reads X_s and Ym_t (4N each) per product instead of Z
+    prods = sum(len(pairs) for b in range(B) for conv in plan.dump(ozfft.DUMP_SCHED, b)
+                for _, pairs in conv) * a.nprimes
+    alg = {"ntt_fwd_col": 8 * N * runtime_fwd, "ntt_fwd_row": 8 * N * runtime_fwd,
+           "ntt_inv_col": 8 * N * inv_vecs, "ntt_inv_row": 8 * N * prods + 4 * N * inv_vecs,
+           "premul": B * (16 * n + 16 * n + 16 * N), "crt": 4 * n * inv_vecs + B * 32 * n}
+    slots = prof["slots"]
+    dom = max(slots, key=lambda k: slots[k]["ms"])
+    execs = max(1, prof["executions"])
+    dom_ms = slots[dom]["ms"] / max(1, slots[dom]["launches"])
+    pk = peaks()
+    roof = None
+    if alg.get(dom):
+        achieved = alg[dom] / (dom_ms / 1e3) / 1e9
+        peak = pk["hbm_gbs"] if pk else 6800.0
+        traffic = None
+        tfile = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+        if os.path.exists(tfile):
+            t = json.load(open(tfile))
+            ent = t.get(dom)
+            if ent and ent.get("source_hash") == kernel_source_hash() and ent.get("config") == f"n={n},B={B},L={a.L}":
+                traffic = ent.get("bytes_per_launch")
+        roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if pk else "fallback 6.8 TB/s",
+                "algorithmic_bytes_per_launch": alg[dom], "launch_ms": dom_ms}
+    total_ntt = runtime_fwd + inv_vecs
+    ntt_ms = sum(slots[k]["ms"] for k in slots if k.startswith("ntt")) / execs
+    breakdown = {k: round(v["ms"] / execs, 4) for k, v in slots.items()}
+
+    # ---- accuracy of one signal and bit parity with the oracle, CPU baseline
+    acc = {}
+    cpu = None
+    if not a.skip_cpu:
+        import oracle
+        oracle.build()
+        y0 = y[0].cpu().numpy()
+        hi, lo = oracle.fft_q(x_host[0])
+        acc["rel_l2_err_signal0"] = oracle.rel_l2_error(y0, hi, lo)
+        t0 = time.perf_counter()
+        same = True
+        for i in range(a.cpu_signals):
+            yo, _ = oracle.ozfft(x_host[i], K=a.K, L=a.L, nprimes=a.nprimes)
+            same = same and np.array_equal(yo.view(np.uint64), y[i].cpu().numpy().view(np.uint64))
+        dt = time.perf_counter() - t0
+        acc["bit_exact_vs_oracle"] = f"{a.cpu_signals} signals: {'yes' if same else 'NO'}"
+        cpu = {"value": a.cpu_signals / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{a.cpu_signals} of the {B} signals (n={n}), single-threaded C oracle"}
+
+    cfg = workload(a)
+    cfg.update({"mode": "batched (one ozfft_execute per step)", "parallelism": f"replicas x{world}",
+                "N": N, "alpha": stats["alpha"]})
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic", "config": cfg,
+        "plain": plain, "e2e": e2e, "roofline": roof, "cpu_baseline": cpu, "clocks": clk,
+        "gpu_launches": int(stats["kernel_launches"] * a.steps),
+        "ntt": {"per_transform_runtime": total_ntt / B, "per_transform_total": (total_ntt + stats["ntt_forward_plan"] * B) / B,
+                "GBps_algorithmic": total_ntt * 8 * N / (ntt_ms / 1e3) / 1e9},
+        "kernel_ms_per_step": breakdown, "accuracy": acc,
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

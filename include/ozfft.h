@@ -1,0 +1,173 @@
+/*
+ * ozfft.h -- C ABI of libozfft, a GB300 (sm_103a) implementation of the
+ * double-precision FFT of "Computing FFTs at Target Precision Using
+ * Lower-Precision FFTs" (arXiv 2603.29129).
+ *
+ * What one transform computes (forward direction), step by step:
+ *   1. x'(j) = x(j) * w(j), w(j) = exp(-i pi j^2 / n)            Alg. 1, §3.2
+ *   2. x~' = ZeroPad(x', N), w~* = ZeroPad+-(conj(w), N)           §3.2
+ *   3. each of Re x~', Im x~', Re w~*, Im w~* is split into at most K integer
+ *      slices q^(k) with |q^(k)| <= 2^alpha and scale c^(k) = 2^(s_k)      Alg. 3
+ *      alpha = max{a : L n 2^(2a) < P/2}, P = product of the primes       §4.2, §4.4
+ *   4. residues of every slice modulo each prime, forward 32-bit NTTs    §3.3, Alg. 6
+ *   5. for each of the four real convolutions (RR, II, IR, RI, §4.5), the
+ *      slice products with equal scale are summed in the NTT domain, at most
+ *      L at a time (Alg. 8), and each sum is inverse-transformed           §4.4
+ *   6. Garner CRT of the per-prime results (symmetric digits, Eq. (1))     §3.3
+ *   7. rescale by 1/(c_x c_y), accumulate in double-word arithmetic, round  Alg. 8
+ *   8. y(k) = y'(k) * w(k)                                               Alg. 1
+ * The inverse direction is conj -> forward -> conj -> divide by n (Eq. (4)).
+ * Steps 1-8 all run in this library's CUDA kernels; w~*'s split and forward
+ * NTTs (steps 2-4 for w~*) run once, when the plan is made (§4.5).
+ *
+ * Conventions for every function below:
+ *   - complex data are interleaved binary64 pairs (re, im), i.e. the layout of
+ *     a C `double _Complex` array or a contiguous torch.complex128 tensor;
+ *     batched data are [batch][n], signal after signal;
+ *   - "device pointer" means memory of the plan's CUDA device (cudaMalloc,
+ *     torch CUDA tensors); "host pointer" means ordinary or pinned host memory;
+ *   - the caller owns every buffer it passes; the plan owns its own tables and
+ *     workspace and frees them in ozfft_destroy;
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *     stream).  Calls that take a stream are asynchronous with respect to the
+ *     host unless stated otherwise;
+ *   - argument errors are returned synchronously as OZFFT_ERR_* codes; errors
+ *     that depend on the data (non-finite input, exponent overflow) are
+ *     recorded on the device and read with ozfft_get_status.
+ */
+#ifndef OZFFT_H
+#define OZFFT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ozfft_plan_s* ozfft_plan_t;
+
+enum { OZFFT_FORWARD = -1, OZFFT_INVERSE = +1 };
+
+enum {
+    OZFFT_OK = 0,
+    OZFFT_ERR_ARG = 1,       /* bad argument (null pointer, n < 1, batch < 1, K/L/nprimes out of range) */
+    OZFFT_ERR_LENGTH = 2,    /* convolution length N is not a power of two, exceeds 2^24 (the 2-adic
+                                order of p0 - 1), is shorter than 2n-1 without being n, or alpha < 1 */
+    OZFFT_ERR_ALLOC = 3,     /* device or host allocation failed */
+    OZFFT_ERR_CUDA = 4,      /* a CUDA runtime call failed (ozfft_last_error has the text) */
+    OZFFT_ERR_NONFINITE = 5, /* device status: the input held a NaN or an infinity */
+    OZFFT_ERR_RANGE = 6,     /* device status: 2^(ceil(log2 max|v|) + 53 - alpha) overflows binary64 */
+    OZFFT_ERR_TIMEOUT = 7    /* reserved for bounded device-side waits */
+};
+
+/* Plan options.  A zero field selects the default. */
+typedef struct {
+    int32_t K;        /* split cap K of §4.4 (default 3; 1..8) */
+    int32_t L;        /* NTT-domain accumulation bound L of §4.4 (default 1 = none; 1..8) */
+    int32_t nprimes;  /* 2 (default: p0 = 2130706433, p1 = 2113929217, §5.1) or 3 (adds 2013265921) */
+    int64_t conv_len; /* cyclic length N (default: n if n is a power of two, else the least power of
+                         two >= 2n-1; §3.2) */
+    int32_t debug;    /* nonzero: keep the slice residues of each execution for ozfft_debug_dump
+                         (costs one extra copy per execution; for tests) */
+} ozfft_options;
+
+/* Create a plan for `batch` transforms of length n in `direction`, with default
+   options, on the current CUDA device.  Returns NULL on error (see
+   ozfft_last_error).  Synchronous: it computes the chirp table, the twiddle
+   tables and the split + forward NTTs of w~* on the device and allocates the
+   workspace for `batch` signals. */
+ozfft_plan_t ozfft_plan(int64_t n, int64_t batch, int direction);
+
+/* Same with explicit options (NULL = defaults). */
+ozfft_plan_t ozfft_plan_ex(int64_t n, int64_t batch, int direction, const ozfft_options* opt);
+
+/* Transform `batch` signals: in and out are device pointers to [batch][n]
+   complex128 (in == out is allowed).  Enqueued on `stream`; nothing waits for
+   the host.  A plan must not be executed on two streams at the same time. */
+int ozfft_execute(ozfft_plan_t plan, const void* in, void* out, void* stream);
+
+/* Same transform with HOST buffers: copies `in` to the device, transforms,
+   copies the result to `out`, and returns after the stream has synchronized.
+   Pinned (page-locked) host memory gives the fastest copies. */
+int ozfft_execute_host(ozfft_plan_t plan, const void* in, void* out, void* stream);
+
+/* Synchronize `stream`, return the data-dependent status recorded by the
+   executions since the previous call (OZFFT_OK, OZFFT_ERR_NONFINITE or
+   OZFFT_ERR_RANGE), and clear it. */
+int ozfft_get_status(ozfft_plan_t plan, void* stream);
+
+/* Plan facts and the transform counts of the most recent execution.
+   Synchronizes `stream` (the counts are computed on the device). */
+typedef struct {
+    int64_t n, N, batch;
+    int32_t K, L, nprimes, alpha, direction;
+    int32_t wstar_levels[2];      /* split levels of Re w~*, Im w~* */
+    int64_t ntt_forward_runtime;  /* forward NTTs of x~' slices, summed over the batch */
+    int64_t ntt_forward_plan;     /* forward NTTs of w~* slices (once per plan) */
+    int64_t ntt_inverse;          /* inverse NTTs, summed over the batch */
+    int64_t kernel_launches;      /* kernels enqueued by one ozfft_execute */
+    int64_t workspace_bytes;      /* device memory held by the plan */
+} ozfft_stats;
+int ozfft_get_stats(ozfft_plan_t plan, void* stream, ozfft_stats* out);
+
+/* Per-kernel device time of executions (the time breakdown of §5.5).  With
+   profiling enabled, ozfft_execute records a CUDA event on its stream before
+   and after every kernel it launches.  ozfft_get_profile synchronizes `stream`,
+   returns the device time summed per kernel slot over the executions since the
+   previous call, and restarts the sums.  Slots: */
+enum {
+    OZFFT_PROF_PREMUL = 0,      /* x~' = x (.) w and level-0 maxima */
+    OZFFT_PROF_SPLIT = 1,       /* the K split levels (K launches) */
+    OZFFT_PROF_SCHEDULE = 2,    /* Alg. 8 flush schedule */
+    OZFFT_PROF_NTT_FWD_COL = 3, /* forward NTT, column pass (two-pass lengths only) */
+    OZFFT_PROF_NTT_FWD_ROW = 4, /* forward NTT, row pass */
+    OZFFT_PROF_NTT_INV_ROW = 5, /* NTT-domain multiply-accumulate + inverse NTT row pass */
+    OZFFT_PROF_NTT_INV_COL = 6, /* inverse NTT, column pass (two-pass lengths only) */
+    OZFFT_PROF_CRT = 7,         /* Garner, rescale, accumulation, post-multiply */
+    OZFFT_PROF_SLOTS = 8
+};
+typedef struct {
+    int64_t executions;                  /* executions summed */
+    int64_t launches[OZFFT_PROF_SLOTS];  /* kernel launches per slot, summed */
+    double ms[OZFFT_PROF_SLOTS];         /* device milliseconds per slot, summed */
+} ozfft_profile;
+int ozfft_set_profiling(ozfft_plan_t plan, int enable);
+int ozfft_get_profile(ozfft_plan_t plan, void* stream, ozfft_profile* out);
+
+/* Release every resource of the plan (synchronizes its device first). */
+void ozfft_destroy(ozfft_plan_t plan);
+
+/* Text of an error code, and the detailed message of the last failure in the
+   calling thread. */
+const char* ozfft_error_string(int code);
+const char* ozfft_last_error(void);
+
+/* Test hook: copy one intermediate of the most recent execution (or of the
+   plan) to host memory in the oracle's natural layout.  Synchronizes
+   `stream`.  `index` selects the signal b (or is ignored).  Stages:
+     OZFFT_DUMP_CHIRP     n complex128                 chirp table w
+     OZFFT_DUMP_XPRIME    [2][N] binary64              Re/Im of x~' of signal b
+     OZFFT_DUMP_MU        [2][K+1] binary64            per-level maxima of signal b
+     OZFFT_DUMP_XRES      [2][K][P][N] uint32          slice residues of signal b before the NTT
+                                                       (plans made with options.debug only)
+     OZFFT_DUMP_XSPEC     [2][K][P][N] uint32          forward spectra of signal b, natural order
+     OZFFT_DUMP_YSPEC     [2][K][P][N] uint32          w~* spectra, natural order, times N^-1 * 2^32 mod p
+     OZFFT_DUMP_SCHED     [4][641] int32               per convolution RR, II, IR, RI of signal b:
+                                                       ngroups, S[64], size[64], pair[64][8] where
+                                                       S = s_x + s_y (c_x c_y = 2^S) and each pair
+                                                       is s*16 + t, in Alg. 8's flush order
+     OZFFT_DUMP_ZRES      [4][G][P][N] uint32          inverse-NTT outputs of signal b, G = K*K
+                                                       (groups beyond ngroups hold no data)
+   Returns the number of bytes written (or a negative OZFFT_ERR_* code); a
+   NULL `dst` just returns the size.  Valid only after one ozfft_execute. */
+enum {
+    OZFFT_DUMP_CHIRP = 0, OZFFT_DUMP_XPRIME = 1, OZFFT_DUMP_MU = 2, OZFFT_DUMP_XRES = 3,
+    OZFFT_DUMP_XSPEC = 4, OZFFT_DUMP_YSPEC = 5, OZFFT_DUMP_SCHED = 6, OZFFT_DUMP_ZRES = 7
+};
+int64_t ozfft_debug_dump(ozfft_plan_t plan, int stage, int64_t index, void* dst, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OZFFT_H */

@@ -1,0 +1,278 @@
+// k_crt.cu -- Garner CRT, exact accumulation, rounding and the Bluestein
+// post-multiply for libozfft (sm_103a).
+//
+// For every output y(k), k < n, of every signal: each flush group g of the
+// four real convolutions (RR, II, IR, RI, §4.5) contributes the CRT integer z'
+// of its inverse NTTs (Garner with symmetric digits, Eq. (1), §3.3) times
+// 1/(c_x c_y) = 2^-S_g (Alg. 8).  The real part of y' is the exact sum of the
+// RR terms minus the II terms and the imaginary part the exact sum of the IR and
+// RI terms, each rounded once to nearest binary64; then y = y' w (Alg. 1).  The
+// inverse direction conjugates and divides by n (Eq. (4)).
+//
+// The exact sums use integer arithmetic only (binary64 throughput is low on
+// this part): a thread keeps its element's sum as int64 limbs of 32-bit digits
+// in units of 2^-max(S), one limb column per thread in shared memory.  A term
+// z * 2^(max S - S_g) is split into four 32-bit digits and added to four limbs
+// without carries; one carry pass and an integer round-to-nearest-even at the
+// end produce the binary64 bit pattern.  Signals whose scales span more than
+// FAST_LIMBS limbs go to a second launch with wider columns.
+#include "oz_common.cuh"
+#include "oz_kernels.h"
+
+namespace oz {
+
+struct GarnerConst {
+    uint32_t inv01, inv01q;   // p0^-1 mod p1 and its Shoup quotient
+    uint32_t inv2, inv2q;     // (p0 p1)^-1 mod p2 and its Shoup quotient
+    uint32_t p0_mod2;         // p0 mod p2
+};
+
+__constant__ GarnerConst c_garner;
+
+constexpr uint32_t P0 = PRIME0, P1 = PRIME1, P2 = PRIME2;
+
+// 128-bit two's complement integer as (hi, lo)
+struct i128p { long long hi; unsigned long long lo; };
+
+__device__ __forceinline__ i128p garner(const uint32_t* z, int P)
+{
+    // z'_0: symmetric representative of z0 mod p0
+    long long v0 = (long long)z[0];
+    if (v0 > (long long)(P0 - 1) / 2) v0 -= P0;
+    // digit 1: ((z1 - z'_0) p0^-1) mod p1, symmetric
+    long long t = (long long)z[1] - v0;
+    if (t < 0) t += P1;
+    else if (t >= (long long)P1) t -= P1;
+    long long d1 = (long long)shoup((uint32_t)t, c_garner.inv01, c_garner.inv01q, P1);
+    if (d1 > (long long)(P1 - 1) / 2) d1 -= P1;
+    const long long z1 = v0 + d1 * (long long)P0;     // |z1| < p0 p1 / 2 < 2^62
+    i128p r;
+    if (P == 2) {
+        r.hi = z1 < 0 ? -1 : 0;
+        r.lo = (unsigned long long)z1;
+        return r;
+    }
+    // digit 2: ((z2 - z'_1) (p0 p1)^-1) mod p2, symmetric
+    const long long v0m = v0 < 0 ? v0 + P2 : v0;
+    const long long d1m = d1 < 0 ? d1 + P2 : d1;
+    const long long zm = (v0m + (d1m * (long long)c_garner.p0_mod2) % P2) % P2;   // z'_1 mod p2
+    long long t2 = (long long)z[2] - zm;
+    if (t2 < 0) t2 += P2;
+    long long d2 = (long long)shoup((uint32_t)t2, c_garner.inv2, c_garner.inv2q, P2);
+    if (d2 > (long long)(P2 - 1) / 2) d2 -= P2;
+    // z'_2 = z'_1 + d2 p0 p1 in 128 bits
+    const unsigned long long p01 = (unsigned long long)P0 * P1;
+    const unsigned long long ad = (unsigned long long)(d2 < 0 ? -d2 : d2);
+    unsigned long long plo = ad * p01, phi = __umul64hi(ad, p01);
+    if (d2 < 0) {
+        plo = ~plo + 1ull;
+        phi = ~phi + (plo == 0 ? 1ull : 0ull);
+    }
+    const unsigned long long zlo = (unsigned long long)z1;
+    const unsigned long long zhi = z1 < 0 ? ~0ull : 0ull;
+    r.lo = plo + zlo;
+    r.hi = (long long)(phi + zhi + (r.lo < plo ? 1ull : 0ull));
+    return r;
+}
+
+// acc[col + l*stride] += digits of z * 2^sh, l = sh/32 .. sh/32+3
+__device__ __forceinline__ void add_term(long long* acc, int stride, i128p z, int sh)
+{
+    const int q = sh >> 5, b = sh & 31;
+    const unsigned long long t0 = z.lo << b;
+    const unsigned long long t1 = b ? (((unsigned long long)z.hi << b) | (z.lo >> (64 - b))) : (unsigned long long)z.hi;
+    long long* a = acc + q * stride;
+    a[0] += (long long)(uint32_t)t0;
+    a[stride] += (long long)(uint32_t)(t0 >> 32);
+    a[2 * stride] += (long long)(uint32_t)t1;
+    a[3 * stride] += (long long)(int32_t)(uint32_t)(t1 >> 32);
+}
+
+// Round the integer sum of nl limbs (value = sum acc[l] 2^(32 l) 2^unit) to the
+// nearest binary64, ties to even, from integer operations only.
+__device__ double limbs_to_double(long long* acc, int stride, int nl, int unit)
+{
+    // carry pass: 32-bit digits in place (two's complement, the top digit signed)
+    long long carry = 0;
+    for (int l = 0; l < nl; ++l) {
+        const long long v = acc[l * stride] + carry;
+        acc[l * stride] = (long long)(uint32_t)v;
+        carry = v >> 32;
+    }
+    const bool neg = (acc[(nl - 1) * stride] >> 31) & 1;
+    if (neg) {   // magnitude by two's complement negation
+        unsigned long long c = 1;
+        for (int l = 0; l < nl; ++l) {
+            const unsigned long long s = (unsigned long long)(uint32_t)~(uint32_t)acc[l * stride] + c;
+            acc[l * stride] = (long long)(uint32_t)s;
+            c = s >> 32;
+        }
+    }
+    int top = nl - 1;
+    while (top >= 0 && (uint32_t)acc[top * stride] == 0) --top;
+    if (top < 0) return 0.0;
+    const uint32_t dt = (uint32_t)acc[top * stride];
+    const int lz = __clz(dt);
+    // 96-bit window from digits top, top-1, top-2, leading one moved to bit 63
+    const uint32_t d1 = top >= 1 ? (uint32_t)acc[(top - 1) * stride] : 0u;
+    const uint32_t d2 = top >= 2 ? (uint32_t)acc[(top - 2) * stride] : 0u;
+    const unsigned long long hi64 = ((unsigned long long)dt << 32) | d1;
+    const unsigned long long w = lz ? (hi64 << lz) | ((unsigned long long)d2 >> (32 - lz)) : hi64;
+    bool sticky = lz ? ((d2 << lz) != 0u) : (d2 != 0u);
+    for (int l = top - 3; l >= 0 && !sticky; --l) sticky = (uint32_t)acc[l * stride] != 0u;
+    const int lead = unit + 32 * top + 31 - lz;           // exponent of the leading one
+    const int eulp = max(lead - 52, -1074);
+    if (eulp > 971) return neg ? -__longlong_as_double(0x7ff0000000000000ll) : __longlong_as_double(0x7ff0000000000000ll);
+    const int kb = lead - eulp + 1;                         // kept bits (<= 53)
+    unsigned long long qv;
+    bool rb;
+    if (kb >= 1) {
+        qv = w >> (64 - kb);
+        rb = (w >> (63 - kb)) & 1ull;
+        sticky = sticky || (kb < 63 && (w << (kb + 1)) != 0ull);
+    } else if (kb == 0) {
+        qv = 0;
+        rb = true;                                          // the leading one is the round bit
+        sticky = sticky || (w << 1) != 0ull;
+    } else {
+        qv = 0;
+        rb = false;
+        sticky = true;
+    }
+    if (rb && (sticky || (qv & 1ull))) qv += 1;
+    const unsigned long long bits = ((unsigned long long)(eulp + 1074) << 52) + qv;
+    const double r = __longlong_as_double((long long)bits);
+    return neg ? -r : r;
+}
+
+constexpr int FAST_LIMBS = 12;
+constexpr int FAST_THREADS = 128;
+constexpr int WIDE_LIMBS = 144;
+constexpr int WIDE_THREADS = 32;
+constexpr int CRT_CHUNK = 2048;
+
+// limbs needed for a signal's scale span
+__device__ __forceinline__ int limbs_for(int smin, int smax) { return ((smax - smin) >> 5) + 5; }
+
+template <bool WIDE>
+__global__ void __launch_bounds__(WIDE ? WIDE_THREADS : FAST_THREADS) crt_post_kernel(CrtArgs a)
+{
+    extern __shared__ long long acc_dyn[];
+    __shared__ long long acc_fast[WIDE ? 1 : FAST_LIMBS * FAST_THREADS];
+    __shared__ int s_info[3];
+    long long* acc = WIDE ? acc_dyn : acc_fast;
+    const int chunks = (int)((a.n + CRT_CHUNK - 1) / CRT_CHUNK);
+    const int64_t work = a.B * chunks;
+    for (int64_t item = blockIdx.x; item < work; item += gridDim.x) {
+        const int64_t b = item / chunks;
+        const int64_t j0 = (item % chunks) * (int64_t)CRT_CHUNK;
+        const int64_t j1 = min(a.n, j0 + CRT_CHUNK);
+        const Sched* sc = a.sched + b * 4;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int smin = 0, smax = 0, any = 0;
+            for (int c = 0; c < 4; ++c)
+                for (int g = 0; g < sc[c].ngroups; ++g) {
+                    const int S = sc[c].S[g];
+                    if (!any || S < smin) smin = S;
+                    if (!any || S > smax) smax = S;
+                    any = 1;
+                }
+            s_info[0] = smin;
+            s_info[1] = smax;
+            s_info[2] = any;
+        }
+        __syncthreads();
+        const int smin = s_info[0], smax = s_info[1], any = s_info[2];
+        const int nl = limbs_for(smin, smax);
+        if (WIDE ? (nl <= FAST_LIMBS) : (nl > FAST_LIMBS)) continue;   // the other launch owns it
+        if (nl > WIDE_LIMBS) {   // cannot happen for finite inputs that passed the split's range check
+            if (threadIdx.x == 0) atomicOr(a.status, ST_RANGE);
+            continue;
+        }
+        long long* col = acc + threadIdx.x;
+        const int stride = blockDim.x;
+        for (int64_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
+            double yp[2] = {0.0, 0.0};
+            if (any) {
+                for (int part = 0; part < 2; ++part) {
+                    for (int l = 0; l < nl; ++l) col[l * stride] = 0;
+                    for (int c = 2 * part; c < 2 * part + 2; ++c) {
+                        const Sched& S = sc[c];
+                        for (int g = 0; g < S.ngroups; ++g) {
+                            const uint32_t* zp = a.Z + (((b * 4 + c) * a.G + g) * a.P) * a.N + j;
+                            uint32_t z[3];
+                            z[0] = zp[0];
+                            z[1] = zp[a.N];
+                            z[2] = a.P > 2 ? zp[2 * a.N] : 0u;
+                            i128p v = garner(z, a.P);
+                            if (c == 1) {   // II enters the real part with a minus sign
+                                v.lo = ~v.lo + 1ull;
+                                v.hi = (long long)(~(unsigned long long)v.hi + (v.lo == 0 ? 1ull : 0ull));
+                            }
+                            add_term(col, stride, v, smax - S.S[g]);
+                        }
+                    }
+                    yp[part] = limbs_to_double(col, stride, nl, -smax);
+                }
+            }
+            const double2 w = a.w[j];
+            double re, im;
+            cmul(yp[0], yp[1], w.x, w.y, re, im);
+            if (a.direction == 1) {
+                im = -im;
+                re = __ddiv_rn(re, (double)a.n);
+                im = __ddiv_rn(im, (double)a.n);
+            }
+            a.out[b * a.n + j] = make_double2(re, im);
+        }
+    }
+}
+
+static bool s_garner_ready = false;
+
+static uint64_t host_powmod(uint64_t b, uint64_t e, uint64_t m)
+{
+    unsigned __int128 r = 1 % m, x = b % m;
+    while (e) {
+        if (e & 1) r = r * x % m;
+        x = x * x % m;
+        e >>= 1;
+    }
+    return (uint64_t)r;
+}
+
+int crt_launches() { return 2; }
+
+cudaError_t launch_crt_post(const CrtArgs& a, cudaStream_t s)
+{
+    if (!s_garner_ready) {
+        GarnerConst gc;
+        gc.inv01 = (uint32_t)host_powmod(P0 % P1, P1 - 2, P1);
+        gc.inv01q = (uint32_t)(((uint64_t)gc.inv01 << 32) / P1);
+        const uint64_t p01m2 = (uint64_t)((unsigned __int128)P0 * P1 % P2);
+        gc.inv2 = (uint32_t)host_powmod(p01m2, P2 - 2, P2);
+        gc.inv2q = (uint32_t)(((uint64_t)gc.inv2 << 32) / P2);
+        gc.p0_mod2 = P0 % P2;
+        cudaError_t e = cudaMemcpyToSymbol(c_garner, &gc, sizeof(gc));
+        if (e != cudaSuccess) return e;
+        s_garner_ready = true;
+    }
+    const int64_t chunks = (a.n + CRT_CHUNK - 1) / CRT_CHUNK;
+    crt_post_kernel<false><<<(unsigned)(a.B * chunks), FAST_THREADS, 0, s>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // signals with a wide scale span (rare): small blocks, one limb column per thread
+    const size_t smem = sizeof(long long) * WIDE_LIMBS * WIDE_THREADS;
+    static bool attr = false;
+    if (!attr) {
+        e = cudaFuncSetAttribute(crt_post_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const int64_t grid = a.B * chunks < 1024 ? a.B * chunks : 1024;
+    crt_post_kernel<true><<<(unsigned)grid, WIDE_THREADS, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace oz

@@ -1,0 +1,254 @@
+// k_split.cu -- chirp table, Bluestein pre-multiply and the Ozaki split for
+// libozfft (sm_103a).
+//
+//   chirp_kernel   w(j) = exp(-i pi j^2 / n) (Alg. 1), correctly rounded to
+//                  binary64 from a double-word evaluation (plan time);
+//   wstar_kernel   w~* = ZeroPad+-(conj w, N) (§3.2) (plan time);
+//   premul_kernel  x~'(j) = x(j) w(j) for j < n, 0 up to N (Alg. 1 step 1);
+//   split_kernel   one level k of Alg. 3 on every real vector of the batch.
+//
+// Each real vector v (Re or Im of a signal) is a contiguous row r[v][0..N).
+// Its per-level maxima mu[v][k] = ||r^(k)||_inf are reduced with atomicMax on
+// the binary64 bit pattern (non-negative doubles order like their bits); a
+// kernel boundary separates level k's reduction from level k+1's use, which is
+// the grid-wide dependency Alg. 3 has between mu^(k) and sigma^(k).
+#include "oz_common.cuh"
+#include "oz_kernels.h"
+
+namespace oz {
+
+// ----------------------------------------------------- double-word sin / cos
+struct dw { double h, l; };
+
+__device__ __forceinline__ dw dw_norm(double a, double b)
+{
+    dw r;
+    fast_two_sum(a, b, r.h, r.l);
+    return r;
+}
+__device__ __forceinline__ dw dw_mul(dw a, dw b)
+{
+    double p = __dmul_rn(a.h, b.h);
+    double e = __fma_rn(a.h, b.h, -p);
+    e = __fma_rn(a.h, b.l, e);
+    e = __fma_rn(a.l, b.h, e);
+    return dw_norm(p, e);
+}
+__device__ __forceinline__ dw dw_div_d(dw a, double d)
+{
+    double q1 = __ddiv_rn(a.h, d);
+    double p = __dmul_rn(q1, d);
+    double pe = __fma_rn(q1, d, -p);                 // q1 d = p + pe exactly
+    double r = __dadd_rn(__dsub_rn(__dsub_rn(a.h, p), pe), a.l);
+    double q2 = __ddiv_rn(r, d);
+    return dw_norm(q1, q2);
+}
+__device__ __forceinline__ dw dw_one_minus(dw a)
+{
+    double s, e;
+    two_sum(1.0, -a.h, s, e);
+    return dw_norm(s, __dsub_rn(e, a.l));
+}
+
+// sin(pi a/d), cos(pi a/d) for 0 <= a/d <= 1/4, Taylor series in Horner form
+// on x = pi a/d in double-word arithmetic (truncation below 1e-40).
+__device__ void sincospi_small(int64_t a, int64_t d, double& s_out, double& c_out)
+{
+    if (a == 0) { s_out = 0.0; c_out = 1.0; return; }
+    const dw pi = {3.141592653589793116e+00, 1.224646799147353207e-16};
+    double ad = (double)a, dd = (double)d;
+    double t1 = __ddiv_rn(ad, dd);
+    double rem = __fma_rn(-t1, dd, ad);              // exact remainder
+    dw t = dw_norm(t1, __ddiv_rn(rem, dd));
+    dw x = dw_mul(pi, t);
+    dw x2 = dw_mul(x, x);
+    dw s = {1.0, 0.0}, c = {1.0, 0.0};
+    for (int k = 17; k >= 1; --k) {
+        s = dw_one_minus(dw_div_d(dw_mul(x2, s), (double)((2 * k) * (2 * k + 1))));
+        c = dw_one_minus(dw_div_d(dw_mul(x2, c), (double)((2 * k - 1) * (2 * k))));
+    }
+    s = dw_mul(x, s);
+    s_out = __dadd_rn(s.h, s.l);
+    c_out = __dadd_rn(c.h, c.l);
+}
+
+// sin, cos of pi a/d for 0 <= a/d < 2: exact integer octant reduction, then
+// the small-angle evaluation.
+__device__ void sincospi_frac(int64_t a, int64_t d, double& s, double& c)
+{
+    bool neg_s = false, neg_c = false, swap = false;
+    if (a >= d) { a -= d; neg_s = !neg_s; neg_c = !neg_c; }
+    if (2 * a > d) { a = d - a; neg_c = !neg_c; }
+    if (4 * a > d) { a = d - 2 * a; d = 2 * d; swap = true; }
+    double sv, cv;
+    sincospi_small(a, d, sv, cv);
+    if (swap) { double t = sv; sv = cv; cv = t; }
+    s = neg_s ? -sv : sv;
+    c = neg_c ? -cv : cv;
+}
+
+__global__ void chirp_kernel(double2* w, int64_t n)
+{
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t r = ((uint64_t)j * (uint64_t)j) % (uint64_t)(2 * n);   // j < n <= 2^24
+        double s, c;
+        sincospi_frac((int64_t)r, n, s, c);
+        w[j] = make_double2(c == 0.0 ? 0.0 : c, s == 0.0 ? 0.0 : -s);   // zero components are +0
+    }
+}
+
+// ------------------------------------------------------------- reductions
+__device__ __forceinline__ void block_max_to(uint64_t* dst, double v)
+{
+    __shared__ double red[32];
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        v = lane < nw ? red[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+        if (lane == 0 && v > 0.0) atomicMax((unsigned long long*)dst, (unsigned long long)__double_as_longlong(v));
+    }
+}
+
+// chunking: a CTA works on CHUNK consecutive elements of one vector
+constexpr int SPLIT_THREADS = 256;
+constexpr int CHUNK = 4096;
+
+__global__ void __launch_bounds__(SPLIT_THREADS) wstar_kernel(const double2* __restrict__ w, int64_t n, int64_t N,
+                                                              double* __restrict__ r, uint64_t* __restrict__ mu, int K)
+{
+    const int64_t chunks = (N + CHUNK - 1) / CHUNK;
+    const int v = (int)(blockIdx.x / chunks);
+    const int64_t j0 = (blockIdx.x % chunks) * CHUNK;
+    const int64_t j1 = min(N, j0 + CHUNK);
+    double m = 0.0;
+    for (int64_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
+        int64_t src = -1;
+        if (j < n) src = j;
+        else if (N != n && j >= N - n + 1) src = N - j;
+        double val = 0.0;
+        if (src >= 0) {
+            const double2 ws = w[src];
+            val = v == 0 ? ws.x : -ws.y;   // conj(w)
+        }
+        r[(int64_t)v * N + j] = val;
+        m = fmax(m, fabs(val));
+    }
+    block_max_to(&mu[(int64_t)v * (K + 1) + 0], m);
+}
+
+__global__ void __launch_bounds__(SPLIT_THREADS) premul_kernel(const double2* __restrict__ x,
+                                                               const double2* __restrict__ w, int64_t n, int64_t N,
+                                                               int conj_in, double* __restrict__ r,
+                                                               uint64_t* __restrict__ mu, int K, int* status)
+{
+    const int64_t chunks = (N + CHUNK - 1) / CHUNK;
+    const int64_t b = blockIdx.x / chunks;
+    const int64_t j0 = (blockIdx.x % chunks) * CHUNK;
+    const int64_t j1 = min(N, j0 + CHUNK);
+    double mr = 0.0, mi = 0.0;
+    bool bad = false;
+    double* rr = r + (2 * b) * N;
+    double* ri = rr + N;
+    for (int64_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
+        double re = 0.0, im = 0.0;
+        if (j < n) {
+            const double2 xv = x[b * n + j];
+            const double2 wv = w[j];
+            const double xi = conj_in ? -xv.y : xv.y;
+            if (!isfinite(xv.x) || !isfinite(xv.y)) bad = true;
+            cmul(xv.x, xi, wv.x, wv.y, re, im);
+        }
+        rr[j] = re;
+        ri[j] = im;
+        mr = fmax(mr, fabs(re));
+        mi = fmax(mi, fabs(im));
+    }
+    if (bad) atomicOr(status, ST_NONFINITE);
+    block_max_to(&mu[(2 * b) * (K + 1)], mr);
+    __syncthreads();
+    block_max_to(&mu[(2 * b + 1) * (K + 1)], mi);
+}
+
+// Level k of Alg. 3 for every vector: sigma = 2^(ceil(log2 mu_k) + rho),
+// slice = (r + sigma) - sigma, r <- r - slice, q = slice * 2^(alpha - e)
+// (an integer with |q| <= 2^alpha), residues q mod p written per prime.
+__global__ void __launch_bounds__(SPLIT_THREADS) split_kernel(int k, double* __restrict__ r,
+                                                              uint64_t* __restrict__ mu, int64_t N, int K,
+                                                              int alpha, int P, uint32_t* __restrict__ X,
+                                                              int write_r, int* status)
+{
+    const int64_t chunks = (N + CHUNK - 1) / CHUNK;
+    const int64_t v = blockIdx.x / chunks;
+    const int64_t j0 = (blockIdx.x % chunks) * CHUNK;
+    const int64_t j1 = min(N, j0 + CHUNK);
+    const double muk = __longlong_as_double((long long)mu[v * (K + 1) + k]);
+    if (!(muk > 0.0)) return;                       // level empty: mu^(k) = 0 ends the split
+    const int rho = 53 - alpha;
+    const int e = ceil_log2_pos(muk);
+    if (e + rho > 1023) {
+        if (threadIdx.x == 0) atomicOr(status, ST_RANGE);
+        return;
+    }
+    const double sigma = ldexp(1.0, e + rho);
+    int sh = alpha - e;                             // q = s * 2^sh, done as exact power-of-two products
+    double pre = 1.0;
+    if (sh > 1000) { pre = ldexp(1.0, 1000); sh -= 1000; }
+    const double scale = ldexp(1.0, sh);
+    double* rv = r + v * N;
+    uint32_t* xk = X + ((v * K + k) * P) * N;
+    double m = 0.0;
+    for (int64_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
+        const double x = rv[j];
+        const double s = __dsub_rn(__dadd_rn(x, sigma), sigma);
+        const double rn = __dsub_rn(x, s);
+        const long long q = __double2ll_rn(__dmul_rn(__dmul_rn(s, pre), scale));
+#pragma unroll
+        for (int pi = 0; pi < MAX_PRIMES; ++pi) {
+            if (pi >= P) break;
+            const long long p = (long long)prime_of(pi);
+            long long a = alpha <= 30 ? q : q % p;   // |q| <= 2^alpha < p when alpha <= 30
+            if (a < 0) a += p;
+            xk[pi * N + j] = (uint32_t)a;
+        }
+        if (write_r) rv[j] = rn;
+        m = fmax(m, fabs(rn));
+    }
+    if (k + 1 <= K) block_max_to(&mu[v * (K + 1) + k + 1], m);
+}
+
+// ------------------------------------------------------------------ launchers
+static unsigned grid_for(int64_t nvec, int64_t N) { return (unsigned)(nvec * ((N + CHUNK - 1) / CHUNK)); }
+
+cudaError_t launch_chirp(double2* w, int64_t n, cudaStream_t s)
+{
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > 65535) blocks = 65535;
+    chirp_kernel<<<(unsigned)blocks, 256, 0, s>>>(w, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wstar(const double2* w, int64_t n, int64_t N, double* r, uint64_t* mu, int K, int*, cudaStream_t s)
+{
+    wstar_kernel<<<grid_for(2, N), SPLIT_THREADS, 0, s>>>(w, n, N, r, mu, K);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_premul(const double2* x, const double2* w, int64_t n, int64_t N, int64_t B, int conj_in, double* r,
+                          uint64_t* mu, int K, int* status, cudaStream_t s)
+{
+    premul_kernel<<<grid_for(B, N), SPLIT_THREADS, 0, s>>>(x, w, n, N, conj_in, r, mu, K, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_split_level(int k, double* r, const uint64_t*, uint64_t* mu, int64_t N, int64_t nvec, int K,
+                               int alpha, int P, uint32_t* X, int write_r, int* status, cudaStream_t s)
+{
+    split_kernel<<<grid_for(nvec, N), SPLIT_THREADS, 0, s>>>(k, r, mu, N, K, alpha, P, X, write_r, status);
+    return cudaGetLastError();
+}
+
+}  // namespace oz

@@ -1,0 +1,63 @@
+// oz_kernels.h -- kernel launch interface between the plan (plan.cu) and the
+// kernel translation units of libozfft.  Internal; not part of the C ABI.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "oz_common.cuh"
+
+namespace oz {
+
+// Geometry of one batched NTT launch (forward or inverse).
+struct NttGeom {
+    int64_t N;          // transform length 2^lgN
+    int64_t nvec;       // vectors in the launch
+    int lgN, m1, m2;    // column-pass stages m1 (0: single pass), row-pass stages m2
+    int T;              // columns per CTA in the column pass
+    int rows_per_cta;   // contiguous 2^m2 blocks per CTA in the row pass
+    int P, K, G;        // primes, split cap, flush-group capacity
+    const int32_t* kcnt;   // [B][2] live split levels of x~' (forward skip test)
+    const Sched* sched;    // [B][4] flush schedules (inverse skip test and MAC)
+};
+
+// Inputs of the multiply-accumulate fused into the inverse NTT's load.
+struct MacSrc {
+    const uint32_t* X;   // [B][2][K][P][N] forward spectra of x~' slices
+    const uint32_t* Ym;  // [2][K][P][N]   w~* spectra * N^-1 * 2^32 mod p
+};
+
+// k_ntt.cu
+void ntt_configure(NttGeom& g, int64_t N);   // fills lgN, m1, m2, T, rows_per_cta
+int64_t ntt_launches(const NttGeom& g);        // kernels per transform direction
+// one pass each; a transform is col+row (forward) or row+col (inverse), the
+// column pass only when g.m1 > 0
+cudaError_t launch_ntt_fwd_col(const NttGeom& g, uint32_t* X, const uint2* tw, cudaStream_t s);
+cudaError_t launch_ntt_fwd_row(const NttGeom& g, uint32_t* X, const uint2* tw, cudaStream_t s);
+cudaError_t launch_ntt_inv_row(const NttGeom& g, uint32_t* Z, const uint2* twinv, MacSrc mac, cudaStream_t s);
+cudaError_t launch_ntt_inv_col(const NttGeom& g, uint32_t* Z, const uint2* twinv, cudaStream_t s);
+cudaError_t launch_ntt_forward(const NttGeom& g, uint32_t* X, const uint2* tw, cudaStream_t s);
+
+// k_split.cu
+cudaError_t launch_chirp(double2* w, int64_t n, cudaStream_t s);
+cudaError_t launch_wstar(const double2* w, int64_t n, int64_t N, double* r, uint64_t* mu, int K, int* status,
+                         cudaStream_t s);
+cudaError_t launch_premul(const double2* x, const double2* w, int64_t n, int64_t N, int64_t B, int conj_in,
+                          double* r, uint64_t* mu, int K, int* status, cudaStream_t s);
+cudaError_t launch_split_level(int k, double* r, const uint64_t* mu_in, uint64_t* mu_out, int64_t N,
+                               int64_t nvec, int K, int alpha, int P, uint32_t* X, int write_r, int* status,
+                               cudaStream_t s);
+
+// k_crt.cu
+struct CrtArgs {
+    const uint32_t* Z;     // [B][4][G][P][N] inverse NTT outputs (natural order)
+    const Sched* sched;    // [B][4]
+    const double2* w;      // [n] chirp
+    double2* out;          // [B][n]
+    int64_t n, N, B;
+    int P, G, direction;
+    int* status;           // data-dependent status bits
+};
+int crt_launches();        // kernels per launch_crt_post
+cudaError_t launch_crt_post(const CrtArgs& a, cudaStream_t s);
+
+}  // namespace oz

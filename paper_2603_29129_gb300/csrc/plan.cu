@@ -1,0 +1,619 @@
+// plan.cu -- plans, the C ABI of include/ozfft.h, and the two small kernels
+// that run between the big stages: the Alg. 8 flush schedule and the
+// conversion of the w~* spectra to Montgomery form.
+//
+// Device memory of a plan (B = batch, K = split cap, P = primes, G = K*K):
+//   chirp  [n] double2                         w(j) = exp(-i pi j^2/n)
+//   tw     [P][N/2] uint2, twinv likewise      (w_N^e, floor(w_N^e 2^32/p)), e < N/2
+//   Ym     [2][K][P][N] uint32                 w~* spectra * N^-1 * 2^32 mod p (bit-reversed order)
+//   r      [B][2][N] binary64                  x~' then the split residuals
+//   mu     [B][2][K+1] uint64                  bit patterns of ||r^(k)||_inf
+//   X      [B][2][K][P][N] uint32              slice residues, then spectra (bit-reversed)
+//   kcnt   [B][2] int32, sched [B][4] Sched    live levels, flush schedules
+//   Z      [B][4][G][P][N] uint32              inverse NTT outputs (natural order)
+// Every array is allocated once per plan; an execution allocates nothing.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/ozfft.h"
+#include "oz_common.cuh"
+#include "oz_kernels.h"
+
+using namespace oz;
+
+static thread_local std::string g_last_error;
+
+static int fail(int code, const std::string& msg)
+{
+    g_last_error = msg;
+    return code;
+}
+
+#define CUDA_TRY(call)                                                                          \
+    do {                                                                                        \
+        cudaError_t e_ = (call);                                                                \
+        if (e_ != cudaSuccess)                                                                  \
+            return fail(OZFFT_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));    \
+    } while (0)
+
+struct ozfft_plan_s {
+    int64_t n = 0, N = 0, B = 0;
+    int direction = -1, K = 3, L = 1, P = 2, alpha = 0, G = 9, debug = 0;
+    int device = 0;
+    NttGeom geom_fwd{}, geom_inv{};
+    int64_t launches = 0, bytes = 0;
+    int32_t wk_host[2] = {0, 0};
+    // device
+    double2* chirp = nullptr;
+    uint2* tw = nullptr;
+    uint2* twinv = nullptr;
+    uint32_t* Ym = nullptr;
+    int32_t* wk = nullptr;       // [2]
+    int32_t* wsexp = nullptr;    // [2][K]
+    double* r = nullptr;
+    uint64_t* mu = nullptr;
+    uint32_t* X = nullptr;
+    int32_t* kcnt = nullptr;
+    Sched* sched = nullptr;
+    uint32_t* Z = nullptr;
+    int* status = nullptr;
+    double* dbg_r = nullptr;     // [B][2][N] (debug plans)
+    uint32_t* dbg_X = nullptr;   // [B][2][K][P][N] (debug plans)
+    double2* stage_in = nullptr; // host-buffer execution staging [B][n]
+    double2* stage_out = nullptr;
+    bool executed = false;
+    // per-kernel timing: each execution leaves a start event and one event per kernel
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev_pool;
+    struct Rec {
+        cudaEvent_t start;
+        std::vector<std::pair<int, cudaEvent_t>> marks;
+    };
+    std::vector<Rec> pending;
+    Rec* cur = nullptr;
+};
+
+static cudaEvent_t take_event(ozfft_plan_s* p)
+{
+    cudaEvent_t e = nullptr;
+    if (!p->ev_pool.empty()) {
+        e = p->ev_pool.back();
+        p->ev_pool.pop_back();
+    } else if (cudaEventCreate(&e) != cudaSuccess) {
+        e = nullptr;
+    }
+    return e;
+}
+
+// record the end of a kernel of `slot` on the execution stream (profiling only)
+static void mark(ozfft_plan_s* p, int slot, cudaStream_t s)
+{
+    if (!p->cur) return;
+    cudaEvent_t e = take_event(p);
+    if (!e) return;
+    cudaEventRecord(e, s);
+    p->cur->marks.emplace_back(slot, e);
+}
+
+// ------------------------------------------------------------ host modular math
+static uint64_t mulmod_h(uint64_t a, uint64_t b, uint64_t m) { return (uint64_t)((unsigned __int128)a * b % m); }
+static uint64_t powmod_h(uint64_t b, uint64_t e, uint64_t m)
+{
+    uint64_t r = 1 % m;
+    b %= m;
+    for (; e; e >>= 1) {
+        if (e & 1) r = mulmod_h(r, b, m);
+        b = mulmod_h(b, b, m);
+    }
+    return r;
+}
+// smallest g whose order modulo the prime p is p - 1
+static uint64_t primitive_root_h(uint64_t p)
+{
+    std::vector<uint64_t> f;
+    uint64_t m = p - 1;
+    for (uint64_t d = 2; d * d <= m; ++d)
+        if (m % d == 0) {
+            f.push_back(d);
+            while (m % d == 0) m /= d;
+        }
+    if (m > 1) f.push_back(m);
+    for (uint64_t g = 2;; ++g) {
+        bool ok = true;
+        for (uint64_t q : f) ok = ok && powmod_h(g, (p - 1) / q, p) != 1;
+        if (ok) return g;
+    }
+}
+
+// alpha = max{a : 2 L n 4^a < P} (§4.4), capped at 52; -1 if none
+static int alpha_h(int64_t n, int L, int P)
+{
+    unsigned __int128 prod = 1;
+    for (int i = 0; i < P; ++i) prod *= prime_of(i);
+    const unsigned __int128 base = (unsigned __int128)2 * (unsigned)L * (uint64_t)n;
+    int a = -1;
+    for (int t = 0; t <= 52; ++t) {
+        int bits = 0;
+        while (bits < 128 && ((unsigned __int128)1 << bits) <= base) ++bits;
+        if (bits + 2 * t >= 127) break;
+        if ((base << (2 * t)) < prod) a = t; else break;
+    }
+    return a;
+}
+
+static int ceil_log2_h(double mu)
+{
+    int E;
+    double m = std::frexp(mu, &E);
+    return m == 0.5 ? E - 1 : E;
+}
+
+// ------------------------------------------------------------ small kernels
+// Alg. 8 flush schedule of every (signal, real convolution): the x~' split
+// levels and scales come from mu, those of w~* from the plan.
+__global__ void schedule_kernel(const uint64_t* __restrict__ mu, int64_t B, int K, int L, int alpha,
+                                const int32_t* __restrict__ wk, const int32_t* __restrict__ wsexp,
+                                Sched* __restrict__ sched, int32_t* __restrict__ kcnt)
+{
+    const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (id >= B * 4) return;
+    const int64_t b = id >> 2;
+    const int c = (int)(id & 3);
+    const int vx = (c == 0 || c == 3) ? 0 : 1;
+    const int vw = (c == 0 || c == 2) ? 0 : 1;
+    int sx[MAX_K];
+    int kx = 0;
+    for (int k = 0; k < K; ++k) {
+        const double m = __longlong_as_double((long long)mu[(b * 2 + vx) * (K + 1) + k]);
+        if (!(m > 0.0)) break;
+        sx[kx++] = alpha - ceil_log2_pos(m);
+    }
+    if (c < 2) kcnt[b * 2 + vx] = kx;
+    const int ky = wk[vw];
+    Sched& S = sched[id];
+    int g = 0, l = 0;
+    if (kx > 0 && ky > 0) {
+        int cur = sx[kx - 1] + wsexp[vw * K + ky - 1];
+        for (int k = kx + ky - 2; k >= 0; --k) {
+            const int s0 = max(0, k - ky + 1), s1 = min(kx - 1, k);
+            for (int s = s0; s <= s1; ++s) {
+                const int t = k - s;
+                const int sc = sx[s] + wsexp[vw * K + t];
+                if (l >= L || sc != cur) {   // flush: start a new group
+                    ++g;
+                    cur = sc;
+                    l = 0;
+                }
+                S.S[g] = cur;
+                S.pair[g][l] = s * 16 + t;
+                ++l;
+                S.size[g] = l;
+            }
+        }
+        ++g;
+    }
+    S.ngroups = g;
+}
+
+// Y -> Y * N^-1 * 2^32 mod p, via Montgomery with the constant N^-1 2^64 mod p
+__global__ void ymont_kernel(uint32_t* Y, int64_t N, int64_t total, int P, uint32_t c0, uint32_t c1, uint32_t c2)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int pi = (int)((i / N) % P);
+        const uint32_t c = pi == 0 ? c0 : (pi == 1 ? c1 : c2);
+        Y[i] = mont_mul(Y[i], c, prime_of(pi), pneg_inv_of(pi));
+    }
+}
+
+// ------------------------------------------------------------ plan lifetime
+static void plan_free(ozfft_plan_s* p)
+{
+    void* ptrs[] = {p->chirp, p->tw, p->twinv, p->Ym, p->wk, p->wsexp, p->r, p->mu, p->X, p->kcnt, p->sched,
+                    p->Z, p->status, p->dbg_r, p->dbg_X, p->stage_in, p->stage_out};
+    for (void* q : ptrs)
+        if (q) cudaFree(q);
+    for (auto& r : p->pending) {
+        p->ev_pool.push_back(r.start);
+        for (auto& m : r.marks) p->ev_pool.push_back(m.second);
+    }
+    for (cudaEvent_t e : p->ev_pool)
+        if (e) cudaEventDestroy(e);
+    delete p;
+}
+
+template <typename T>
+static int dalloc(ozfft_plan_s* p, T** ptr, size_t count)
+{
+    const size_t bytes = sizeof(T) * (count ? count : 1);
+    cudaError_t e = cudaMalloc((void**)ptr, bytes);
+    if (e != cudaSuccess) {
+        *ptr = nullptr;
+        return fail(OZFFT_ERR_ALLOC, std::string("cudaMalloc of ") + std::to_string(bytes) + " bytes: " +
+                                         cudaGetErrorString(e));
+    }
+    p->bytes += (int64_t)bytes;
+    return OZFFT_OK;
+}
+
+static int plan_build(ozfft_plan_s* p)
+{
+    const int64_t N = p->N, B = p->B;
+    const int K = p->K, P = p->P;
+    int rc;
+    CUDA_TRY(cudaGetDevice(&p->device));
+    for (int i = 0; i < P; ++i)
+        if ((uint32_t)(prime_of(i) * pneg_inv_of(i)) != 0xffffffffu) return fail(OZFFT_ERR_ARG, "Montgomery constant");
+    if ((rc = dalloc(p, &p->chirp, p->n))) return rc;
+    if ((rc = dalloc(p, &p->tw, (size_t)P * (N / 2)))) return rc;
+    if ((rc = dalloc(p, &p->twinv, (size_t)P * (N / 2)))) return rc;
+    if ((rc = dalloc(p, &p->Ym, (size_t)2 * K * P * N))) return rc;
+    if ((rc = dalloc(p, &p->wk, 2))) return rc;
+    if ((rc = dalloc(p, &p->wsexp, (size_t)2 * K))) return rc;
+    if ((rc = dalloc(p, &p->r, (size_t)B * 2 * N))) return rc;
+    if ((rc = dalloc(p, &p->mu, (size_t)B * 2 * (K + 1)))) return rc;
+    if ((rc = dalloc(p, &p->X, (size_t)B * 2 * K * P * N))) return rc;
+    if ((rc = dalloc(p, &p->kcnt, (size_t)B * 2))) return rc;
+    if ((rc = dalloc(p, &p->sched, (size_t)B * 4))) return rc;
+    if ((rc = dalloc(p, &p->Z, (size_t)B * 4 * p->G * P * N))) return rc;
+    if ((rc = dalloc(p, &p->status, 1))) return rc;
+    if (p->debug) {
+        if ((rc = dalloc(p, &p->dbg_r, (size_t)B * 2 * N))) return rc;
+        if ((rc = dalloc(p, &p->dbg_X, (size_t)B * 2 * K * P * N))) return rc;
+    }
+    CUDA_TRY(cudaMemset(p->status, 0, sizeof(int)));
+    CUDA_TRY(cudaMemset(p->sched, 0, sizeof(Sched) * B * 4));
+    CUDA_TRY(cudaMemset(p->kcnt, 0, sizeof(int32_t) * B * 2));
+
+    // twiddle tables: w_N = g^((p-1)/N), entries (w^e, floor(w^e 2^32 / p)) for e < N/2
+    {
+        std::vector<uint2> t((size_t)P * (N / 2)), ti((size_t)P * (N / 2));
+        for (int i = 0; i < P; ++i) {
+            const uint64_t pr = prime_of(i);
+            const uint64_t w = powmod_h(primitive_root_h(pr), (pr - 1) / (uint64_t)N, pr);
+            const uint64_t wi = powmod_h(w, pr - 2, pr);
+            uint64_t a = 1, ai = 1;
+            for (int64_t e = 0; e < N / 2; ++e) {
+                t[(size_t)i * (N / 2) + e] = make_uint2((uint32_t)a, (uint32_t)((a << 32) / pr));
+                ti[(size_t)i * (N / 2) + e] = make_uint2((uint32_t)ai, (uint32_t)((ai << 32) / pr));
+                a = mulmod_h(a, w, pr);
+                ai = mulmod_h(ai, wi, pr);
+            }
+        }
+        if (N >= 2) {
+            CUDA_TRY(cudaMemcpy(p->tw, t.data(), sizeof(uint2) * t.size(), cudaMemcpyHostToDevice));
+            CUDA_TRY(cudaMemcpy(p->twinv, ti.data(), sizeof(uint2) * ti.size(), cudaMemcpyHostToDevice));
+        }
+    }
+
+    ntt_configure(p->geom_fwd, N);
+    p->geom_fwd.P = P;
+    p->geom_fwd.K = K;
+    p->geom_fwd.G = p->G;
+    p->geom_inv = p->geom_fwd;
+
+    // chirp, then w~* split + forward NTTs (§4.5: precomputed once)
+    cudaStream_t s = 0;
+    CUDA_TRY(launch_chirp(p->chirp, p->n, s));
+    {
+        double* rw = nullptr;
+        uint64_t* wmu = nullptr;
+        if ((rc = dalloc(p, &rw, (size_t)2 * N))) return rc;
+        if ((rc = dalloc(p, &wmu, (size_t)2 * (K + 1)))) { cudaFree(rw); return rc; }
+        p->bytes -= (int64_t)(sizeof(double) * 2 * N + sizeof(uint64_t) * 2 * (K + 1));
+        cudaError_t e = cudaMemset(wmu, 0, sizeof(uint64_t) * 2 * (K + 1));
+        if (e == cudaSuccess) e = launch_wstar(p->chirp, p->n, N, rw, wmu, K, p->status, s);
+        for (int k = 0; k < K && e == cudaSuccess; ++k)
+            e = launch_split_level(k, rw, wmu, wmu, N, 2, K, p->alpha, P, p->Ym, k + 1 < K, p->status, s);
+        std::vector<uint64_t> hmu(2 * (K + 1));
+        if (e == cudaSuccess) e = cudaMemcpy(hmu.data(), wmu, sizeof(uint64_t) * hmu.size(), cudaMemcpyDeviceToHost);
+        cudaFree(rw);
+        cudaFree(wmu);
+        if (e != cudaSuccess) return fail(OZFFT_ERR_CUDA, std::string("w* split: ") + cudaGetErrorString(e));
+        std::vector<int32_t> sexp(2 * K, 0);
+        for (int v = 0; v < 2; ++v) {
+            int k = 0;
+            for (; k < K; ++k) {
+                double m;
+                std::memcpy(&m, &hmu[v * (K + 1) + k], sizeof m);
+                if (!(m > 0.0)) break;
+                if (ceil_log2_h(m) + 53 - p->alpha > 1023) return fail(OZFFT_ERR_RANGE, "w* scale");
+                sexp[v * K + k] = p->alpha - ceil_log2_h(m);
+            }
+            p->wk_host[v] = k;
+        }
+        CUDA_TRY(cudaMemcpy(p->wk, p->wk_host, sizeof(int32_t) * 2, cudaMemcpyHostToDevice));
+        CUDA_TRY(cudaMemcpy(p->wsexp, sexp.data(), sizeof(int32_t) * 2 * K, cudaMemcpyHostToDevice));
+        NttGeom gw = p->geom_fwd;
+        gw.nvec = (int64_t)2 * K * P;
+        gw.kcnt = p->wk;
+        CUDA_TRY(launch_ntt_forward(gw, p->Ym, p->tw, s));
+        uint32_t c[3] = {0, 0, 0};
+        for (int i = 0; i < P; ++i) {
+            const uint64_t pr = prime_of(i);
+            const uint64_t ninv = powmod_h((uint64_t)N % pr, pr - 2, pr);
+            c[i] = (uint32_t)mulmod_h(ninv, mulmod_h(1ull << 32, 1ull << 32, pr), pr);
+        }
+        const int64_t total = (int64_t)2 * K * P * N;
+        ymont_kernel<<<(unsigned)std::min<int64_t>((total + 255) / 256, 65535), 256, 0, s>>>(p->Ym, N, total, P, c[0],
+                                                                                           c[1], c[2]);
+        CUDA_TRY(cudaGetLastError());
+        CUDA_TRY(cudaDeviceSynchronize());
+        int st = 0;
+        CUDA_TRY(cudaMemcpy(&st, p->status, sizeof(int), cudaMemcpyDeviceToHost));
+        if (st) return fail(OZFFT_ERR_RANGE, "w* split status");
+    }
+    p->geom_fwd.nvec = B * 2 * K * P;
+    p->geom_fwd.kcnt = p->kcnt;
+    p->geom_fwd.sched = p->sched;
+    p->geom_inv.nvec = B * 4 * p->G * P;
+    p->geom_inv.kcnt = p->kcnt;
+    p->geom_inv.sched = p->sched;
+    p->launches = 1 /*premul*/ + K /*split*/ + 1 /*schedule*/ + ntt_launches(p->geom_fwd) + ntt_launches(p->geom_inv) +
+                  crt_launches();
+    return OZFFT_OK;
+}
+
+extern "C" {
+
+ozfft_plan_t ozfft_plan_ex(int64_t n, int64_t batch, int direction, const ozfft_options* opt)
+{
+    ozfft_options o{};
+    if (opt) o = *opt;
+    const int K = o.K ? o.K : 3, L = o.L ? o.L : 1, P = o.nprimes ? o.nprimes : 2;
+    if (n < 1 || batch < 1 || (direction != OZFFT_FORWARD && direction != OZFFT_INVERSE) || K < 1 || K > MAX_K ||
+        L < 1 || L > MAX_L || P < 2 || P > 3) {
+        fail(OZFFT_ERR_ARG, "ozfft_plan: argument out of range");
+        return nullptr;
+    }
+    int64_t N = o.conv_len;
+    if (N == 0) {
+        if ((n & (n - 1)) == 0) N = n;
+        else { N = 1; while (N < 2 * n - 1) N <<= 1; }
+    }
+    if (N < n || (N & (N - 1)) || N > (int64_t(1) << 24) || !(N == n || N >= 2 * n - 1)) {
+        fail(OZFFT_ERR_LENGTH, "ozfft_plan: convolution length must be a power of two <= 2^24, equal to n or >= 2n-1");
+        return nullptr;
+    }
+    const int alpha = alpha_h(n, L, P);
+    if (alpha < 1) {
+        fail(OZFFT_ERR_LENGTH, "ozfft_plan: no split width alpha >= 1 for this n, L and prime count");
+        return nullptr;
+    }
+    ozfft_plan_s* p = new ozfft_plan_s;
+    p->n = n;
+    p->N = N;
+    p->B = batch;
+    p->direction = direction;
+    p->K = K;
+    p->L = L;
+    p->P = P;
+    p->G = K * K;
+    p->alpha = alpha;
+    p->debug = o.debug;
+    if (plan_build(p) != OZFFT_OK) {
+        plan_free(p);
+        return nullptr;
+    }
+    return p;
+}
+
+ozfft_plan_t ozfft_plan(int64_t n, int64_t batch, int direction) { return ozfft_plan_ex(n, batch, direction, nullptr); }
+
+int ozfft_execute(ozfft_plan_t p, const void* in, void* out, void* stream)
+{
+    if (!p || !in || !out) return fail(OZFFT_ERR_ARG, "ozfft_execute: null argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t N = p->N, B = p->B;
+    const int K = p->K;
+    CUDA_TRY(cudaMemsetAsync(p->mu, 0, sizeof(uint64_t) * B * 2 * (K + 1), s));
+    p->cur = nullptr;
+    if (p->profiling) {
+        cudaEvent_t e0 = take_event(p);
+        if (e0) {
+            cudaEventRecord(e0, s);
+            p->pending.push_back({e0, {}});
+            p->cur = &p->pending.back();
+        }
+    }
+    CUDA_TRY(launch_premul((const double2*)in, p->chirp, p->n, N, B, p->direction == OZFFT_INVERSE, p->r, p->mu, K,
+                           p->status, s));
+    mark(p, OZFFT_PROF_PREMUL, s);
+    if (p->debug) CUDA_TRY(cudaMemcpyAsync(p->dbg_r, p->r, sizeof(double) * B * 2 * N, cudaMemcpyDeviceToDevice, s));
+    for (int k = 0; k < K; ++k) {
+        CUDA_TRY(launch_split_level(k, p->r, p->mu, p->mu, N, B * 2, K, p->alpha, p->P, p->X, k + 1 < K, p->status, s));
+        mark(p, OZFFT_PROF_SPLIT, s);
+    }
+    if (p->debug)
+        CUDA_TRY(cudaMemcpyAsync(p->dbg_X, p->X, sizeof(uint32_t) * B * 2 * K * p->P * N, cudaMemcpyDeviceToDevice, s));
+    schedule_kernel<<<(unsigned)((B * 4 + 127) / 128), 128, 0, s>>>(p->mu, B, K, p->L, p->alpha, p->wk, p->wsexp,
+                                                                     p->sched, p->kcnt);
+    CUDA_TRY(cudaGetLastError());
+    mark(p, OZFFT_PROF_SCHEDULE, s);
+    if (p->geom_fwd.m1 > 0) {
+        CUDA_TRY(launch_ntt_fwd_col(p->geom_fwd, p->X, p->tw, s));
+        mark(p, OZFFT_PROF_NTT_FWD_COL, s);
+    }
+    CUDA_TRY(launch_ntt_fwd_row(p->geom_fwd, p->X, p->tw, s));
+    mark(p, OZFFT_PROF_NTT_FWD_ROW, s);
+    CUDA_TRY(launch_ntt_inv_row(p->geom_inv, p->Z, p->twinv, MacSrc{p->X, p->Ym}, s));
+    mark(p, OZFFT_PROF_NTT_INV_ROW, s);
+    if (p->geom_inv.m1 > 0) {
+        CUDA_TRY(launch_ntt_inv_col(p->geom_inv, p->Z, p->twinv, s));
+        mark(p, OZFFT_PROF_NTT_INV_COL, s);
+    }
+    CrtArgs ca{p->Z, p->sched, p->chirp, (double2*)out, p->n, N, B, p->P, p->G, p->direction, p->status};
+    CUDA_TRY(launch_crt_post(ca, s));
+    mark(p, OZFFT_PROF_CRT, s);
+    p->cur = nullptr;
+    p->executed = true;
+    return OZFFT_OK;
+}
+
+int ozfft_set_profiling(ozfft_plan_t p, int enable)
+{
+    if (!p) return fail(OZFFT_ERR_ARG, "ozfft_set_profiling: null plan");
+    p->profiling = enable != 0;
+    return OZFFT_OK;
+}
+
+int ozfft_get_profile(ozfft_plan_t p, void* stream, ozfft_profile* out)
+{
+    if (!p || !out) return fail(OZFFT_ERR_ARG, "ozfft_get_profile: null argument");
+    std::memset(out, 0, sizeof(*out));
+    CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    for (auto& r : p->pending) {
+        cudaEvent_t prev = r.start;
+        for (auto& m : r.marks) {
+            float ms = 0.f;
+            CUDA_TRY(cudaEventSynchronize(m.second));
+            CUDA_TRY(cudaEventElapsedTime(&ms, prev, m.second));
+            out->ms[m.first] += ms;
+            out->launches[m.first] += 1;
+            prev = m.second;
+        }
+        out->executions += 1;
+        p->ev_pool.push_back(r.start);
+        for (auto& m : r.marks) p->ev_pool.push_back(m.second);
+    }
+    p->pending.clear();
+    return OZFFT_OK;
+}
+
+int ozfft_execute_host(ozfft_plan_t p, const void* in, void* out, void* stream)
+{
+    if (!p || !in || !out) return fail(OZFFT_ERR_ARG, "ozfft_execute_host: null argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t bytes = sizeof(double2) * p->n * p->B;
+    if (!p->stage_in) {
+        int rc;
+        if ((rc = dalloc(p, &p->stage_in, p->n * p->B))) return rc;
+        if ((rc = dalloc(p, &p->stage_out, p->n * p->B))) return rc;
+    }
+    CUDA_TRY(cudaMemcpyAsync(p->stage_in, in, bytes, cudaMemcpyHostToDevice, s));
+    int rc = ozfft_execute(p, p->stage_in, p->stage_out, stream);
+    if (rc) return rc;
+    CUDA_TRY(cudaMemcpyAsync(out, p->stage_out, bytes, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return OZFFT_OK;
+}
+
+int ozfft_get_status(ozfft_plan_t p, void* stream)
+{
+    if (!p) return fail(OZFFT_ERR_ARG, "ozfft_get_status: null plan");
+    cudaStream_t s = (cudaStream_t)stream;
+    int st = 0;
+    CUDA_TRY(cudaStreamSynchronize(s));
+    CUDA_TRY(cudaMemcpy(&st, p->status, sizeof(int), cudaMemcpyDeviceToHost));
+    CUDA_TRY(cudaMemset(p->status, 0, sizeof(int)));
+    if (st & ST_NONFINITE) return OZFFT_ERR_NONFINITE;
+    if (st & ST_RANGE) return OZFFT_ERR_RANGE;
+    return OZFFT_OK;
+}
+
+int ozfft_get_stats(ozfft_plan_t p, void* stream, ozfft_stats* out)
+{
+    if (!p || !out) return fail(OZFFT_ERR_ARG, "ozfft_get_stats: null argument");
+    std::memset(out, 0, sizeof(*out));
+    out->n = p->n;
+    out->N = p->N;
+    out->batch = p->B;
+    out->K = p->K;
+    out->L = p->L;
+    out->nprimes = p->P;
+    out->alpha = p->alpha;
+    out->direction = p->direction;
+    out->wstar_levels[0] = p->wk_host[0];
+    out->wstar_levels[1] = p->wk_host[1];
+    out->ntt_forward_plan = (int64_t)(p->wk_host[0] + p->wk_host[1]) * p->P;
+    out->kernel_launches = p->launches;
+    out->workspace_bytes = p->bytes;
+    if (p->executed) {
+        CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+        std::vector<int32_t> kc(p->B * 2);
+        std::vector<Sched> sc(p->B * 4);
+        CUDA_TRY(cudaMemcpy(kc.data(), p->kcnt, sizeof(int32_t) * kc.size(), cudaMemcpyDeviceToHost));
+        CUDA_TRY(cudaMemcpy(sc.data(), p->sched, sizeof(Sched) * sc.size(), cudaMemcpyDeviceToHost));
+        for (int32_t k : kc) out->ntt_forward_runtime += (int64_t)k * p->P;
+        for (const Sched& s : sc) out->ntt_inverse += (int64_t)s.ngroups * p->P;
+    }
+    return OZFFT_OK;
+}
+
+void ozfft_destroy(ozfft_plan_t p)
+{
+    if (!p) return;
+    cudaDeviceSynchronize();
+    plan_free(p);
+}
+
+const char* ozfft_error_string(int code)
+{
+    switch (code) {
+    case OZFFT_OK: return "ok";
+    case OZFFT_ERR_ARG: return "invalid argument";
+    case OZFFT_ERR_LENGTH: return "unsupported length";
+    case OZFFT_ERR_ALLOC: return "allocation failed";
+    case OZFFT_ERR_CUDA: return "CUDA runtime error";
+    case OZFFT_ERR_NONFINITE: return "non-finite input";
+    case OZFFT_ERR_RANGE: return "input magnitude out of range";
+    case OZFFT_ERR_TIMEOUT: return "device wait timed out";
+    default: return "unknown error";
+    }
+}
+
+const char* ozfft_last_error(void) { return g_last_error.c_str(); }
+
+// bit reversal of the low lg bits
+static int64_t bitrev(int64_t v, int lg)
+{
+    int64_t r = 0;
+    for (int b = 0; b < lg; ++b)
+        if (v >> b & 1) r |= int64_t(1) << (lg - 1 - b);
+    return r;
+}
+
+int64_t ozfft_debug_dump(ozfft_plan_t p, int stage, int64_t index, void* dst, void* stream)
+{
+    if (!p) return -fail(OZFFT_ERR_ARG, "ozfft_debug_dump: null plan");
+    const int64_t N = p->N, K = p->K, P = p->P, G = p->G;
+    const int64_t b = index;
+    const bool per_signal = stage != OZFFT_DUMP_CHIRP && stage != OZFFT_DUMP_YSPEC;
+    if (per_signal && (b < 0 || b >= p->B)) return -fail(OZFFT_ERR_ARG, "ozfft_debug_dump: signal index");
+    const void* src = nullptr;
+    int64_t bytes = 0;
+    bool bitrev_vectors = false;
+    switch (stage) {
+    case OZFFT_DUMP_CHIRP: src = p->chirp; bytes = 16 * p->n; break;
+    case OZFFT_DUMP_XPRIME: src = p->dbg_r ? p->dbg_r + b * 2 * N : nullptr; bytes = 8 * 2 * N; break;
+    case OZFFT_DUMP_MU: src = p->mu + b * 2 * (K + 1); bytes = 8 * 2 * (K + 1); break;
+    case OZFFT_DUMP_XRES: src = p->dbg_X ? p->dbg_X + b * 2 * K * P * N : nullptr; bytes = 4 * 2 * K * P * N; break;
+    case OZFFT_DUMP_XSPEC: src = p->X + b * 2 * K * P * N; bytes = 4 * 2 * K * P * N; bitrev_vectors = true; break;
+    case OZFFT_DUMP_YSPEC: src = p->Ym; bytes = 4 * 2 * K * P * N; bitrev_vectors = true; break;
+    case OZFFT_DUMP_SCHED: src = p->sched + b * 4; bytes = sizeof(Sched) * 4; break;
+    case OZFFT_DUMP_ZRES: src = p->Z + b * 4 * G * P * N; bytes = 4 * 4 * G * P * N; break;
+    default: return -fail(OZFFT_ERR_ARG, "ozfft_debug_dump: unknown stage");
+    }
+    if (!src) return -fail(OZFFT_ERR_ARG, "ozfft_debug_dump: stage kept only by debug plans");
+    if (!dst) return bytes;
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess ||
+        cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return -fail(OZFFT_ERR_CUDA, "ozfft_debug_dump: copy failed");
+    if (bitrev_vectors) {
+        int lg = 0;
+        while ((int64_t(1) << lg) < N) ++lg;
+        uint32_t* d = (uint32_t*)dst;
+        std::vector<uint32_t> tmp(N);
+        for (int64_t v = 0; v < bytes / 4 / N; ++v) {
+            uint32_t* vec = d + v * N;
+            for (int64_t k = 0; k < N; ++k) tmp[k] = vec[bitrev(k, lg)];
+            std::memcpy(vec, tmp.data(), 4 * N);
+        }
+    }
+    return bytes;
+}
+
+}  // extern "C"

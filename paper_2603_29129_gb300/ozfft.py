@@ -1,0 +1,211 @@
+"""ctypes binding of libozfft (include/ozfft.h).
+
+Argument marshalling only: every step of the transform runs in the library's
+CUDA kernels.  PyTorch supplies device memory and the current stream.  There is
+no CPU fallback: if libozfft.so is missing or cannot load, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libozfft.so")
+
+FORWARD, INVERSE = -1, 1
+OK, ERR_ARG, ERR_LENGTH, ERR_ALLOC, ERR_CUDA, ERR_NONFINITE, ERR_RANGE, ERR_TIMEOUT = range(8)
+DUMP_CHIRP, DUMP_XPRIME, DUMP_MU, DUMP_XRES, DUMP_XSPEC, DUMP_YSPEC, DUMP_SCHED, DUMP_ZRES = range(8)
+MAX_GROUPS, MAX_L = 64, 8
+
+# every symbol include/ozfft.h declares
+EXPORTS = ("ozfft_plan", "ozfft_plan_ex", "ozfft_execute", "ozfft_execute_host", "ozfft_get_status",
+           "ozfft_get_stats", "ozfft_set_profiling", "ozfft_get_profile", "ozfft_destroy", "ozfft_error_string",
+           "ozfft_last_error", "ozfft_debug_dump")
+PROF_SLOTS = ("premul", "split", "schedule", "ntt_fwd_col", "ntt_fwd_row", "ntt_inv_row", "ntt_inv_col", "crt")
+
+
+class Options(C.Structure):
+    _fields_ = [("K", C.c_int32), ("L", C.c_int32), ("nprimes", C.c_int32), ("conv_len", C.c_int64),
+                ("debug", C.c_int32)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("n", C.c_int64), ("N", C.c_int64), ("batch", C.c_int64),
+                ("K", C.c_int32), ("L", C.c_int32), ("nprimes", C.c_int32), ("alpha", C.c_int32),
+                ("direction", C.c_int32), ("wstar_levels", C.c_int32 * 2),
+                ("ntt_forward_runtime", C.c_int64), ("ntt_forward_plan", C.c_int64), ("ntt_inverse", C.c_int64),
+                ("kernel_launches", C.c_int64), ("workspace_bytes", C.c_int64)]
+
+
+class Profile(C.Structure):
+    _fields_ = [("executions", C.c_int64), ("launches", C.c_int64 * 8), ("ms", C.c_double * 8)]
+
+
+class OzfftError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"ozfft error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load(path: str = LIB_PATH):
+    """Load libozfft.so (raises if it is missing: build it with build.build())."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(path):
+                raise OzfftError(ERR_ARG, f"{path} not found; run paper_2603_29129_gb300.build.build()")
+            L = C.CDLL(path)
+            P, i64 = C.c_void_p, C.c_int64
+            L.ozfft_plan.restype = P; L.ozfft_plan.argtypes = [i64, i64, C.c_int]
+            L.ozfft_plan_ex.restype = P; L.ozfft_plan_ex.argtypes = [i64, i64, C.c_int, C.POINTER(Options)]
+            L.ozfft_execute.restype = C.c_int; L.ozfft_execute.argtypes = [P, P, P, P]
+            L.ozfft_execute_host.restype = C.c_int; L.ozfft_execute_host.argtypes = [P, P, P, P]
+            L.ozfft_get_status.restype = C.c_int; L.ozfft_get_status.argtypes = [P, P]
+            L.ozfft_get_stats.restype = C.c_int; L.ozfft_get_stats.argtypes = [P, P, C.POINTER(Stats)]
+            L.ozfft_set_profiling.restype = C.c_int; L.ozfft_set_profiling.argtypes = [P, C.c_int]
+            L.ozfft_get_profile.restype = C.c_int; L.ozfft_get_profile.argtypes = [P, P, C.POINTER(Profile)]
+            L.ozfft_destroy.restype = None; L.ozfft_destroy.argtypes = [P]
+            L.ozfft_error_string.restype = C.c_char_p; L.ozfft_error_string.argtypes = [C.c_int]
+            L.ozfft_last_error.restype = C.c_char_p; L.ozfft_last_error.argtypes = []
+            L.ozfft_debug_dump.restype = i64; L.ozfft_debug_dump.argtypes = [P, C.c_int, i64, P, P]
+            _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc != OK:
+        L = load()
+        raise OzfftError(rc, f"{L.ozfft_error_string(rc).decode()} ({L.ozfft_last_error().decode()})")
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+class Plan:
+    """A plan for `batch` transforms of length n (see ozfft_plan_ex)."""
+
+    def __init__(self, n, batch=1, direction=FORWARD, K=3, L=1, nprimes=2, conv_len=0, debug=False):
+        lib = load()
+        self.n, self.batch, self.direction = int(n), int(batch), int(direction)
+        self.K, self.L, self.nprimes = int(K), int(L), int(nprimes)
+        opt = Options(self.K, self.L, self.nprimes, int(conv_len), int(bool(debug)))
+        self._h = lib.ozfft_plan_ex(self.n, self.batch, self.direction, C.byref(opt))
+        if not self._h:
+            raise OzfftError(-1, lib.ozfft_last_error().decode())
+        st = self.stats()
+        self.N, self.alpha = st["N"], st["alpha"]
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h and _lib is not None:
+            _lib.ozfft_destroy(h)
+            self._h = None
+
+    close = __del__
+
+    # -- execution -------------------------------------------------------------
+    def execute(self, x, out=None, stream=None):
+        """x: contiguous CUDA complex128 tensor [batch, n] (or [n] for batch 1)."""
+        import torch
+        if x.dtype != torch.complex128 or not x.is_cuda or not x.is_contiguous():
+            raise OzfftError(ERR_ARG, "input must be a contiguous CUDA complex128 tensor")
+        if x.numel() != self.n * self.batch:
+            raise OzfftError(ERR_ARG, f"input has {x.numel()} elements, plan wants {self.n * self.batch}")
+        if out is None:
+            out = torch.empty_like(x)
+        _check(load().ozfft_execute(self._h, x.data_ptr(), out.data_ptr(), _stream_ptr(stream)))
+        return out
+
+    def execute_ptr(self, in_ptr, out_ptr, stream_ptr):
+        _check(load().ozfft_execute(self._h, in_ptr, out_ptr, stream_ptr))
+
+    def execute_host(self, x, out, stream=None):
+        """x, out: host buffers (numpy complex128 arrays or pinned CPU tensors) of batch*n elements."""
+        xp = x.ctypes.data if isinstance(x, np.ndarray) else x.data_ptr()
+        op = out.ctypes.data if isinstance(out, np.ndarray) else out.data_ptr()
+        _check(load().ozfft_execute_host(self._h, xp, op, _stream_ptr(stream)))
+        return out
+
+    def status(self, stream=None):
+        return load().ozfft_get_status(self._h, _stream_ptr(stream))
+
+    def stats(self, stream=0):
+        s = Stats()
+        _check(load().ozfft_get_stats(self._h, _stream_ptr(stream), C.byref(s)))
+        d = {name: getattr(s, name) for name, _ in Stats._fields_}
+        d["wstar_levels"] = list(s.wstar_levels)
+        return d
+
+    def set_profiling(self, enable=True):
+        _check(load().ozfft_set_profiling(self._h, int(bool(enable))))
+
+    def profile(self, stream=None):
+        """Per-kernel-slot device time summed over the executions since the last call."""
+        pr = Profile()
+        _check(load().ozfft_get_profile(self._h, _stream_ptr(stream), C.byref(pr)))
+        return {"executions": pr.executions,
+                "slots": {name: {"launches": pr.launches[i], "ms": pr.ms[i]} for i, name in enumerate(PROF_SLOTS)}}
+
+    # -- test hook -------------------------------------------------------------
+    def dump(self, stage, index=0, stream=None):
+        lib = load()
+        sp = _stream_ptr(stream)
+        nbytes = lib.ozfft_debug_dump(self._h, stage, index, None, sp)
+        if nbytes < 0:
+            _check(-nbytes)
+        buf = np.empty(nbytes, dtype=np.uint8)
+        got = lib.ozfft_debug_dump(self._h, stage, index, buf.ctypes.data, sp)
+        if got < 0:
+            _check(-got)
+        N, K, P, G = self.N, self.K, self.nprimes, self.K * self.K
+        if stage == DUMP_CHIRP:
+            return buf.view(np.complex128)
+        if stage == DUMP_XPRIME:
+            return buf.view(np.float64).reshape(2, N)
+        if stage == DUMP_MU:
+            return buf.view(np.float64).reshape(2, K + 1)
+        if stage in (DUMP_XRES, DUMP_XSPEC, DUMP_YSPEC):
+            return buf.view(np.uint32).reshape(2, K, P, N)
+        if stage == DUMP_SCHED:
+            raw = buf.view(np.int32).reshape(4, 1 + 2 * MAX_GROUPS + MAX_GROUPS * MAX_L)
+            out = []
+            for c in range(4):
+                ng = int(raw[c, 0])
+                S = raw[c, 1:1 + MAX_GROUPS]
+                sz = raw[c, 1 + MAX_GROUPS:1 + 2 * MAX_GROUPS]
+                pr = raw[c, 1 + 2 * MAX_GROUPS:].reshape(MAX_GROUPS, MAX_L)
+                out.append([(int(S[g]), [(int(v) >> 4, int(v) & 15) for v in pr[g, :sz[g]]]) for g in range(ng)])
+            return out
+        if stage == DUMP_ZRES:
+            return buf.view(np.uint32).reshape(4, G, P, N)
+        return buf
+
+
+_plans = {}
+
+
+def fft(x, direction=FORWARD, K=3, L=1, nprimes=2, stream=None):
+    """FP64-accurate DFT of the last axis of a CUDA complex128 tensor (plans cached)."""
+    shape = x.shape
+    n = shape[-1]
+    batch = x.numel() // n
+    key = (n, batch, direction, K, L, nprimes, x.device.index)
+    p = _plans.get(key)
+    if p is None:
+        p = _plans[key] = Plan(n, batch, direction, K, L, nprimes)
+    return p.execute(x.contiguous().reshape(batch, n), stream=stream).reshape(shape)
+
+
+def ifft(x, **kw):
+    return fft(x, direction=INVERSE, **kw)
