@@ -1,260 +1,347 @@
 // k_ntt.cu -- batched 32-bit NTTs (§3.3) for libozfft on sm_103a.
 //
-// Forward transforms are radix-2 decimation-in-frequency (Gentleman-Sande):
-// natural-order input, output in bit-reversed order (position bitrev(k) holds
-// X(k)).  Inverse transforms are decimation-in-time on bit-reversed input,
-// natural-order output; they run the forward stages backwards with w^-1 and
-// omit the 1/N, which the plan folds into the w~* spectra.  The pointwise
-// products of Alg. 8 are order-agnostic, so no bit reversal is ever done.
+// Forward transforms are radix-2 Cooley-Tukey on natural-order input with the
+// output in bit-reversed order (position bitrev(k) holds X(k)); inverse
+// transforms are Gentleman-Sande on bit-reversed input with natural-order
+// output and no 1/N (the plan folds N^-1 into the w~* spectra).  The pointwise
+// products of Alg. 8 do not care about the order, so nothing is ever permuted.
 //
-// A length N = 2^m transform runs in one or two passes over HBM:
-//   column pass -- global stages 0..m1-1; a CTA holds T adjacent columns
-//                  j2 of the N1 x N2 view (j = j1*N2 + j2, N1 = 2^m1), loaded
-//                  row by row (coalesced), and transforms each column over j1
-//                  with the full-length twiddles w_N^((j mod h_s) 2^s);
-//   row pass    -- global stages m1..m-1, which act inside contiguous blocks
-//                  of N2 = 2^m2 elements; a CTA holds TILE/N2 blocks.
-// Inside a pass the stages run in rounds of up to three: each thread loads
-// 2^r elements of one column from shared memory, does r radix-2 stages in
-// registers, and stores them back.
+// Twiddles are per block: at stage s (2^s blocks of 2t = N/2^s elements) every
+// butterfly of block i uses tw[2^s + i] = w^((N/2^(s+1)) * bitrev_s(i)), so a
+// stage needs 2^s table entries, contiguous in memory.  The butterflies are
+//   forward:  (a, b) -> (a + b W, a - b W)
+//   inverse:  (a, b) -> (a + b, (a - b) W^-1)
+// with residues kept canonical in [0, p) and Shoup products (oz_common.cuh).
+//
+// A length N = 2^m transform takes one or two passes over HBM:
+//   column pass -- stages 0..m1-1.  With j = j1*N2 + j2 (N1 = 2^m1, N2 = 2^m2)
+//                  these stages act on each column j2 exactly as a length-N1
+//                  transform with the same table entries, so a CTA loads T
+//                  adjacent columns (row segments, coalesced) and transforms
+//                  them in shared memory;
+//   row pass    -- stages m1..m-1 act inside contiguous rows of N2 elements;
+//                  for row r, local stage s and local block i the twiddle is
+//                  tw[((2^m1 + r) << s) + i].
+// Inside a pass, stages run in rounds of up to four: a thread loads 2^RL
+// elements of one column from shared memory, does RL stages in registers
+// (2^j contiguous twiddles at the j-th), and stores them back.
 //
 // The inverse's first pass (the row pass) builds its input on the fly:
 // Z(f) = sum over the flush group of X_s(f) * Ym_t(f) mod p (Montgomery,
-// Ym = Y * N^-1 * 2^32 mod p), i.e. the NTT-domain accumulation of Alg. 8
-// is fused into the load, and Z never goes to HBM.
+// Ym = Y * N^-1 * 2^32 mod p): the NTT-domain accumulation of Alg. 8 is fused
+// into the load, and Z never goes to HBM.
 #include "oz_common.cuh"
 #include "oz_kernels.h"
 
 namespace oz {
 
+constexpr int NTT_THREADS = 512;
+constexpr int TILE_LOG = 13;
+
 __device__ __forceinline__ int pad_idx(int i) { return i + (i >> 5); }
 
-// DIF butterfly: (a, b) -> (a + b, (a - b) w)
-__device__ __forceinline__ void bfly_dif(uint32_t& a, uint32_t& b, uint2 w, uint32_t p)
+__device__ __forceinline__ void bfly_ct(uint32_t& a, uint32_t& b, uint2 w, uint32_t p)
 {
-    uint32_t s = mod_add(a, b, p);
-    uint32_t d = a - b + p;                 // (0, 2p)
-    b = shoup(d, w.x, w.y, p);
-    a = s;
-}
-// DIT butterfly: (a, b) -> (a + b w, a - b w)
-__device__ __forceinline__ void bfly_dit(uint32_t& a, uint32_t& b, uint2 w, uint32_t p)
-{
-    uint32_t t = shoup(b, w.x, w.y, p);
+    const uint32_t t = shoup(b, w.x, w.y, p);
     b = mod_sub(a, t, p);
     a = mod_add(a, t, p);
 }
+__device__ __forceinline__ void bfly_gs(uint32_t& a, uint32_t& b, uint2 w, uint32_t p)
+{
+    const uint32_t s = mod_add(a, b, p);
+    b = shoup(a - b + p, w.x, w.y, p);
+    a = s;
+}
 
-// Twiddle source of a round: the table of prime pi is tw_all + pi * (N/2).
-// With pvar set, column c uses prime (pi0 + c) mod P (rows that are whole
-// vectors of alternating primes); otherwise every column uses pi0.
-struct TwSel {
-    const uint2* __restrict__ tw_all;
-    int64_t stride;   // N / 2
-    int pi0, P;
-    bool pvar;
-};
-
-// One round of R = 2^RL elements per thread on `cols` columns of M = 2^mloc
-// elements held in shared memory.  Stages s0 .. s0+RL-1 (local numbering).
-// Element i of column c is at sm[pad_idx(c * cstride + i * istride)].
-// Twiddle exponent of a butterfly with top element i at stage s:
-//   e = ((i mod h_s) * estride + c * ecol + ebase) << s,  h_s = M >> (s+1).
+// RL stages on v[0 .. 2^RL) in registers; the stage-j twiddles are
+// tw[(B0 << j) + q], q < 2^j (q = sub-block of the element).
 template <bool INV, int RL>
-__device__ __forceinline__ void ntt_round(uint32_t* sm, int mloc, int s0, int cols, int cstride, int istride,
-                                          int estride, int ebase, int ecol, TwSel ts, bool col_fast)
+__device__ __forceinline__ void radix_group(uint32_t (&v)[1 << RL], const uint2* __restrict__ tw, int B0, uint32_t p)
 {
     constexpr int R = 1 << RL;
-    const int lg_hlast = mloc - s0 - RL;
-    const int hlast = 1 << lg_hlast;
-    const int gpc = (1 << mloc) >> RL;   // groups per column
-    const int ngroups = gpc * cols;
-    for (int gid = threadIdx.x; gid < ngroups; gid += blockDim.x) {
-        int c, g;
-        if (col_fast) { c = gid % cols; g = gid / cols; }
-        else { g = gid & (gpc - 1); c = gid >> (mloc - RL); }
-        const int pi = ts.pvar ? (ts.pi0 + c) % ts.P : ts.pi0;
-        const uint32_t p = prime_of(pi);
-        const uint2* __restrict__ tw = ts.tw_all + pi * ts.stride;
-        const int blk = g >> lg_hlast;
-        const int low = g & (hlast - 1);
-        const int base = (blk << (mloc - s0)) + low;
-        const int a0 = c * cstride;
-        uint32_t v[R];
 #pragma unroll
-        for (int t = 0; t < R; ++t) v[t] = sm[pad_idx(a0 + (base + t * hlast) * istride)];
-        const int e0 = low * estride + ebase + c * ecol;
-        const int estep = hlast * estride;
-        if (!INV) {
-#pragma unroll
-            for (int j = 0; j < RL; ++j) {
-                const int half = R >> (j + 1);
-                const int sh = s0 + j;
-#pragma unroll
-                for (int t = 0; t < R; ++t) {
-                    if (t & half) continue;
-                    const int e = (e0 + (t & (half - 1)) * estep) << sh;
-                    bfly_dif(v[t], v[t + half], __ldg(&tw[e]), p);
-                }
-            }
+    for (int jj = 0; jj < RL; ++jj) {
+        const int j = INV ? RL - 1 - jj : jj;
+        const int half = R >> (j + 1);
+        uint2 w[1 << (RL - 1)];
+        const uint2* base = tw + (B0 << j);
+        if (j == 0) {
+            w[0] = __ldg(base);
         } else {
 #pragma unroll
-            for (int j = RL - 1; j >= 0; --j) {
-                const int half = R >> (j + 1);
-                const int sh = s0 + j;
-#pragma unroll
-                for (int t = 0; t < R; ++t) {
-                    if (t & half) continue;
-                    const int e = (e0 + (t & (half - 1)) * estep) << sh;
-                    bfly_dit(v[t], v[t + half], __ldg(&tw[e]), p);
-                }
+            for (int q = 0; q < (1 << j); q += 2) {
+                const uint4 t = __ldg(reinterpret_cast<const uint4*>(base + q));
+                w[q] = make_uint2(t.x, t.y);
+                w[q + 1] = make_uint2(t.z, t.w);
             }
         }
 #pragma unroll
-        for (int t = 0; t < R; ++t) sm[pad_idx(a0 + (base + t * hlast) * istride)] = v[t];
+        for (int u = 0; u < R; ++u) {
+            if (u & half) continue;
+            const int q = u >> (RL - j);
+            if (INV) bfly_gs(v[u], v[u + half], w[q], p);
+            else bfly_ct(v[u], v[u + half], w[q], p);
+        }
     }
 }
 
-// all stages of a pass, in rounds of 3 (DIF ascending / DIT descending)
-template <bool INV>
-__device__ void ntt_stages(uint32_t* sm, int mloc, int cols, int cstride, int istride, int estride, int ebase,
-                           int ecol, TwSel ts, bool col_fast)
+// One round: stages s0 .. s0+RL-1 of an M = 2^mloc point transform on `cols`
+// columns held in shared memory; element l of column c is at
+// sm[pad_idx((c << cshift) + (l << ishift))].  Column c's table row is
+// R0(c) = rbase + c * rstep, its prime pi0 (or (pi0 + c) mod P with pvar).
+struct RoundCfg {
+    int mloc, cols, cshift, ishift;
+    int rbase, rstep;
+    const uint2* tw_all;
+    int64_t tw_stride;
+    int pi0, P;
+    bool pvar, col_fast;
+};
+
+template <bool INV, int RL>
+__device__ __forceinline__ void ntt_round(uint32_t* sm, const RoundCfg& rc, int s0)
 {
-    const int nfull = mloc / 3, rem = mloc % 3;
-    if (!INV) {
-        for (int r = 0; r < nfull; ++r) {
-            ntt_round<false, 3>(sm, mloc, 3 * r, cols, cstride, istride, estride, ebase, ecol, ts, col_fast);
-            __syncthreads();
+    constexpr int R = 1 << RL;
+    const int lg_h = rc.mloc - s0 - RL;
+    const int h = 1 << lg_h;
+    const int lg_gpc = rc.mloc - RL;        // groups per column = 2^lg_gpc
+    const int ngroups = rc.cols << lg_gpc;
+    const int lg_cols = 31 - __clz(rc.cols);
+    for (int gid = threadIdx.x; gid < ngroups; gid += blockDim.x) {
+        int c, grp;
+        if (rc.col_fast) { c = gid & (rc.cols - 1); grp = gid >> lg_cols; }
+        else { grp = gid & ((1 << lg_gpc) - 1); c = gid >> lg_gpc; }
+        const int blk = grp >> lg_h;
+        const int low = grp & (h - 1);
+        const int base = (blk << (rc.mloc - s0)) + low;
+        const int cbase = c << rc.cshift;
+        int pi = rc.pi0;
+        if (rc.pvar) pi = (int)((unsigned)(rc.pi0 + c) % (unsigned)rc.P);
+        const uint32_t p = prime_of(pi);
+        const uint2* __restrict__ tw = rc.tw_all + pi * rc.tw_stride;
+        const int B0 = ((rc.rbase + c * rc.rstep) << s0) + blk;
+        uint32_t v[R];
+#pragma unroll
+        for (int u = 0; u < R; ++u) v[u] = sm[pad_idx(cbase + ((base + (u << lg_h)) << rc.ishift))];
+        radix_group<INV, RL>(v, tw, B0, p);
+#pragma unroll
+        for (int u = 0; u < R; ++u) sm[pad_idx(cbase + ((base + (u << lg_h)) << rc.ishift))] = v[u];
+    }
+}
+
+// all stages of a pass in rounds of at most four, sizes as equal as possible
+template <bool INV>
+__device__ void ntt_pass_stages(uint32_t* sm, const RoundCfg& rc)
+{
+    const int m = rc.mloc;
+    if (m == 0) return;
+    const int nr = (m + 3) / 4;
+    for (int rr = 0; rr < nr; ++rr) {
+        const int r = INV ? nr - 1 - rr : rr;
+        const int size = m / nr + (r < m % nr ? 1 : 0);
+        const int start = r * (m / nr) + min(r, m % nr);
+        switch (size) {
+        case 1: ntt_round<INV, 1>(sm, rc, start); break;
+        case 2: ntt_round<INV, 2>(sm, rc, start); break;
+        case 3: ntt_round<INV, 3>(sm, rc, start); break;
+        default: ntt_round<INV, 4>(sm, rc, start); break;
         }
-        if (rem == 2) ntt_round<false, 2>(sm, mloc, 3 * nfull, cols, cstride, istride, estride, ebase, ecol, ts, col_fast);
-        if (rem == 1) ntt_round<false, 1>(sm, mloc, 3 * nfull, cols, cstride, istride, estride, ebase, ecol, ts, col_fast);
-        if (rem) __syncthreads();
-    } else {
-        if (rem == 2) ntt_round<true, 2>(sm, mloc, 3 * nfull, cols, cstride, istride, estride, ebase, ecol, ts, col_fast);
-        if (rem == 1) ntt_round<true, 1>(sm, mloc, 3 * nfull, cols, cstride, istride, estride, ebase, ecol, ts, col_fast);
-        if (rem) __syncthreads();
-        for (int r = nfull - 1; r >= 0; --r) {
-            ntt_round<true, 3>(sm, mloc, 3 * r, cols, cstride, istride, estride, ebase, ecol, ts, col_fast);
-            __syncthreads();
-        }
+        __syncthreads();
     }
 }
 
 // vector activity: forward vectors [B][2][K][P] are live when k < kcnt[b][v];
 // inverse vectors [B][4][G][P] when g < ngroups of (b, conv).
-__device__ __forceinline__ bool fwd_live(const NttGeom& g, int64_t vec)
+__device__ __forceinline__ bool fwd_live(const NttGeom& g, unsigned vec)
 {
-    int64_t bv = vec / (g.P * g.K);
-    int k = (int)((vec / g.P) % g.K);
+    const unsigned bv = vec / (unsigned)(g.P * g.K);
+    const int k = (int)((vec / (unsigned)g.P) % (unsigned)g.K);
     return k < g.kcnt[bv];
 }
-__device__ __forceinline__ bool inv_live(const NttGeom& g, int64_t vec)
+__device__ __forceinline__ bool inv_live(const NttGeom& g, unsigned vec)
 {
-    int64_t bc = vec / (g.P * g.G);
-    int grp = (int)((vec / g.P) % g.G);
+    const unsigned bc = vec / (unsigned)(g.P * g.G);
+    const int grp = (int)((vec / (unsigned)g.P) % (unsigned)g.G);
     return grp < g.sched[bc].ngroups;
 }
 
 // ---------------------------------------------------------------- column pass
 template <bool INV>
-__global__ void __launch_bounds__(512) ntt_col_kernel(NttGeom g, uint32_t* __restrict__ data,
-                                                      const uint2* __restrict__ tw_all)
+__global__ void __launch_bounds__(NTT_THREADS, 2) ntt_col_kernel(NttGeom g, uint32_t* __restrict__ data,
+                                                              const uint2* __restrict__ tw_all)
 {
     extern __shared__ uint32_t sm[];
-    const int N1 = 1 << g.m1, N2 = 1 << g.m2, T = g.T;
-    const int tpv = N2 / T;
-    const int64_t vec = blockIdx.x / tpv;
-    const int col0 = (blockIdx.x % tpv) * T;
+    const int lgT = 31 - __clz(g.T);
+    const int lg_tpv = g.m2 - lgT;                     // tiles per vector = N2 / T
+    const unsigned vec = blockIdx.x >> lg_tpv;
+    const int col0 = (int)(blockIdx.x & ((1u << lg_tpv) - 1)) << lgT;
     if (INV ? !inv_live(g, vec) : !fwd_live(g, vec)) return;
-    const int pi = (int)(vec % g.P);
-    uint32_t* v = data + vec * g.N;
-    const int tile = N1 * T;
-    for (int idx = threadIdx.x; idx < tile; idx += blockDim.x) {
-        int row = idx / T, c = idx % T;
-        sm[pad_idx(idx)] = v[(int64_t)row * N2 + col0 + c];
+    const int pi = (int)(vec % (unsigned)g.P);
+    uint32_t* v = data + (int64_t)vec * g.N;
+    const int tile4 = (g.T << g.m1) >> 2;              // uint4 per tile
+    const int lgT4 = lgT - 2;
+    for (int q = threadIdx.x; q < tile4; q += blockDim.x) {
+        const int row = q >> lgT4, c = (q & ((1 << lgT4) - 1)) << 2;
+        const uint4 t = *reinterpret_cast<const uint4*>(v + ((int64_t)row << g.m2) + col0 + c);
+        const int a = (row << lgT) + c;
+        sm[pad_idx(a)] = t.x; sm[pad_idx(a + 1)] = t.y; sm[pad_idx(a + 2)] = t.z; sm[pad_idx(a + 3)] = t.w;
     }
     __syncthreads();
-    // columns c < T, element i at row i: sm[pad(i*T + c)]
-    const TwSel ts{tw_all, g.N >> 1, pi, g.P, false};
-    ntt_stages<INV>(sm, g.m1, T, 1, T, N2, col0, 1, ts, true);
-    for (int idx = threadIdx.x; idx < tile; idx += blockDim.x) {
-        int row = idx / T, c = idx % T;
-        v[(int64_t)row * N2 + col0 + c] = sm[pad_idx(idx)];
+    const RoundCfg rc{g.m1, g.T, 0, lgT, 1, 0, tw_all, g.N, pi, g.P, false, true};
+    ntt_pass_stages<INV>(sm, rc);
+    for (int q = threadIdx.x; q < tile4; q += blockDim.x) {
+        const int row = q >> lgT4, c = (q & ((1 << lgT4) - 1)) << 2;
+        const int a = (row << lgT) + c;
+        *reinterpret_cast<uint4*>(v + ((int64_t)row << g.m2) + col0 + c) =
+            make_uint4(sm[pad_idx(a)], sm[pad_idx(a + 1)], sm[pad_idx(a + 2)], sm[pad_idx(a + 3)]);
     }
 }
 
 // ------------------------------------------------------------------- row pass
-// MAC: build the inverse input from the forward spectra X and the plan's w~*
-// spectra Ym according to the flush schedule.
+// Decoded flush group of one inverse vector (for the fused MAC): X_s lives at
+// xbase + s * step and Ym_t at ybase + t * step (step = P N elements).
+struct MacVec {
+    int n;                     // products (0: empty group)
+    uint32_t st[2];            // (s, t) nibbles of up to 8 products
+    int64_t xbase, ybase, step;
+    uint32_t p, pn;
+};
+
+__device__ __forceinline__ MacVec mac_decode(const NttGeom& g, unsigned vec)
+{
+    MacVec m;
+    const int pi = (int)(vec % (unsigned)g.P);
+    const unsigned rest = vec / (unsigned)g.P;
+    const int grp = (int)(rest % (unsigned)g.G);
+    const unsigned bc = rest / (unsigned)g.G;
+    const int conv = (int)(bc & 3u);
+    const unsigned b = bc >> 2;
+    const Sched& S = g.sched[bc];
+    const int vx = (conv == 0 || conv == 3) ? 0 : 1;   // RR, RI use Re x'; II, IR use Im x'
+    const int vw = (conv == 0 || conv == 2) ? 0 : 1;   // RR, IR use Re w*; II, RI use Im w*
+    m.n = grp < S.ngroups ? S.size[grp] : 0;
+    m.st[0] = m.st[1] = 0u;
+    for (int k = 0; k < m.n; ++k) m.st[k >> 2] |= (uint32_t)(S.pair[grp][k] & 0xff) << (8 * (k & 3));
+    m.step = (int64_t)g.P * g.N;
+    m.xbase = (((int64_t)b * 2 + vx) * g.K * g.P + pi) * g.N;
+    m.ybase = ((int64_t)vw * g.K * g.P + pi) * g.N;
+    m.p = prime_of(pi);
+    m.pn = pneg_inv_of(pi);
+    return m;
+}
+
+__device__ __forceinline__ void mac_offsets(const MacVec& m, int k, int64_t& xo, int64_t& yo)
+{
+    const uint32_t pr = (m.st[k >> 2] >> (8 * (k & 3))) & 0xffu;
+    xo = m.xbase + (int64_t)(pr >> 4) * m.step;
+    yo = m.ybase + (int64_t)(pr & 15u) * m.step;
+}
+
+__device__ __forceinline__ uint4 mac_load4(const MacVec& m, const MacSrc& mac, int64_t j)
+{
+    uint32_t acc[4] = {0u, 0u, 0u, 0u};
+    for (int k = 0; k < m.n; ++k) {
+        int64_t xo, yo;
+        mac_offsets(m, k, xo, yo);
+        const uint4 x = __ldg(reinterpret_cast<const uint4*>(mac.X + xo + j));
+        const uint4 y = __ldg(reinterpret_cast<const uint4*>(mac.Ym + yo + j));
+        acc[0] = mod_add(acc[0], mont_mul(x.x, y.x, m.p, m.pn), m.p);
+        acc[1] = mod_add(acc[1], mont_mul(x.y, y.y, m.p, m.pn), m.p);
+        acc[2] = mod_add(acc[2], mont_mul(x.z, y.z, m.p, m.pn), m.p);
+        acc[3] = mod_add(acc[3], mont_mul(x.w, y.w, m.p, m.pn), m.p);
+    }
+    return make_uint4(acc[0], acc[1], acc[2], acc[3]);
+}
+
+__device__ __forceinline__ uint32_t mac_load1(const MacVec& m, const MacSrc& mac, int64_t j)
+{
+    uint32_t acc = 0u;
+    for (int k = 0; k < m.n; ++k) {
+        int64_t xo, yo;
+        mac_offsets(m, k, xo, yo);
+        acc = mod_add(acc, mont_mul(__ldg(mac.X + xo + j), __ldg(mac.Ym + yo + j), m.p, m.pn), m.p);
+    }
+    return acc;
+}
+
 template <bool INV, bool MAC>
-__global__ void __launch_bounds__(512) ntt_row_kernel(NttGeom g, uint32_t* __restrict__ data,
-                                                      const uint2* __restrict__ tw_all, MacSrc mac)
+__global__ void __launch_bounds__(NTT_THREADS, 2) ntt_row_kernel(NttGeom g, uint32_t* __restrict__ data,
+                                                              const uint2* __restrict__ tw_all, MacSrc mac)
 {
     extern __shared__ uint32_t sm[];
     const int M = 1 << g.m2;
-    const int64_t rows_total = g.nvec * (g.N >> g.m2);
+    const int lg_rpv = g.lgN - g.m2;                   // rows per vector = 2^lg_rpv
+    const int64_t rows_total = (int64_t)g.nvec << lg_rpv;
     const int rpc = g.rows_per_cta;
     const int64_t row0 = (int64_t)blockIdx.x * rpc;
     const int rows = (int)min((int64_t)rpc, rows_total - row0);
-    // skip when no row of this CTA belongs to a live vector
-    {
-        const int64_t vfirst = (row0 * M) >> g.lgN, vlast = ((row0 + rows) * M - 1) >> g.lgN;
-        bool any = false;
-        for (int64_t vv = vfirst; vv <= vlast && !any; ++vv) any = INV ? inv_live(g, vv) : fwd_live(g, vv);
-        if (!any) return;
-    }
-    const int nel = rows * M;
-    const int64_t gbase = row0 * M;
-    for (int idx = threadIdx.x; idx < nel; idx += blockDim.x) {
-        const int64_t gi = gbase + idx;
-        uint32_t val;
-        if (MAC) {
-            const int64_t vec = gi >> g.lgN;
-            const int64_t j = gi & (g.N - 1);
-            const int pi = (int)(vec % g.P);
-            const int grp = (int)((vec / g.P) % g.G);
-            const int64_t bc = vec / ((int64_t)g.P * g.G);
-            const int conv = (int)(bc & 3);
-            const int64_t b = bc >> 2;
-            const Sched& S = g.sched[bc];
-            const uint32_t p = prime_of(pi), pn = pneg_inv_of(pi);
-            const int vx = (conv == 0 || conv == 3) ? 0 : 1;   // RR, RI use Re x'; II, IR use Im x'
-            const int vw = (conv == 0 || conv == 2) ? 0 : 1;   // RR, IR use Re w*; II, RI use Im w*
-            uint32_t acc = 0;
-            if (grp < S.ngroups) {
-                const int sz = S.size[grp];
-                for (int m = 0; m < sz; ++m) {
-                    const int pr = S.pair[grp][m];
-                    const int s = pr >> 4, t = pr & 15;
-                    const uint32_t xv = mac.X[(((b * 2 + vx) * g.K + s) * g.P + pi) * g.N + j];
-                    const uint32_t yv = mac.Ym[(((int64_t)vw * g.K + t) * g.P + pi) * g.N + j];
-                    acc = mod_add(acc, mont_mul(xv, yv, p, pn), p);
+    const int nel = rows << g.m2;
+    const int64_t gbase = row0 << g.m2;
+    const bool one_vec = lg_rpv >= 31 - __clz(rpc);    // every row of the CTA in one vector
+    if (one_vec) {
+        const unsigned vec = (unsigned)(row0 >> lg_rpv);
+        if (INV ? !inv_live(g, vec) : !fwd_live(g, vec)) return;
+        const int pi = (int)(vec % (unsigned)g.P);
+        const int64_t j0 = gbase - ((int64_t)vec << g.lgN);   // offset inside the vector
+        if (nel >= 4) {
+            if (MAC) {
+                const MacVec mv = mac_decode(g, vec);
+                for (int q = threadIdx.x; q < (nel >> 2); q += blockDim.x) {
+                    const uint4 t = mac_load4(mv, mac, j0 + 4 * q);
+                    const int a = 4 * q;
+                    sm[pad_idx(a)] = t.x; sm[pad_idx(a + 1)] = t.y; sm[pad_idx(a + 2)] = t.z; sm[pad_idx(a + 3)] = t.w;
+                }
+            } else {
+                for (int q = threadIdx.x; q < (nel >> 2); q += blockDim.x) {
+                    const uint4 t = *reinterpret_cast<const uint4*>(data + gbase + 4 * q);
+                    const int a = 4 * q;
+                    sm[pad_idx(a)] = t.x; sm[pad_idx(a + 1)] = t.y; sm[pad_idx(a + 2)] = t.z; sm[pad_idx(a + 3)] = t.w;
                 }
             }
-            val = acc;
         } else {
-            val = data[gi];
+            const MacVec mv = MAC ? mac_decode(g, vec) : MacVec{};
+            for (int i = threadIdx.x; i < nel; i += blockDim.x)
+                sm[pad_idx(i)] = MAC ? mac_load1(mv, mac, j0 + i) : data[gbase + i];
         }
-        sm[pad_idx(idx)] = val;
+        __syncthreads();
+        const int rin0 = (int)(row0 & ((int64_t(1) << lg_rpv) - 1));
+        const RoundCfg rc{g.m2, rows, g.m2, 0, (1 << g.m1) + rin0, 1, tw_all, g.N, pi, g.P, false, false};
+        ntt_pass_stages<INV>(sm, rc);
+    } else {
+        // rows are whole vectors (N = M < tile): vector row0 + r, primes alternate
+        bool any = false;
+        for (int r = 0; r < rows && !any; ++r)
+            any = INV ? inv_live(g, (unsigned)(row0 + r)) : fwd_live(g, (unsigned)(row0 + r));
+        if (!any) return;
+        for (int r = 0; r < rows; ++r) {
+            const unsigned vec = (unsigned)(row0 + r);
+            if (MAC) {
+                const MacVec mv = mac_decode(g, vec);
+                for (int l = threadIdx.x; l < M; l += blockDim.x) sm[pad_idx((r << g.m2) + l)] = mac_load1(mv, mac, l);
+            } else {
+                for (int l = threadIdx.x; l < M; l += blockDim.x)
+                    sm[pad_idx((r << g.m2) + l)] = data[((int64_t)vec << g.lgN) + l];
+            }
+        }
+        __syncthreads();
+        const RoundCfg rc{g.m2, rows, g.m2, 0, 1, 0, tw_all, g.N, (int)(row0 % g.P), g.P, g.P > 1, false};
+        ntt_pass_stages<INV>(sm, rc);
     }
-    __syncthreads();
-    {
-        // each row is a column of M elements at sm[pad(r*M + i)]; rows that are
-        // whole vectors (N = M) alternate primes
-        const int64_t vec0 = gbase >> g.lgN;
-        const bool pvar = (g.N >> g.m2) < rpc && g.P > 1;
-        const TwSel ts{tw_all, g.N >> 1, (int)(vec0 % g.P), g.P, pvar};
-        ntt_stages<INV>(sm, g.m2, rows, M, 1, 1 << g.m1, 0, 0, ts, false);
+    if ((nel & 3) == 0) {
+        for (int q = threadIdx.x; q < (nel >> 2); q += blockDim.x) {
+            const int a = 4 * q;
+            *reinterpret_cast<uint4*>(data + gbase + a) =
+                make_uint4(sm[pad_idx(a)], sm[pad_idx(a + 1)], sm[pad_idx(a + 2)], sm[pad_idx(a + 3)]);
+        }
+    } else {
+        for (int i = threadIdx.x; i < nel; i += blockDim.x) data[gbase + i] = sm[pad_idx(i)];
     }
-    for (int idx = threadIdx.x; idx < nel; idx += blockDim.x) data[gbase + idx] = sm[pad_idx(idx)];
 }
 
 }  // namespace oz
 
 // --------------------------------------------------------------------- host
 namespace oz {
-
-static constexpr int TILE_LOG = 13;
 
 void ntt_configure(NttGeom& g, int64_t N)
 {
@@ -283,11 +370,10 @@ void ntt_configure(NttGeom& g, int64_t N)
 
 int64_t ntt_launches(const NttGeom& g) { return g.m1 > 0 ? 2 : 1; }
 
-static int threads_for(int64_t tile) { return tile <= (1 << TILE_LOG) ? 256 : 512; }
 static size_t smem_for(int64_t tile) { return (size_t)(tile + tile / 32) * sizeof(uint32_t); }
 
-template <typename K>
-static cudaError_t prep(K kernel, size_t smem)
+template <typename Kern>
+static cudaError_t prep(Kern kernel, size_t smem)
 {
     if (smem > 48 * 1024)
         return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -302,7 +388,7 @@ static cudaError_t launch_col(const NttGeom& g, uint32_t* data, const uint2* tw,
     cudaError_t e = prep(ntt_col_kernel<INV>, smem);
     if (e != cudaSuccess) return e;
     const int64_t grid = g.nvec * ((int64_t(1) << g.m2) / g.T);
-    ntt_col_kernel<INV><<<(unsigned)grid, threads_for(tile), smem, s>>>(g, data, tw);
+    ntt_col_kernel<INV><<<(unsigned)grid, NTT_THREADS, smem, s>>>(g, data, tw);
     return cudaGetLastError();
 }
 
@@ -315,7 +401,7 @@ static cudaError_t launch_row(const NttGeom& g, uint32_t* data, const uint2* tw,
     if (e != cudaSuccess) return e;
     const int64_t rows_total = g.nvec * (g.N >> g.m2);
     const int64_t grid = (rows_total + g.rows_per_cta - 1) / g.rows_per_cta;
-    ntt_row_kernel<INV, MAC><<<(unsigned)grid, threads_for(tile), smem, s>>>(g, data, tw, mac);
+    ntt_row_kernel<INV, MAC><<<(unsigned)grid, NTT_THREADS, smem, s>>>(g, data, tw, mac);
     return cudaGetLastError();
 }
 

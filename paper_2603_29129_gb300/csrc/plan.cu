@@ -4,7 +4,8 @@
 //
 // Device memory of a plan (B = batch, K = split cap, P = primes, G = K*K):
 //   chirp  [n] double2                         w(j) = exp(-i pi j^2/n)
-//   tw     [P][N/2] uint2, twinv likewise      (w_N^e, floor(w_N^e 2^32/p)), e < N/2
+//   tw     [P][N] uint2, twinv likewise        per-block twiddles in bit-reversed order with
+//                                              Shoup quotients (k_ntt.cu)
 //   Ym     [2][K][P][N] uint32                 w~* spectra * N^-1 * 2^32 mod p (bit-reversed order)
 //   r      [B][2][N] binary64                  x~' then the split residuals
 //   mu     [B][2][K+1] uint64                  bit patterns of ||r^(k)||_inf
@@ -248,8 +249,8 @@ static int plan_build(ozfft_plan_s* p)
     for (int i = 0; i < P; ++i)
         if ((uint32_t)(prime_of(i) * pneg_inv_of(i)) != 0xffffffffu) return fail(OZFFT_ERR_ARG, "Montgomery constant");
     if ((rc = dalloc(p, &p->chirp, p->n))) return rc;
-    if ((rc = dalloc(p, &p->tw, (size_t)P * (N / 2)))) return rc;
-    if ((rc = dalloc(p, &p->twinv, (size_t)P * (N / 2)))) return rc;
+    if ((rc = dalloc(p, &p->tw, (size_t)P * N))) return rc;
+    if ((rc = dalloc(p, &p->twinv, (size_t)P * N))) return rc;
     if ((rc = dalloc(p, &p->Ym, (size_t)2 * K * P * N))) return rc;
     if ((rc = dalloc(p, &p->wk, 2))) return rc;
     if ((rc = dalloc(p, &p->wsexp, (size_t)2 * K))) return rc;
@@ -268,25 +269,41 @@ static int plan_build(ozfft_plan_s* p)
     CUDA_TRY(cudaMemset(p->sched, 0, sizeof(Sched) * B * 4));
     CUDA_TRY(cudaMemset(p->kcnt, 0, sizeof(int32_t) * B * 2));
 
-    // twiddle tables: w_N = g^((p-1)/N), entries (w^e, floor(w^e 2^32 / p)) for e < N/2
+    // twiddle tables, one per prime and direction: w_N = g^((p-1)/N) (inverse:
+    // w_N^-1); entry 2^s + i = w^((N/2^(s+1)) bitrev_s(i)) with its Shoup
+    // quotient, for the block-i butterflies of stage s (k_ntt.cu)
     {
-        std::vector<uint2> t((size_t)P * (N / 2)), ti((size_t)P * (N / 2));
+        std::vector<uint2> t((size_t)P * N), ti((size_t)P * N);
+        std::vector<uint64_t> pw(N > 1 ? N / 2 : 1), pwi(N > 1 ? N / 2 : 1);
+        int lg = 0;
+        while ((int64_t(1) << lg) < N) ++lg;
         for (int i = 0; i < P; ++i) {
             const uint64_t pr = prime_of(i);
             const uint64_t w = powmod_h(primitive_root_h(pr), (pr - 1) / (uint64_t)N, pr);
             const uint64_t wi = powmod_h(w, pr - 2, pr);
-            uint64_t a = 1, ai = 1;
-            for (int64_t e = 0; e < N / 2; ++e) {
-                t[(size_t)i * (N / 2) + e] = make_uint2((uint32_t)a, (uint32_t)((a << 32) / pr));
-                ti[(size_t)i * (N / 2) + e] = make_uint2((uint32_t)ai, (uint32_t)((ai << 32) / pr));
-                a = mulmod_h(a, w, pr);
-                ai = mulmod_h(ai, wi, pr);
+            pw[0] = pwi[0] = 1;
+            for (int64_t e = 1; e < N / 2; ++e) {
+                pw[e] = mulmod_h(pw[e - 1], w, pr);
+                pwi[e] = mulmod_h(pwi[e - 1], wi, pr);
+            }
+            auto entry = [&](uint64_t a) { return make_uint2((uint32_t)a, (uint32_t)((a << 32) / pr)); };
+            uint2* ti_ = &ti[(size_t)i * N];
+            uint2* t_ = &t[(size_t)i * N];
+            t_[0] = ti_[0] = entry(1);
+            for (int s = 0; s < lg; ++s) {
+                const int64_t m = int64_t(1) << s;
+                for (int64_t b = 0; b < m; ++b) {
+                    int64_t r = 0;
+                    for (int k = 0; k < s; ++k)
+                        if (b >> k & 1) r |= int64_t(1) << (s - 1 - k);
+                    const int64_t e = (N / (2 * m)) * r;
+                    t_[m + b] = entry(pw[e]);
+                    ti_[m + b] = entry(pwi[e]);
+                }
             }
         }
-        if (N >= 2) {
-            CUDA_TRY(cudaMemcpy(p->tw, t.data(), sizeof(uint2) * t.size(), cudaMemcpyHostToDevice));
-            CUDA_TRY(cudaMemcpy(p->twinv, ti.data(), sizeof(uint2) * ti.size(), cudaMemcpyHostToDevice));
-        }
+        CUDA_TRY(cudaMemcpy(p->tw, t.data(), sizeof(uint2) * t.size(), cudaMemcpyHostToDevice));
+        CUDA_TRY(cudaMemcpy(p->twinv, ti.data(), sizeof(uint2) * ti.size(), cudaMemcpyHostToDevice));
     }
 
     ntt_configure(p->geom_fwd, N);
