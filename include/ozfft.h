@@ -134,6 +134,24 @@ typedef struct {
 int ozfft_set_profiling(ozfft_plan_t plan, int enable);
 int ozfft_get_profile(ozfft_plan_t plan, void* stream, ozfft_profile* out);
 
+/* Transform without any allocation (the paper has no counterpart): for
+   callers that cannot call cudaMalloc, such as code inside an application that
+   owns the whole device memory pool (a stray cudaMalloc fails or fragments it)
+   or a latency-critical path that must not enter the allocator.  Transforms
+   one signal of length n in `direction` with the default options, exactly as
+   ozfft_execute on a plan from ozfft_plan(n, 1, direction) would (bit-identical
+   output).  `in`/`out` are device pointers to n complex128 (caller-owned).
+   Every table and work buffer lives in one static device array of 4 MiB that
+   each GPU loading the library holds until the process exits; N (the
+   convolution length) must be <= 8192, i.e. n <= 8192 for powers of two and
+   n <= 4096 otherwise, else OZFFT_ERR_LENGTH.  The first call on a device, and
+   the first call after a call with another n, builds the tables of n in the
+   array and synchronizes the device: make that call before any stream capture.
+   Later calls only enqueue kernels on `stream`.  All calls share the array and
+   it keeps the last call's contents; calls that overlap on the GPU race on it.
+   Data-dependent status is recorded in the array and not reported. */
+int ozfft_execute_noalloc(int64_t n, int direction, const void* in, void* out, void* stream);
+
 /* Release every resource of the plan (synchronizes its device first). */
 void ozfft_destroy(ozfft_plan_t plan);
 

@@ -634,3 +634,198 @@ int64_t ozfft_debug_dump(ozfft_plan_t p, int stage, int64_t index, void* dst, vo
 }
 
 }  // extern "C"
+
+// ============================================================================
+// Transform without allocation: ozfft_execute_noalloc.
+//
+// Some callers cannot call cudaMalloc: code that runs inside a host
+// application which owns the device memory pool (an extra cudaMalloc there
+// fails or fragments the pool), and latency-critical paths that must not
+// block in the allocator or fail on it.  For them, this entry point runs the
+// kernels of ozfft_execute on one signal of length n with the default options
+// (K = 3, L = 1, two primes, N as ozfft_plan picks it), with every table and
+// work buffer carved out of g_noalloc_scratch, a file-scope device array of
+// NOALLOC_BYTES that each GPU which loads the library holds until the process
+// exits.  The convolution length N is limited to NOALLOC_MAX_N.
+//
+// The array's name in host code is only a host-side stand-in, never a device
+// address: the first call on a device, with that device current, asks
+// cudaGetSymbolAddress for the real address and passes that to every kernel.
+// The first call for a length n (and the first call on a device) also builds
+// the length's tables in the array and synchronizes the device, so it should
+// come before any stream capture; later calls with the same n only enqueue
+// kernels on `stream`.  All calls share the array, which keeps the last call's
+// contents: each call clears what must start at zero, and calls that overlap on
+// the GPU (two streams, or a call for another n before the previous finished)
+// race on it.
+// ============================================================================
+#include <mutex>
+
+namespace {
+constexpr int64_t NOALLOC_MAX_N = 8192;
+constexpr size_t NOALLOC_BYTES = size_t(4) << 20;
+constexpr int NOALLOC_MAX_DEVICES = 64;
+
+struct NoallocState {
+    bool have_base = false;
+    unsigned char* base = nullptr;   // device address of g_noalloc_scratch on this device
+    int64_t n = 0;                   // length the tables in the array belong to (0: none)
+    ozfft_plan_s plan;               // views into the array, never freed
+};
+NoallocState g_noalloc[NOALLOC_MAX_DEVICES];
+std::mutex g_noalloc_mutex;
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
+
+// the NTT twiddle table of one prime (same entries as plan_build's host table):
+// tw[2^s + i] = w^((N/2^(s+1)) bitrev_s(i)) with its Shoup quotient, tw[0] = 1
+__global__ void noalloc_twiddle_kernel(uint2* tw, int64_t N, uint32_t p, uint32_t w)
+{
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t e = 0;
+        if (k > 0) {
+            const int s = 63 - __clzll((long long)k);
+            const int64_t i = k - (int64_t(1) << s);
+            int64_t r = 0;
+            for (int b = 0; b < s; ++b)
+                if (i >> b & 1) r |= int64_t(1) << (s - 1 - b);
+            e = (uint64_t)((N >> (s + 1)) * r);
+        }
+        uint64_t a = 1, x = w;
+        for (; e; e >>= 1) {
+            if (e & 1) a = a * x % p;
+            x = x * x % p;
+        }
+        tw[k] = make_uint2((uint32_t)a, (uint32_t)((a << 32) / p));
+    }
+}
+
+static unsigned char* noalloc_take(unsigned char*& cur, size_t bytes)
+{
+    unsigned char* q = cur;
+    cur += (bytes + 255) & ~size_t(255);
+    return q;
+}
+
+// lay the plan's buffers out in the array and build the tables for length n
+static int noalloc_setup(NoallocState& st, int dev, int64_t n, int64_t N, int alpha)
+{
+    if (!st.have_base) {
+        void* ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess)
+            return fail(OZFFT_ERR_CUDA, std::string("ozfft_execute_noalloc: cudaGetSymbolAddress: ") +
+                                            cudaGetErrorString(e));
+        st.base = (unsigned char*)ptr;
+        st.have_base = true;
+    }
+    st.n = 0;
+    ozfft_plan_s& p = st.plan;
+    const int K = 3, P = 2, NM = (int)NOALLOC_MAX_N;
+    p.n = n; p.N = N; p.B = 1; p.K = K; p.L = 1; p.P = P; p.G = K * K; p.alpha = alpha; p.debug = 0;
+    p.device = dev; p.profiling = false; p.bytes = 0;
+    unsigned char* cur = st.base;
+    p.chirp = (double2*)noalloc_take(cur, sizeof(double2) * NM);
+    p.tw = (uint2*)noalloc_take(cur, sizeof(uint2) * P * NM);
+    p.twinv = (uint2*)noalloc_take(cur, sizeof(uint2) * P * NM);
+    p.Ym = (uint32_t*)noalloc_take(cur, sizeof(uint32_t) * 2 * K * P * NM);
+    p.wk = (int32_t*)noalloc_take(cur, sizeof(int32_t) * 2);
+    p.wsexp = (int32_t*)noalloc_take(cur, sizeof(int32_t) * 2 * K);
+    p.r = (double*)noalloc_take(cur, sizeof(double) * 2 * NM);
+    p.mu = (uint64_t*)noalloc_take(cur, sizeof(uint64_t) * 2 * (K + 1));
+    p.X = (uint32_t*)noalloc_take(cur, sizeof(uint32_t) * 2 * K * P * NM);
+    p.kcnt = (int32_t*)noalloc_take(cur, sizeof(int32_t) * 2);
+    p.sched = (Sched*)noalloc_take(cur, sizeof(Sched) * 4);
+    p.Z = (uint32_t*)noalloc_take(cur, sizeof(uint32_t) * 4 * K * K * P * NM);
+    p.status = (int*)noalloc_take(cur, sizeof(int));
+    if ((size_t)(cur - st.base) > NOALLOC_BYTES)
+        return fail(OZFFT_ERR_ALLOC, "ozfft_execute_noalloc: static workspace layout exceeds its array");
+
+    // tables: twiddles, chirp, then w~*'s split and forward NTTs (as plan_build)
+    for (int i = 0; i < P; ++i) {
+        const uint64_t pr = prime_of(i);
+        const uint64_t w = powmod_h(primitive_root_h(pr), (pr - 1) / (uint64_t)N, pr);
+        noalloc_twiddle_kernel<<<(unsigned)((N + 255) / 256), 256>>>(p.tw + (int64_t)i * N, N, (uint32_t)pr, (uint32_t)w);
+        noalloc_twiddle_kernel<<<(unsigned)((N + 255) / 256), 256>>>(p.twinv + (int64_t)i * N, N, (uint32_t)pr,
+                                                                    (uint32_t)powmod_h(w, pr - 2, pr));
+    }
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(launch_chirp(p.chirp, n, 0));
+    CUDA_TRY(cudaMemset(p.status, 0, sizeof(int)));
+    CUDA_TRY(cudaMemset(p.mu, 0, sizeof(uint64_t) * 2 * (K + 1)));
+    CUDA_TRY(launch_wstar(p.chirp, n, N, p.r, p.mu, K, p.status, 0));
+    for (int k = 0; k < K; ++k) CUDA_TRY(launch_split_level(k, p.r, p.mu, p.mu, N, 2, K, alpha, P, p.Ym, k + 1 < K, p.status, 0));
+    uint64_t hmu[2 * (MAX_K + 1)];
+    CUDA_TRY(cudaMemcpy(hmu, p.mu, sizeof(uint64_t) * 2 * (K + 1), cudaMemcpyDeviceToHost));
+    int32_t sexp[2 * MAX_K] = {0};
+    for (int v = 0; v < 2; ++v) {
+        int k = 0;
+        for (; k < K; ++k) {
+            double m;
+            std::memcpy(&m, &hmu[v * (K + 1) + k], sizeof m);
+            if (!(m > 0.0)) break;
+            sexp[v * K + k] = alpha - ceil_log2_h(m);
+        }
+        p.wk_host[v] = k;
+    }
+    CUDA_TRY(cudaMemcpy(p.wk, p.wk_host, sizeof(int32_t) * 2, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(p.wsexp, sexp, sizeof(int32_t) * 2 * K, cudaMemcpyHostToDevice));
+    ntt_configure(p.geom_fwd, N);
+    p.geom_fwd.P = P;
+    p.geom_fwd.K = K;
+    p.geom_fwd.G = p.G;
+    p.geom_inv = p.geom_fwd;
+    NttGeom gw = p.geom_fwd;
+    gw.nvec = (int64_t)2 * K * P;
+    gw.kcnt = p.wk;
+    CUDA_TRY(launch_ntt_forward(gw, p.Ym, p.tw, 0));
+    uint32_t c[3] = {0, 0, 0};
+    for (int i = 0; i < P; ++i) {
+        const uint64_t pr = prime_of(i);
+        c[i] = (uint32_t)mulmod_h(powmod_h((uint64_t)N % pr, pr - 2, pr), mulmod_h(1ull << 32, 1ull << 32, pr), pr);
+    }
+    const int64_t total = (int64_t)2 * K * P * N;
+    ymont_kernel<<<(unsigned)((total + 255) / 256), 256>>>(p.Ym, N, total, P, c[0], c[1], c[2]);
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaMemset(p.sched, 0, sizeof(Sched) * 4));
+    CUDA_TRY(cudaMemset(p.kcnt, 0, sizeof(int32_t) * 2));
+    CUDA_TRY(cudaDeviceSynchronize());
+    int stv = 0;
+    CUDA_TRY(cudaMemcpy(&stv, p.status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (stv) return fail(OZFFT_ERR_RANGE, "ozfft_execute_noalloc: w* split status");
+    p.geom_fwd.nvec = 2 * K * P;
+    p.geom_fwd.kcnt = p.kcnt;
+    p.geom_fwd.sched = p.sched;
+    p.geom_inv.nvec = 4 * p.G * P;
+    p.geom_inv.kcnt = p.kcnt;
+    p.geom_inv.sched = p.sched;
+    st.n = n;
+    return OZFFT_OK;
+}
+
+extern "C" int ozfft_execute_noalloc(int64_t n, int direction, const void* in, void* out, void* stream)
+{
+    if (!in || !out || n < 1 || (direction != OZFFT_FORWARD && direction != OZFFT_INVERSE))
+        return fail(OZFFT_ERR_ARG, "ozfft_execute_noalloc: bad argument");
+    int64_t N = n;
+    if (n & (n - 1)) { N = 1; while (N < 2 * n - 1) N <<= 1; }
+    if (N > NOALLOC_MAX_N)
+        return fail(OZFFT_ERR_LENGTH, "ozfft_execute_noalloc: convolution length " + std::to_string(N) +
+                                          " exceeds the static workspace limit " + std::to_string(NOALLOC_MAX_N) +
+                                          " (n <= 8192 for powers of two, n <= 4096 otherwise)");
+    const int alpha = alpha_h(n, 1, 2);
+    if (alpha < 1) return fail(OZFFT_ERR_LENGTH, "ozfft_execute_noalloc: no split width for this n");
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return fail(OZFFT_ERR_ARG, "ozfft_execute_noalloc: device index");
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    NoallocState& st = g_noalloc[dev];
+    if (st.n != n) {
+        const int rc = noalloc_setup(st, dev, n, N, alpha);
+        if (rc != OZFFT_OK) return rc;
+    }
+    st.plan.direction = direction;
+    CUDA_TRY(cudaMemsetAsync(st.plan.status, 0, sizeof(int), (cudaStream_t)stream));
+    return ozfft_execute(&st.plan, in, out, stream);
+}

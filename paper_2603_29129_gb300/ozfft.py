@@ -23,7 +23,7 @@ MAX_GROUPS, MAX_L = 64, 8
 # every symbol include/ozfft.h declares
 EXPORTS = ("ozfft_plan", "ozfft_plan_ex", "ozfft_execute", "ozfft_execute_host", "ozfft_get_status",
            "ozfft_get_stats", "ozfft_set_profiling", "ozfft_get_profile", "ozfft_destroy", "ozfft_error_string",
-           "ozfft_last_error", "ozfft_debug_dump")
+           "ozfft_last_error", "ozfft_debug_dump", "ozfft_execute_noalloc")
 PROF_SLOTS = ("premul", "split", "schedule", "ntt_fwd_col", "ntt_fwd_row", "ntt_inv_row", "ntt_inv_col", "crt")
 
 
@@ -75,6 +75,8 @@ def load(path: str = LIB_PATH):
             L.ozfft_error_string.restype = C.c_char_p; L.ozfft_error_string.argtypes = [C.c_int]
             L.ozfft_last_error.restype = C.c_char_p; L.ozfft_last_error.argtypes = []
             L.ozfft_debug_dump.restype = i64; L.ozfft_debug_dump.argtypes = [P, C.c_int, i64, P, P]
+            L.ozfft_execute_noalloc.restype = C.c_int
+            L.ozfft_execute_noalloc.argtypes = [i64, C.c_int, P, P, P]
             _lib = L
     return _lib
 
@@ -190,6 +192,17 @@ class Plan:
         if stage == DUMP_ZRES:
             return buf.view(np.uint32).reshape(4, G, P, N)
         return buf
+
+
+def execute_noalloc(x, out, direction=FORWARD, stream=None):
+    """One transform of a CUDA complex128 vector through ozfft_execute_noalloc,
+    which allocates no device memory (its workspace is a static device array;
+    n <= 8192 for powers of two, n <= 4096 otherwise)."""
+    import torch
+    if x.dtype != torch.complex128 or not x.is_cuda or not x.is_contiguous() or out.shape != x.shape:
+        raise OzfftError(ERR_ARG, "input and output must be contiguous CUDA complex128 tensors of one shape")
+    _check(load().ozfft_execute_noalloc(x.numel(), int(direction), x.data_ptr(), out.data_ptr(), _stream_ptr(stream)))
+    return out
 
 
 _plans = {}
