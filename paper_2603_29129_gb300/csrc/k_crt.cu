@@ -10,12 +10,14 @@
 // inverse direction conjugates and divides by n (Eq. (4)).
 //
 // The exact sums use integer arithmetic only (binary64 throughput is low on
-// this part): a thread keeps its element's sum as int64 limbs of 32-bit digits
-// in units of 2^-max(S), one limb column per thread in shared memory.  A term
-// z * 2^(max S - S_g) is split into four 32-bit digits and added to four limbs
-// without carries; one carry pass and an integer round-to-nearest-even at the
-// end produce the binary64 bit pattern.  Signals whose scales span more than
-// FAST_LIMBS limbs go to a second launch with wider columns.
+// this part).  A thread keeps its element's sum as int64 limbs, each holding a
+// sum of 32-bit digits, in units of 2^-max(S).  A term z * 2^(max S - S_g) is
+// split into 32-bit digits and added to consecutive limbs without carries; one
+// carry pass and an integer round-to-nearest-even at the end produce the
+// binary64 bit pattern.  Two-prime signals whose scales span at most
+// REG_LIMBS - 5 limbs keep the limbs in registers (crt_reg_kernel, the common
+// case); the others go to crt_wide_kernel, which keeps a wider limb column per
+// thread in shared memory.
 #include "oz_common.cuh"
 #include "oz_kernels.h"
 
@@ -145,52 +147,221 @@ __device__ double limbs_to_double(long long* acc, int stride, int nl, int unit)
     return neg ? -r : r;
 }
 
-constexpr int FAST_LIMBS = 12;
+// ---------------------------------------------------------------- fast path
+// Two-prime Garner in 32-bit arithmetic: z'_0 = z0 symmetric, the digit
+// d = ((z1 - z'_0) p0^-1) mod p1 symmetric, z' = z'_0 + d p0 (|z'| < p0 p1 / 2).
+__device__ __forceinline__ long long garner2(uint32_t z0, uint32_t z1)
+{
+    const int32_t v0 = (int32_t)(z0 > (P0 - 1) / 2 ? z0 - P0 : z0);
+    const uint32_t vm = v0 < 0 ? (uint32_t)(v0 + (int32_t)P1) : (uint32_t)v0;   // z'_0 mod p1
+    const uint32_t d = shoup(mod_sub(z1, vm, P1), c_garner.inv01, c_garner.inv01q, P1);
+    const int32_t ds = (int32_t)(d > (P1 - 1) / 2 ? d - P1 : d);
+    return (long long)v0 + (long long)ds * (long long)P0;
+}
+
+// acc[q..q+2] += digits of z * 2^b for a signed z with |z 2^b| < 2^95: two
+// unsigned low digits and a signed top digit; q is uniform across the warp, so
+// the switch selects fixed registers without divergence.
+template <int NL>
+__device__ __forceinline__ void acc_add3(long long (&acc)[NL], long long z, int sh)
+{
+    const int q = sh >> 5, b = sh & 31;
+    const unsigned long long lo = (unsigned long long)z << b;
+    const long long hi = b ? (z >> (64 - b)) : (z >> 63);   // bits 64.. of z 2^b, sign-extended
+    const long long c0 = (long long)(uint32_t)lo, c1 = (long long)(uint32_t)(lo >> 32);
+    const long long c2 = (long long)(int32_t)(uint32_t)hi;
+#define OZ_ADD3(Q)                                   \
+    case Q:                                          \
+        if (Q + 2 < NL) {                            \
+            acc[Q] += c0;                            \
+            acc[Q + 1] += c1;                        \
+            acc[Q + 2] += c2;                        \
+        }                                            \
+        break;
+    switch (q) {
+        OZ_ADD3(0) OZ_ADD3(1) OZ_ADD3(2) OZ_ADD3(3) OZ_ADD3(4) OZ_ADD3(5) OZ_ADD3(6) OZ_ADD3(7)
+    default: break;
+    }
+#undef OZ_ADD3
+}
+
+// round sum acc[l] 2^(32 l) 2^unit to the nearest binary64, ties to even
+template <int NL>
+__device__ __forceinline__ double acc_to_double(long long (&acc)[NL], int unit)
+{
+    uint32_t d[NL];
+    long long carry = 0;
+#pragma unroll
+    for (int l = 0; l < NL; ++l) {
+        const long long v = acc[l] + carry;
+        d[l] = (uint32_t)v;
+        carry = v >> 32;
+    }
+    const bool neg = (d[NL - 1] >> 31) != 0;
+    if (neg) {
+        unsigned long long c = 1;
+#pragma unroll
+        for (int l = 0; l < NL; ++l) {
+            const unsigned long long t = (unsigned long long)(uint32_t)~d[l] + c;
+            d[l] = (uint32_t)t;
+            c = t >> 32;
+        }
+    }
+    int top = -1;
+    uint32_t dt = 0, d1 = 0, d2 = 0;
+    bool low_nz = false;   // any digit below top-2
+    // scan from the top digit down (unrolled, no dynamic register indexing)
+#pragma unroll
+    for (int l = NL - 1; l >= 0; --l) {
+        if (top < 0) {
+            if (d[l]) { top = l; dt = d[l]; }
+        } else if (l == top - 1) {
+            d1 = d[l];
+        } else if (l == top - 2) {
+            d2 = d[l];
+        } else {
+            low_nz = low_nz || d[l] != 0u;
+        }
+    }
+    if (top < 0) return 0.0;
+    const int lz = __clz(dt);
+    const unsigned long long hi64 = ((unsigned long long)dt << 32) | d1;
+    const unsigned long long w = lz ? (hi64 << lz) | ((unsigned long long)d2 >> (32 - lz)) : hi64;
+    bool sticky = low_nz || (lz ? ((d2 << lz) != 0u) : (d2 != 0u));
+    const int lead = unit + 32 * top + 31 - lz;
+    const int eulp = max(lead - 52, -1074);
+    if (eulp > 971) return neg ? -__longlong_as_double(0x7ff0000000000000ll) : __longlong_as_double(0x7ff0000000000000ll);
+    const int kb = lead - eulp + 1;
+    unsigned long long qv;
+    bool rb;
+    if (kb >= 1) {
+        qv = w >> (64 - kb);
+        rb = (w >> (63 - kb)) & 1ull;
+        sticky = sticky || (w << (kb + 1)) != 0ull;
+    } else if (kb == 0) {
+        qv = 0;
+        rb = true;
+        sticky = sticky || (w << 1) != 0ull;
+    } else {
+        qv = 0;
+        rb = false;
+        sticky = true;
+    }
+    if (rb && (sticky || (qv & 1ull))) qv += 1;
+    const double r = __longlong_as_double((long long)(((unsigned long long)(eulp + 1074) << 52) + qv));
+    return neg ? -r : r;
+}
+
+constexpr int REG_LIMBS = 10;   // register accumulator: spans up to 8 limbs of shift
+
 constexpr int FAST_THREADS = 128;
 constexpr int WIDE_LIMBS = 144;
 constexpr int WIDE_THREADS = 32;
-constexpr int CRT_CHUNK = 2048;
+constexpr int CRT_CHUNK = 256;
 
 // limbs needed for a signal's scale span
 __device__ __forceinline__ int limbs_for(int smin, int smax) { return ((smax - smin) >> 5) + 5; }
 
-template <bool WIDE>
-__global__ void __launch_bounds__(WIDE ? WIDE_THREADS : FAST_THREADS) crt_post_kernel(CrtArgs a)
+__device__ __forceinline__ void load_res(const CrtArgs& a, const Sched* sc, int part, int i, int n0, int64_t b,
+                                         int64_t j, uint32_t (&z)[3], int& S, bool& negate)
+{
+    const int c = i < n0 ? 2 * part : 2 * part + 1;
+    const int g = i < n0 ? i : i - n0;
+    const uint32_t* zp = a.Z + (((b * 4 + c) * a.G + g) * a.P) * a.N + j;
+    z[0] = __ldg(zp);
+    z[1] = __ldg(zp + a.N);
+    z[2] = a.P > 2 ? __ldg(zp + 2 * a.N) : 0u;
+    S = sc[c].S[g];
+    negate = c == 1;   // II enters the real part with a minus sign
+}
+
+// signals whose exact sums fit the register accumulator (two primes, scale
+// span of at most REG_LIMBS - 5 limbs) take the register path; the rest the
+// shared-memory path
+__device__ __forceinline__ bool reg_path(const CrtArgs& a, int64_t b)
+{
+    return a.P == 2 && limbs_for(a.span[b * 3], a.span[b * 3 + 1]) <= REG_LIMBS;
+}
+
+__device__ __forceinline__ void post_store(const CrtArgs& a, int64_t b, int64_t j, double yr, double yi)
+{
+    const double2 w = a.w[j];
+    double re, im;
+    cmul(yr, yi, w.x, w.y, re, im);
+    if (a.direction == 1) {
+        im = -im;
+        re = __ddiv_rn(re, (double)a.n);
+        im = __ddiv_rn(im, (double)a.n);
+    }
+    a.out[b * a.n + j] = make_double2(re, im);
+}
+
+// register path: one output element per thread, integer-only accumulation
+__global__ void __launch_bounds__(FAST_THREADS) crt_reg_kernel(CrtArgs a)
+{
+    const int64_t chunks = (a.n + CRT_CHUNK - 1) / CRT_CHUNK;
+    const int64_t b = blockIdx.x / chunks;
+    if (!reg_path(a, b)) return;
+    const int64_t j0 = (blockIdx.x % chunks) * (int64_t)CRT_CHUNK;
+    const int64_t j1 = min(a.n, j0 + CRT_CHUNK);
+    const Sched* sc = a.sched + b * 4;
+    const int smax = a.span[b * 3 + 1], any = a.span[b * 3 + 2];
+    for (int64_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
+        double yp[2] = {0.0, 0.0};
+        if (any) {
+#pragma unroll
+            for (int part = 0; part < 2; ++part) {
+                long long acc[REG_LIMBS];
+#pragma unroll
+                for (int l = 0; l < REG_LIMBS; ++l) acc[l] = 0;
+#pragma unroll
+                for (int cc = 0; cc < 2; ++cc) {
+                    const int c = 2 * part + cc;
+                    const Sched& S = sc[c];
+                    const uint32_t* zp = a.Z + ((b * 4 + c) * a.G) * 2 * a.N + j;
+                    const int ng = S.ngroups;
+                    uint32_t z0 = 0, z1 = 0;
+                    if (ng > 0) { z0 = __ldg(zp); z1 = __ldg(zp + a.N); }
+                    for (int g = 0; g < ng; ++g) {
+                        const uint32_t c0 = z0, c1 = z1;
+                        if (g + 1 < ng) {   // prefetch the next group
+                            z0 = __ldg(zp + (int64_t)(g + 1) * 2 * a.N);
+                            z1 = __ldg(zp + (int64_t)(g + 1) * 2 * a.N + a.N);
+                        }
+                        long long z = garner2(c0, c1);
+                        if (c == 1) z = -z;   // II enters the real part with a minus sign
+                        acc_add3(acc, z, smax - S.S[g]);
+                    }
+                }
+                yp[part] = acc_to_double(acc, -smax);
+            }
+        }
+        post_store(a, b, j, yp[0], yp[1]);
+    }
+}
+
+// shared-memory path: any prime count and scale span, one limb column per thread
+__global__ void __launch_bounds__(WIDE_THREADS) crt_wide_kernel(CrtArgs a)
 {
     extern __shared__ long long acc_dyn[];
-    __shared__ long long acc_fast[WIDE ? 1 : FAST_LIMBS * FAST_THREADS];
-    __shared__ int s_info[3];
-    long long* acc = WIDE ? acc_dyn : acc_fast;
     const int chunks = (int)((a.n + CRT_CHUNK - 1) / CRT_CHUNK);
     const int64_t work = a.B * chunks;
     for (int64_t item = blockIdx.x; item < work; item += gridDim.x) {
         const int64_t b = item / chunks;
+        if (reg_path(a, b)) {   // skip the signal
+            item += ((chunks - 1 - item % chunks) / gridDim.x) * gridDim.x;
+            continue;
+        }
         const int64_t j0 = (item % chunks) * (int64_t)CRT_CHUNK;
         const int64_t j1 = min(a.n, j0 + CRT_CHUNK);
         const Sched* sc = a.sched + b * 4;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            int smin = 0, smax = 0, any = 0;
-            for (int c = 0; c < 4; ++c)
-                for (int g = 0; g < sc[c].ngroups; ++g) {
-                    const int S = sc[c].S[g];
-                    if (!any || S < smin) smin = S;
-                    if (!any || S > smax) smax = S;
-                    any = 1;
-                }
-            s_info[0] = smin;
-            s_info[1] = smax;
-            s_info[2] = any;
-        }
-        __syncthreads();
-        const int smin = s_info[0], smax = s_info[1], any = s_info[2];
+        const int smin = a.span[b * 3 + 0], smax = a.span[b * 3 + 1], any = a.span[b * 3 + 2];
         const int nl = limbs_for(smin, smax);
-        if (WIDE ? (nl <= FAST_LIMBS) : (nl > FAST_LIMBS)) continue;   // the other launch owns it
         if (nl > WIDE_LIMBS) {   // cannot happen for finite inputs that passed the split's range check
             if (threadIdx.x == 0) atomicOr(a.status, ST_RANGE);
             continue;
         }
-        long long* col = acc + threadIdx.x;
+        long long* col = acc_dyn + threadIdx.x;
         const int stride = blockDim.x;
         for (int64_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
             double yp[2] = {0.0, 0.0};
@@ -216,15 +387,7 @@ __global__ void __launch_bounds__(WIDE ? WIDE_THREADS : FAST_THREADS) crt_post_k
                     yp[part] = limbs_to_double(col, stride, nl, -smax);
                 }
             }
-            const double2 w = a.w[j];
-            double re, im;
-            cmul(yp[0], yp[1], w.x, w.y, re, im);
-            if (a.direction == 1) {
-                im = -im;
-                re = __ddiv_rn(re, (double)a.n);
-                im = __ddiv_rn(im, (double)a.n);
-            }
-            a.out[b * a.n + j] = make_double2(re, im);
+            post_store(a, b, j, yp[0], yp[1]);
         }
     }
 }
@@ -259,19 +422,19 @@ cudaError_t launch_crt_post(const CrtArgs& a, cudaStream_t s)
         s_garner_ready = true;
     }
     const int64_t chunks = (a.n + CRT_CHUNK - 1) / CRT_CHUNK;
-    crt_post_kernel<false><<<(unsigned)(a.B * chunks), FAST_THREADS, 0, s>>>(a);
+    crt_reg_kernel<<<(unsigned)(a.B * chunks), FAST_THREADS, 0, s>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    // signals with a wide scale span (rare): small blocks, one limb column per thread
+    // signals with three primes or a wide scale span: small blocks, limb columns in shared memory
     const size_t smem = sizeof(long long) * WIDE_LIMBS * WIDE_THREADS;
     static bool attr = false;
     if (!attr) {
-        e = cudaFuncSetAttribute(crt_post_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaFuncSetAttribute(crt_wide_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         attr = true;
     }
     const int64_t grid = a.B * chunks < 1024 ? a.B * chunks : 1024;
-    crt_post_kernel<true><<<(unsigned)grid, WIDE_THREADS, smem, s>>>(a);
+    crt_wide_kernel<<<(unsigned)grid, WIDE_THREADS, smem, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -8,8 +8,9 @@
 //   split_kernel   one level k of Alg. 3 on every real vector of the batch.
 //
 // Each real vector v (Re or Im of a signal) is a contiguous row r[v][0..N).
-// Its per-level maxima mu[v][k] = ||r^(k)||_inf are reduced with atomicMax on
-// the binary64 bit pattern (non-negative doubles order like their bits); a
+// Its per-level maxima mu[v][k] = ||r^(k)||_inf are reduced with integer max and
+// atomicMax on the binary64 bit pattern (non-negative doubles order like their
+// bits); a
 // kernel boundary separates level k's reduction from level k+1's use, which is
 // the grid-wide dependency Alg. 3 has between mu^(k) and sigma^(k).
 #include "oz_common.cuh"
@@ -97,25 +98,27 @@ __global__ void chirp_kernel(double2* w, int64_t n)
     }
 }
 
-// ------------------------------------------------------------- reductions
-__device__ __forceinline__ void block_max_to(uint64_t* dst, double v)
-{
-    __shared__ double red[32];
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0) red[wid] = v;
-    __syncthreads();
-    if (wid == 0) {
-        const int nw = (blockDim.x + 31) >> 5;
-        v = lane < nw ? red[lane] : 0.0;
-        for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-        if (lane == 0 && v > 0.0) atomicMax((unsigned long long*)dst, (unsigned long long)__double_as_longlong(v));
-    }
-}
-
 // chunking: a CTA works on CHUNK consecutive elements of one vector
 constexpr int SPLIT_THREADS = 256;
 constexpr int CHUNK = 4096;
+
+__device__ __forceinline__ uint64_t umax64(uint64_t a, uint64_t b) { return a > b ? a : b; }
+
+// block-wide max of non-negative binary64 bit patterns, then atomicMax into *dst
+__device__ __forceinline__ void block_umax_to(uint64_t* dst, uint64_t v)
+{
+    __shared__ uint64_t redu[32];
+    for (int o = 16; o > 0; o >>= 1) v = umax64(v, (uint64_t)__shfl_xor_sync(0xffffffffu, (unsigned long long)v, o));
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) redu[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        v = lane < nw ? redu[lane] : 0ull;
+        for (int o = 16; o > 0; o >>= 1) v = umax64(v, (uint64_t)__shfl_xor_sync(0xffffffffu, (unsigned long long)v, o));
+        if (lane == 0 && v) atomicMax((unsigned long long*)dst, (unsigned long long)v);
+    }
+}
 
 __global__ void __launch_bounds__(SPLIT_THREADS) wstar_kernel(const double2* __restrict__ w, int64_t n, int64_t N,
                                                               double* __restrict__ r, uint64_t* __restrict__ mu, int K)
@@ -124,7 +127,7 @@ __global__ void __launch_bounds__(SPLIT_THREADS) wstar_kernel(const double2* __r
     const int v = (int)(blockIdx.x / chunks);
     const int64_t j0 = (blockIdx.x % chunks) * CHUNK;
     const int64_t j1 = min(N, j0 + CHUNK);
-    double m = 0.0;
+    uint64_t m = 0;
     for (int64_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
         int64_t src = -1;
         if (j < n) src = j;
@@ -135,9 +138,9 @@ __global__ void __launch_bounds__(SPLIT_THREADS) wstar_kernel(const double2* __r
             val = v == 0 ? ws.x : -ws.y;   // conj(w)
         }
         r[(int64_t)v * N + j] = val;
-        m = fmax(m, fabs(val));
+        m = umax64(m, (uint64_t)__double_as_longlong(val) & 0x7fffffffffffffffull);
     }
-    block_max_to(&mu[(int64_t)v * (K + 1) + 0], m);
+    block_umax_to(&mu[(int64_t)v * (K + 1) + 0], m);
 }
 
 __global__ void __launch_bounds__(SPLIT_THREADS) premul_kernel(const double2* __restrict__ x,
@@ -149,7 +152,7 @@ __global__ void __launch_bounds__(SPLIT_THREADS) premul_kernel(const double2* __
     const int64_t b = blockIdx.x / chunks;
     const int64_t j0 = (blockIdx.x % chunks) * CHUNK;
     const int64_t j1 = min(N, j0 + CHUNK);
-    double mr = 0.0, mi = 0.0;
+    uint64_t mr = 0, mi = 0;   // bit patterns of |.|: non-negative doubles order like their bits
     bool bad = false;
     double* rr = r + (2 * b) * N;
     double* ri = rr + N;
@@ -164,18 +167,68 @@ __global__ void __launch_bounds__(SPLIT_THREADS) premul_kernel(const double2* __
         }
         rr[j] = re;
         ri[j] = im;
-        mr = fmax(mr, fabs(re));
-        mi = fmax(mi, fabs(im));
+        mr = umax64(mr, (uint64_t)__double_as_longlong(re) & 0x7fffffffffffffffull);
+        mi = umax64(mi, (uint64_t)__double_as_longlong(im) & 0x7fffffffffffffffull);
     }
     if (bad) atomicOr(status, ST_NONFINITE);
-    block_max_to(&mu[(2 * b) * (K + 1)], mr);
+    block_umax_to(&mu[(2 * b) * (K + 1)], mr);
     __syncthreads();
-    block_max_to(&mu[(2 * b + 1) * (K + 1)], mi);
+    block_umax_to(&mu[(2 * b + 1) * (K + 1)], mi);
 }
 
-// Level k of Alg. 3 for every vector: sigma = 2^(ceil(log2 mu_k) + rho),
-// slice = (r + sigma) - sigma, r <- r - slice, q = slice * 2^(alpha - e)
-// (an integer with |q| <= 2^alpha), residues q mod p written per prime.
+// One level of Alg. 3 on one element, from its bit pattern, in integer
+// arithmetic only (binary64 throughput is low on this part).  With
+// sigma = 2^(e + rho), |r| <= 2^e and rho >= 1, r + sigma stays in the binade
+// [sigma, 2 sigma) for r >= 0 and [sigma/2, sigma) for r < 0, whose spacing is
+// 2^g with g = e + rho - 52 (resp. - 53), never below 2^-1074.  Hence
+//   s = fl(fl(r + sigma) - sigma) = 2^g * round_half_even(r / 2^g),
+// the residual r - s is exact, and q = s / 2^(e - alpha) = s * 2^(alpha - e).
+// "Even" is the parity of round(r / 2^g) because sigma / 2^g is even.
+__device__ __forceinline__ void split_level_int(uint64_t rb, int e, int alpha, long long& q, uint64_t& rnb)
+{
+    const int rho = 53 - alpha;
+    const bool neg = (rb >> 63) != 0;
+    const int Eb = (int)((rb >> 52) & 0x7ff);
+    uint64_t m = rb & ((1ull << 52) - 1);
+    if (Eb == 0 && m == 0) { q = 0; rnb = rb; return; }
+    int E = -1074;
+    if (Eb) { m |= 1ull << 52; E = Eb - 1075; }          // r = +-m 2^E
+    const int g = max(neg ? e + rho - 53 : e + rho - 52, -1074);
+    uint64_t k;
+    long long d;                                           // residual in units 2^E
+    if (g <= E) {
+        k = m << (E - g);
+        d = 0;
+    } else {
+        const int sh = g - E;
+        if (sh >= 64) {
+            k = 0;
+            d = (long long)m;
+        } else {
+            k = m >> sh;
+            const uint64_t rem = m & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+            if (rem > half || (rem == half && (k & 1))) ++k;
+            d = (long long)m - (long long)(k << sh);
+        }
+    }
+    q = (long long)(k << (g - (e - alpha)));
+    if (neg) { q = -q; d = -d; }
+    if (d == 0) { rnb = 0; return; }                      // r - s == 0 is +0
+    const uint64_t a = (uint64_t)(d < 0 ? -d : d);
+    const int pb = 63 - __clzll((long long)a);            // leading bit of |d|
+    uint64_t bits;
+    if (E + pb >= -1022) {
+        const uint64_t mant = pb <= 52 ? (a << (52 - pb)) : (a >> (pb - 52));
+        bits = ((uint64_t)(E + pb + 1023) << 52) | (mant & ((1ull << 52) - 1));
+    } else {
+        bits = a << (E + 1074);                            // subnormal
+    }
+    rnb = bits | (d < 0 ? (1ull << 63) : 0ull);
+}
+
+// Level k of Alg. 3 for every vector: q = s 2^(alpha - e) with |q| <= 2^alpha,
+// residues q mod p written per prime, the residual written back for the next
+// level and its maximum reduced into mu[v][k+1].
 __global__ void __launch_bounds__(SPLIT_THREADS) split_kernel(int k, double* __restrict__ r,
                                                               uint64_t* __restrict__ mu, int64_t N, int K,
                                                               int alpha, int P, uint32_t* __restrict__ X,
@@ -185,27 +238,20 @@ __global__ void __launch_bounds__(SPLIT_THREADS) split_kernel(int k, double* __r
     const int64_t v = blockIdx.x / chunks;
     const int64_t j0 = (blockIdx.x % chunks) * CHUNK;
     const int64_t j1 = min(N, j0 + CHUNK);
-    const double muk = __longlong_as_double((long long)mu[v * (K + 1) + k]);
-    if (!(muk > 0.0)) return;                       // level empty: mu^(k) = 0 ends the split
-    const int rho = 53 - alpha;
-    const int e = ceil_log2_pos(muk);
-    if (e + rho > 1023) {
+    const uint64_t mub = mu[v * (K + 1) + k];
+    if (mub == 0) return;                                 // level empty: mu^(k) = 0 ends the split
+    const int e = ceil_log2_pos(__longlong_as_double((long long)mub));
+    if (e + 53 - alpha > 1023) {
         if (threadIdx.x == 0) atomicOr(status, ST_RANGE);
         return;
     }
-    const double sigma = ldexp(1.0, e + rho);
-    int sh = alpha - e;                             // q = s * 2^sh, done as exact power-of-two products
-    double pre = 1.0;
-    if (sh > 1000) { pre = ldexp(1.0, 1000); sh -= 1000; }
-    const double scale = ldexp(1.0, sh);
-    double* rv = r + v * N;
+    uint64_t* rv = reinterpret_cast<uint64_t*>(r + v * N);
     uint32_t* xk = X + ((v * K + k) * P) * N;
-    double m = 0.0;
+    uint64_t m = 0;
     for (int64_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
-        const double x = rv[j];
-        const double s = __dsub_rn(__dadd_rn(x, sigma), sigma);
-        const double rn = __dsub_rn(x, s);
-        const long long q = __double2ll_rn(__dmul_rn(__dmul_rn(s, pre), scale));
+        long long q;
+        uint64_t rn;
+        split_level_int(rv[j], e, alpha, q, rn);
 #pragma unroll
         for (int pi = 0; pi < MAX_PRIMES; ++pi) {
             if (pi >= P) break;
@@ -215,9 +261,9 @@ __global__ void __launch_bounds__(SPLIT_THREADS) split_kernel(int k, double* __r
             xk[pi * N + j] = (uint32_t)a;
         }
         if (write_r) rv[j] = rn;
-        m = fmax(m, fabs(rn));
+        m = umax64(m, rn & 0x7fffffffffffffffull);
     }
-    if (k + 1 <= K) block_max_to(&mu[v * (K + 1) + k + 1], m);
+    if (k + 1 <= K) block_umax_to(&mu[v * (K + 1) + k + 1], m);
 }
 
 // ------------------------------------------------------------------ launchers

@@ -1,0 +1,404 @@
+// ntt_impl.cuh -- batched 32-bit NTTs (§3.3) for libozfft on sm_103a.
+//
+// Forward transforms are radix-2 Cooley-Tukey on natural-order input with the
+// output in bit-reversed order (position bitrev(k) holds X(k)); inverse
+// transforms are Gentleman-Sande on bit-reversed input with natural-order
+// output and no 1/N (the plan folds N^-1 into the w~* spectra).  The pointwise
+// products of Alg. 8 do not care about the order, so nothing is ever permuted.
+//
+// Twiddles are per block: at stage s (2^s blocks of 2t = N/2^s elements) every
+// butterfly of block i uses tw[2^s + i] = w^((N/2^(s+1)) * bitrev_s(i)), so a
+// stage needs 2^s table entries, contiguous in memory.  The butterflies are
+//   forward:  (a, b) -> (a + b W, a - b W)
+//   inverse:  (a, b) -> (a + b, (a - b) W^-1)
+// with residues kept canonical in [0, p) and Shoup products (oz_common.cuh).
+//
+// A length N = 2^m transform takes one or two passes over HBM:
+//   column pass -- stages 0..m1-1.  With j = j1*N2 + j2 (N1 = 2^m1, N2 = 2^m2)
+//                  these stages act on each column j2 exactly as a length-N1
+//                  transform with the same table entries, so a CTA loads T
+//                  adjacent columns (row segments, coalesced) and transforms
+//                  them in shared memory;
+//   row pass    -- stages m1..m-1 act inside contiguous rows of N2 elements;
+//                  for row r, local stage s and local block i the twiddle is
+//                  tw[((2^m1 + r) << s) + i].
+// Inside a pass the stages run in rounds of up to four: a thread loads 2^RL
+// elements of one column from shared memory, does RL stages in registers
+// (2^j contiguous twiddles at the j-th), and stores them back.  The kernels are
+// instantiated per local transform size, so every shared-memory address of a
+// group is its base plus a compile-time offset: with one pad word per 32,
+// element u of a group with stride S sits at pad(base) + u*S + floor(u*S/32).
+//
+// The inverse's first pass (the row pass) builds its input on the fly:
+// Z(f) = sum over the flush group of X_s(f) * Ym_t(f) mod p (Montgomery,
+// Ym = Y * N^-1 * 2^32 mod p): the NTT-domain accumulation of Alg. 8 is fused
+// into the load, and Z never goes to HBM.
+#pragma once
+#include "oz_common.cuh"
+#include "oz_kernels.h"
+
+namespace oz {
+
+constexpr int NTT_THREADS = 512;
+constexpr int TILE_LOG = 13;
+
+__device__ __forceinline__ int pad_idx(int i) { return i + (i >> 5); }
+
+__device__ __forceinline__ void bfly_ct(uint32_t& a, uint32_t& b, uint2 w, uint32_t p)
+{
+    const uint32_t t = shoup(b, w.x, w.y, p);
+    b = mod_sub(a, t, p);
+    a = mod_add(a, t, p);
+}
+__device__ __forceinline__ void bfly_gs(uint32_t& a, uint32_t& b, uint2 w, uint32_t p)
+{
+    const uint32_t s = mod_add(a, b, p);
+    b = shoup(a - b + p, w.x, w.y, p);
+    a = s;
+}
+
+// RL stages on v[0 .. 2^RL) in registers; the stage-j twiddles are
+// tw[(B0 << j) + q], q < 2^j (q = sub-block of the element).
+template <bool INV, int RL>
+__device__ __forceinline__ void radix_group(uint32_t (&v)[1 << RL], const uint2* __restrict__ tw, int B0, uint32_t p)
+{
+    constexpr int R = 1 << RL;
+#pragma unroll
+    for (int jj = 0; jj < RL; ++jj) {
+        const int j = INV ? RL - 1 - jj : jj;
+        const int half = R >> (j + 1);
+        uint2 w[1 << (RL - 1)];
+        const uint2* base = tw + (B0 << j);
+        if (j == 0) {
+            w[0] = __ldg(base);
+        } else {
+#pragma unroll
+            for (int q = 0; q < (1 << j); q += 2) {
+                const uint4 t = __ldg(reinterpret_cast<const uint4*>(base + q));
+                w[q] = make_uint2(t.x, t.y);
+                w[q + 1] = make_uint2(t.z, t.w);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < R; ++u) {
+            if (u & half) continue;
+            const int q = u >> (RL - j);
+            if (INV) bfly_gs(v[u], v[u + half], w[q], p);
+            else bfly_ct(v[u], v[u + half], w[q], p);
+        }
+    }
+}
+
+// load, transform and store one group whose elements are S words apart
+template <bool INV, int RL, int S>
+__device__ __forceinline__ void group_bfly(uint32_t* smp, const uint2* __restrict__ tw, int B0, uint32_t p)
+{
+    constexpr int R = 1 << RL;
+    uint32_t v[R];
+#pragma unroll
+    for (int u = 0; u < R; ++u) v[u] = smp[u * S + (u * S) / 32];
+    radix_group<INV, RL>(v, tw, B0, p);
+#pragma unroll
+    for (int u = 0; u < R; ++u) smp[u * S + (u * S) / 32] = v[u];
+}
+
+// round partition of an M = 2^ML point pass: ceil(ML/4) rounds, sizes equal
+// up to one, the larger rounds last (fewer bank conflicts, e.g. 3,3,3,4 for 13)
+template <int ML>
+struct Part {
+    static constexpr int NR = (ML + 3) / 4;
+    static constexpr int EXTRA = NR ? ML % NR : 0;
+    static constexpr int size(int r) { return ML / NR + (r >= NR - EXTRA ? 1 : 0); }
+    static constexpr int start(int r) { return r * (ML / NR) + (r > NR - EXTRA ? r - (NR - EXTRA) : 0); }
+};
+
+// runtime facts of a pass: number of columns (rows of a row pass), table row
+// of column c = rbase + c * rstep, prime of column c = pi0 or (pi0 + c) mod P
+struct PassArgs {
+    int cols, rbase, rstep;
+    const uint2* tw_all;
+    int64_t tw_stride;
+    int pi0, P;
+    bool pvar;
+};
+
+__device__ __forceinline__ const uint2* table_of(const PassArgs& a, int c, uint32_t& p)
+{
+    int pi = a.pi0;
+    if (a.pvar) pi = (int)((unsigned)(a.pi0 + c) % (unsigned)a.P);
+    p = prime_of(pi);
+    return a.tw_all + pi * a.tw_stride;
+}
+
+// row pass round: element l of row c at sm[pad((c << ML) + l)]
+template <bool INV, int ML, int S0, int RL>
+__device__ __forceinline__ void row_round(uint32_t* sm, const PassArgs& a)
+{
+    constexpr int LOG_H = ML - S0 - RL, H = 1 << LOG_H, LOG_GPC = ML - RL;
+    const int ngroups = a.cols << LOG_GPC;
+    for (int gid = threadIdx.x; gid < ngroups; gid += blockDim.x) {
+        const int grp = gid & ((1 << LOG_GPC) - 1);
+        const int c = gid >> LOG_GPC;
+        const int blk = grp >> LOG_H;
+        const int base = (c << ML) + (blk << (ML - S0)) + (grp & (H - 1));
+        uint32_t p;
+        const uint2* tw = table_of(a, c, p);
+        group_bfly<INV, RL, H>(sm + pad_idx(base), tw, ((a.rbase + c * a.rstep) << S0) + blk, p);
+    }
+}
+
+// column pass round: element l of column c at sm[pad((l << LOG_T) + c)]
+template <bool INV, int ML, int S0, int RL, int LOG_T>
+__device__ __forceinline__ void col_round(uint32_t* sm, const PassArgs& a)
+{
+    constexpr int LOG_H = ML - S0 - RL, H = 1 << LOG_H, LOG_GPC = ML - RL;
+    constexpr int T = 1 << LOG_T;
+    for (int gid = threadIdx.x; gid < (T << LOG_GPC); gid += blockDim.x) {
+        const int c = gid & (T - 1);
+        const int grp = gid >> LOG_T;
+        const int blk = grp >> LOG_H;
+        const int l0 = (blk << (ML - S0)) + (grp & (H - 1));
+        uint32_t p;
+        const uint2* tw = table_of(a, 0, p);
+        group_bfly<INV, RL, H * T>(sm + pad_idx((l0 << LOG_T) + c), tw, (1 << S0) + blk, p);
+    }
+}
+
+template <bool INV, bool COL, int ML, int LOG_T, int I>
+__device__ __forceinline__ void run_rounds(uint32_t* sm, const PassArgs& a)
+{
+    if constexpr (I < Part<ML>::NR) {
+        constexpr int R_ = INV ? Part<ML>::NR - 1 - I : I;
+        constexpr int S0 = Part<ML>::start(R_), RL = Part<ML>::size(R_);
+        if constexpr (COL) col_round<INV, ML, S0, RL, LOG_T>(sm, a);
+        else row_round<INV, ML, S0, RL>(sm, a);
+        __syncthreads();
+        run_rounds<INV, COL, ML, LOG_T, I + 1>(sm, a);
+    }
+}
+
+// vector activity: forward vectors [B][2][K][P] are live when k < kcnt[b][v];
+// inverse vectors [B][4][G][P] when g < ngroups of (b, conv).
+__device__ __forceinline__ bool fwd_live(const NttGeom& g, unsigned vec)
+{
+    const unsigned bv = vec / (unsigned)(g.P * g.K);
+    const int k = (int)((vec / (unsigned)g.P) % (unsigned)g.K);
+    return k < g.kcnt[bv];
+}
+__device__ __forceinline__ bool inv_live(const NttGeom& g, unsigned vec)
+{
+    const unsigned bc = vec / (unsigned)(g.P * g.G);
+    const int grp = (int)((vec / (unsigned)g.P) % (unsigned)g.G);
+    return grp < g.sched[bc].ngroups;
+}
+
+constexpr int col_log_t(int m1) { return (TILE_LOG - m1) > 5 ? (TILE_LOG - m1) : 5; }
+
+// ---------------------------------------------------------------- column pass
+template <bool INV, int M1>
+__global__ void __launch_bounds__(NTT_THREADS, 2) ntt_col_kernel(NttGeom g, uint32_t* __restrict__ data,
+                                                                 const uint2* __restrict__ tw_all)
+{
+    extern __shared__ uint32_t sm[];
+    constexpr int LOG_T = col_log_t(M1), T = 1 << LOG_T;
+    const int lg_tpv = g.m2 - LOG_T;                   // tiles per vector = N2 / T
+    const unsigned vec = blockIdx.x >> lg_tpv;
+    const int col0 = (int)(blockIdx.x & ((1u << lg_tpv) - 1)) << LOG_T;
+    if (INV ? !inv_live(g, vec) : !fwd_live(g, vec)) return;
+    const int pi = (int)(vec % (unsigned)g.P);
+    uint32_t* v = data + (int64_t)vec * g.N + col0;
+    constexpr int TILE4 = (T << M1) >> 2;
+    for (int q = threadIdx.x; q < TILE4; q += blockDim.x) {
+        const int row = q >> (LOG_T - 2), c = (q & ((T >> 2) - 1)) << 2;
+        const uint4 t = *reinterpret_cast<const uint4*>(v + ((int64_t)row << g.m2) + c);
+        uint32_t* s = sm + pad_idx((row << LOG_T) + c);
+        s[0] = t.x; s[1] = t.y; s[2] = t.z; s[3] = t.w;
+    }
+    __syncthreads();
+    const PassArgs a{T, 1, 0, tw_all, g.N, pi, g.P, false};
+    run_rounds<INV, true, M1, LOG_T, 0>(sm, a);
+    for (int q = threadIdx.x; q < TILE4; q += blockDim.x) {
+        const int row = q >> (LOG_T - 2), c = (q & ((T >> 2) - 1)) << 2;
+        const uint32_t* s = sm + pad_idx((row << LOG_T) + c);
+        *reinterpret_cast<uint4*>(v + ((int64_t)row << g.m2) + c) = make_uint4(s[0], s[1], s[2], s[3]);
+    }
+}
+
+// ------------------------------------------------------------------- row pass
+// Decoded flush group of one inverse vector (for the fused MAC): X_s lives at
+// xbase + s * step and Ym_t at ybase + t * step (step = P N elements).
+struct MacVec {
+    int n;                     // products (0: empty group)
+    uint32_t st[2];            // (s, t) nibbles of up to 8 products
+    int64_t xbase, ybase, step;
+    uint32_t p, pn;
+};
+
+__device__ __forceinline__ MacVec mac_decode(const NttGeom& g, unsigned vec)
+{
+    MacVec m;
+    const int pi = (int)(vec % (unsigned)g.P);
+    const unsigned rest = vec / (unsigned)g.P;
+    const int grp = (int)(rest % (unsigned)g.G);
+    const unsigned bc = rest / (unsigned)g.G;
+    const int conv = (int)(bc & 3u);
+    const unsigned b = bc >> 2;
+    const Sched& S = g.sched[bc];
+    const int vx = (conv == 0 || conv == 3) ? 0 : 1;   // RR, RI use Re x'; II, IR use Im x'
+    const int vw = (conv == 0 || conv == 2) ? 0 : 1;   // RR, IR use Re w*; II, RI use Im w*
+    m.n = grp < S.ngroups ? S.size[grp] : 0;
+    m.st[0] = m.st[1] = 0u;
+    for (int k = 0; k < m.n; ++k) m.st[k >> 2] |= (uint32_t)(S.pair[grp][k] & 0xff) << (8 * (k & 3));
+    m.step = (int64_t)g.P * g.N;
+    m.xbase = (((int64_t)b * 2 + vx) * g.K * g.P + pi) * g.N;
+    m.ybase = ((int64_t)vw * g.K * g.P + pi) * g.N;
+    m.p = prime_of(pi);
+    m.pn = pneg_inv_of(pi);
+    return m;
+}
+
+__device__ __forceinline__ void mac_offsets(const MacVec& m, int k, int64_t& xo, int64_t& yo)
+{
+    const uint32_t pr = (m.st[k >> 2] >> (8 * (k & 3))) & 0xffu;
+    xo = m.xbase + (int64_t)(pr >> 4) * m.step;
+    yo = m.ybase + (int64_t)(pr & 15u) * m.step;
+}
+
+__device__ __forceinline__ uint4 mac_load4(const MacVec& m, const MacSrc& mac, int64_t j)
+{
+    uint32_t acc[4] = {0u, 0u, 0u, 0u};
+    for (int k = 0; k < m.n; ++k) {
+        int64_t xo, yo;
+        mac_offsets(m, k, xo, yo);
+        const uint4 x = __ldg(reinterpret_cast<const uint4*>(mac.X + xo + j));
+        const uint4 y = __ldg(reinterpret_cast<const uint4*>(mac.Ym + yo + j));
+        acc[0] = mod_add(acc[0], mont_mul(x.x, y.x, m.p, m.pn), m.p);
+        acc[1] = mod_add(acc[1], mont_mul(x.y, y.y, m.p, m.pn), m.p);
+        acc[2] = mod_add(acc[2], mont_mul(x.z, y.z, m.p, m.pn), m.p);
+        acc[3] = mod_add(acc[3], mont_mul(x.w, y.w, m.p, m.pn), m.p);
+    }
+    return make_uint4(acc[0], acc[1], acc[2], acc[3]);
+}
+
+__device__ __forceinline__ uint32_t mac_load1(const MacVec& m, const MacSrc& mac, int64_t j)
+{
+    uint32_t acc = 0u;
+    for (int k = 0; k < m.n; ++k) {
+        int64_t xo, yo;
+        mac_offsets(m, k, xo, yo);
+        acc = mod_add(acc, mont_mul(__ldg(mac.X + xo + j), __ldg(mac.Ym + yo + j), m.p, m.pn), m.p);
+    }
+    return acc;
+}
+
+template <bool INV, bool MAC, int M2>
+__global__ void __launch_bounds__(NTT_THREADS, 2) ntt_row_kernel(NttGeom g, uint32_t* __restrict__ data,
+                                                                 const uint2* __restrict__ tw_all, MacSrc mac)
+{
+    extern __shared__ uint32_t sm[];
+    constexpr int M = 1 << M2;
+    constexpr int RPC = M2 <= TILE_LOG ? (1 << (TILE_LOG - M2)) : 1;   // rows per CTA
+    const int lg_rpv = g.lgN - M2;                     // rows per vector = 2^lg_rpv
+    const int64_t rows_total = (int64_t)g.nvec << lg_rpv;
+    const int64_t row0 = (int64_t)blockIdx.x * RPC;
+    const int rows = (int)min((int64_t)RPC, rows_total - row0);
+    const int nel = rows << M2;
+    const int64_t gbase = row0 << M2;
+    if ((1 << lg_rpv) >= RPC) {
+        // every row of the CTA belongs to one vector
+        const unsigned vec = (unsigned)(row0 >> lg_rpv);
+        if (INV ? !inv_live(g, vec) : !fwd_live(g, vec)) return;
+        const int pi = (int)(vec % (unsigned)g.P);
+        const int64_t j0 = gbase - ((int64_t)vec << g.lgN);   // offset inside the vector
+        if (nel >= 4) {
+            if (MAC) {
+                const MacVec mv = mac_decode(g, vec);
+                for (int q = threadIdx.x; q < (nel >> 2); q += blockDim.x) {
+                    const uint4 t = mac_load4(mv, mac, j0 + 4 * q);
+                    uint32_t* s = sm + pad_idx(4 * q);
+                    s[0] = t.x; s[1] = t.y; s[2] = t.z; s[3] = t.w;
+                }
+            } else {
+                for (int q = threadIdx.x; q < (nel >> 2); q += blockDim.x) {
+                    const uint4 t = *reinterpret_cast<const uint4*>(data + gbase + 4 * q);
+                    uint32_t* s = sm + pad_idx(4 * q);
+                    s[0] = t.x; s[1] = t.y; s[2] = t.z; s[3] = t.w;
+                }
+            }
+        } else {
+            const MacVec mv = MAC ? mac_decode(g, vec) : MacVec{};
+            for (int i = threadIdx.x; i < nel; i += blockDim.x)
+                sm[pad_idx(i)] = MAC ? mac_load1(mv, mac, j0 + i) : data[gbase + i];
+        }
+        __syncthreads();
+        const int rin0 = (int)(row0 & ((int64_t(1) << lg_rpv) - 1));
+        const PassArgs a{rows, (1 << g.m1) + rin0, 1, tw_all, g.N, pi, g.P, false};
+        run_rounds<INV, false, M2, 0, 0>(sm, a);
+    } else {
+        // rows are whole vectors (N = M < tile): vector row0 + r, primes alternate
+        bool any = false;
+        for (int r = 0; r < rows && !any; ++r)
+            any = INV ? inv_live(g, (unsigned)(row0 + r)) : fwd_live(g, (unsigned)(row0 + r));
+        if (!any) return;
+        for (int r = 0; r < rows; ++r) {
+            const unsigned vec = (unsigned)(row0 + r);
+            if (MAC) {
+                const MacVec mv = mac_decode(g, vec);
+                for (int l = threadIdx.x; l < M; l += blockDim.x) sm[pad_idx((r << M2) + l)] = mac_load1(mv, mac, l);
+            } else {
+                for (int l = threadIdx.x; l < M; l += blockDim.x)
+                    sm[pad_idx((r << M2) + l)] = data[((int64_t)vec << g.lgN) + l];
+            }
+        }
+        __syncthreads();
+        const PassArgs a{rows, 1, 0, tw_all, g.N, (int)(row0 % g.P), g.P, g.P > 1};
+        run_rounds<INV, false, M2, 0, 0>(sm, a);
+    }
+    if ((nel & 3) == 0) {
+        for (int q = threadIdx.x; q < (nel >> 2); q += blockDim.x) {
+            const uint32_t* s = sm + pad_idx(4 * q);
+            *reinterpret_cast<uint4*>(data + gbase + 4 * q) = make_uint4(s[0], s[1], s[2], s[3]);
+        }
+    } else {
+        for (int i = threadIdx.x; i < nel; i += blockDim.x) data[gbase + i] = sm[pad_idx(i)];
+    }
+}
+
+// ------------------------------------------------------------------ launches
+static inline size_t ntt_smem_for(int64_t tile) { return (size_t)(tile + tile / 32) * sizeof(uint32_t); }
+
+template <typename Kern>
+static cudaError_t ntt_prep(Kern kernel, size_t smem)
+{
+    if (smem > 48 * 1024)
+        return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return cudaSuccess;
+}
+
+template <bool INV, int M1>
+cudaError_t launch_col_m(const NttGeom& g, uint32_t* data, const uint2* tw, cudaStream_t s)
+{
+    constexpr int64_t tile = (int64_t(1) << col_log_t(M1)) << M1;
+    const size_t smem = ntt_smem_for(tile);
+    cudaError_t e = ntt_prep(ntt_col_kernel<INV, M1>, smem);
+    if (e != cudaSuccess) return e;
+    const int64_t grid = g.nvec * ((int64_t(1) << g.m2) >> col_log_t(M1));
+    ntt_col_kernel<INV, M1><<<(unsigned)grid, NTT_THREADS, smem, s>>>(g, data, tw);
+    return cudaGetLastError();
+}
+
+template <bool INV, bool MAC, int M2>
+cudaError_t launch_row_m(const NttGeom& g, uint32_t* data, const uint2* tw, MacSrc mac, cudaStream_t s)
+{
+    constexpr int RPC = M2 <= TILE_LOG ? (1 << (TILE_LOG - M2)) : 1;
+    constexpr int64_t tile = (int64_t(1) << M2) * RPC;
+    const size_t smem = ntt_smem_for(tile);
+    cudaError_t e = ntt_prep(ntt_row_kernel<INV, MAC, M2>, smem);
+    if (e != cudaSuccess) return e;
+    const int64_t rows_total = g.nvec * (g.N >> M2);
+    const int64_t grid = (rows_total + RPC - 1) / RPC;
+    ntt_row_kernel<INV, MAC, M2><<<(unsigned)grid, NTT_THREADS, smem, s>>>(g, data, tw, mac);
+    return cudaGetLastError();
+}
+
+}  // namespace oz

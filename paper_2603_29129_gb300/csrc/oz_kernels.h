@@ -51,6 +51,7 @@ cudaError_t launch_split_level(int k, double* r, const uint64_t* mu_in, uint64_t
 struct CrtArgs {
     const uint32_t* Z;     // [B][4][G][P][N] inverse NTT outputs (natural order)
     const Sched* sched;    // [B][4]
+    const int32_t* span;   // [B][3] min S, max S, any group
     const double2* w;      // [n] chirp
     double2* out;          // [B][n]
     int64_t n, N, B;

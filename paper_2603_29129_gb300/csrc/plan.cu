@@ -11,6 +11,7 @@
 //   mu     [B][2][K+1] uint64                  bit patterns of ||r^(k)||_inf
 //   X      [B][2][K][P][N] uint32              slice residues, then spectra (bit-reversed)
 //   kcnt   [B][2] int32, sched [B][4] Sched    live levels, flush schedules
+//   span   [B][3] int32                        min S, max S, any group (per signal)
 //   Z      [B][4][G][P][N] uint32              inverse NTT outputs (natural order)
 // Every array is allocated once per plan; an execution allocates nothing.
 #include <cmath>
@@ -60,6 +61,7 @@ struct ozfft_plan_s {
     uint32_t* X = nullptr;
     int32_t* kcnt = nullptr;
     Sched* sched = nullptr;
+    int32_t* span = nullptr;     // [B][3] scale span of each signal's flush groups
     uint32_t* Z = nullptr;
     int* status = nullptr;
     double* dbg_r = nullptr;     // [B][2][N] (debug plans)
@@ -154,50 +156,63 @@ static int ceil_log2_h(double mu)
 }
 
 // ------------------------------------------------------------ small kernels
-// Alg. 8 flush schedule of every (signal, real convolution): the x~' split
-// levels and scales come from mu, those of w~* from the plan.
+// Alg. 8 flush schedules of every signal's four real convolutions: the x~'
+// split levels and scales come from mu, those of w~* from the plan.  One
+// thread per signal; it also records the signal's scale span over all groups
+// (span[b] = {min S, max S, any group}) for the exact accumulation.
 __global__ void schedule_kernel(const uint64_t* __restrict__ mu, int64_t B, int K, int L, int alpha,
                                 const int32_t* __restrict__ wk, const int32_t* __restrict__ wsexp,
-                                Sched* __restrict__ sched, int32_t* __restrict__ kcnt)
+                                Sched* __restrict__ sched, int32_t* __restrict__ kcnt, int32_t* __restrict__ span)
 {
-    const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (id >= B * 4) return;
-    const int64_t b = id >> 2;
-    const int c = (int)(id & 3);
-    const int vx = (c == 0 || c == 3) ? 0 : 1;
-    const int vw = (c == 0 || c == 2) ? 0 : 1;
-    int sx[MAX_K];
-    int kx = 0;
-    for (int k = 0; k < K; ++k) {
-        const double m = __longlong_as_double((long long)mu[(b * 2 + vx) * (K + 1) + k]);
-        if (!(m > 0.0)) break;
-        sx[kx++] = alpha - ceil_log2_pos(m);
-    }
-    if (c < 2) kcnt[b * 2 + vx] = kx;
-    const int ky = wk[vw];
-    Sched& S = sched[id];
-    int g = 0, l = 0;
-    if (kx > 0 && ky > 0) {
-        int cur = sx[kx - 1] + wsexp[vw * K + ky - 1];
-        for (int k = kx + ky - 2; k >= 0; --k) {
-            const int s0 = max(0, k - ky + 1), s1 = min(kx - 1, k);
-            for (int s = s0; s <= s1; ++s) {
-                const int t = k - s;
-                const int sc = sx[s] + wsexp[vw * K + t];
-                if (l >= L || sc != cur) {   // flush: start a new group
-                    ++g;
-                    cur = sc;
-                    l = 0;
-                }
-                S.S[g] = cur;
-                S.pair[g][l] = s * 16 + t;
-                ++l;
-                S.size[g] = l;
-            }
+    const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    int sx[2][MAX_K];
+    int kxv[2];
+    for (int v = 0; v < 2; ++v) {
+        int kx = 0;
+        for (int k = 0; k < K; ++k) {
+            const double m = __longlong_as_double((long long)mu[(b * 2 + v) * (K + 1) + k]);
+            if (!(m > 0.0)) break;
+            sx[v][kx++] = alpha - ceil_log2_pos(m);
         }
-        ++g;
+        kxv[v] = kx;
+        kcnt[b * 2 + v] = kx;
     }
-    S.ngroups = g;
+    int smin = 0, smax = 0, any = 0;
+    for (int c = 0; c < 4; ++c) {
+        const int vx = (c == 0 || c == 3) ? 0 : 1;
+        const int vw = (c == 0 || c == 2) ? 0 : 1;
+        const int kx = kxv[vx], ky = wk[vw];
+        Sched& S = sched[b * 4 + c];
+        int g = 0, l = 0;
+        if (kx > 0 && ky > 0) {
+            int cur = sx[vx][kx - 1] + wsexp[vw * K + ky - 1];
+            for (int k = kx + ky - 2; k >= 0; --k) {
+                const int s0 = max(0, k - ky + 1), s1 = min(kx - 1, k);
+                for (int s = s0; s <= s1; ++s) {
+                    const int t = k - s;
+                    const int sc = sx[vx][s] + wsexp[vw * K + t];
+                    if (l >= L || sc != cur) {   // flush: start a new group
+                        ++g;
+                        cur = sc;
+                        l = 0;
+                    }
+                    S.S[g] = cur;
+                    S.pair[g][l] = s * 16 + t;
+                    ++l;
+                    S.size[g] = l;
+                    smin = any ? min(smin, cur) : cur;
+                    smax = any ? max(smax, cur) : cur;
+                    any = 1;
+                }
+            }
+            ++g;
+        }
+        S.ngroups = g;
+    }
+    span[b * 3 + 0] = smin;
+    span[b * 3 + 1] = smax;
+    span[b * 3 + 2] = any;
 }
 
 // Y -> Y * N^-1 * 2^32 mod p, via Montgomery with the constant N^-1 2^64 mod p
@@ -214,7 +229,7 @@ __global__ void ymont_kernel(uint32_t* Y, int64_t N, int64_t total, int P, uint3
 static void plan_free(ozfft_plan_s* p)
 {
     void* ptrs[] = {p->chirp, p->tw, p->twinv, p->Ym, p->wk, p->wsexp, p->r, p->mu, p->X, p->kcnt, p->sched,
-                    p->Z, p->status, p->dbg_r, p->dbg_X, p->stage_in, p->stage_out};
+                    p->span, p->Z, p->status, p->dbg_r, p->dbg_X, p->stage_in, p->stage_out};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     for (auto& r : p->pending) {
@@ -259,6 +274,7 @@ static int plan_build(ozfft_plan_s* p)
     if ((rc = dalloc(p, &p->X, (size_t)B * 2 * K * P * N))) return rc;
     if ((rc = dalloc(p, &p->kcnt, (size_t)B * 2))) return rc;
     if ((rc = dalloc(p, &p->sched, (size_t)B * 4))) return rc;
+    if ((rc = dalloc(p, &p->span, (size_t)B * 3))) return rc;
     if ((rc = dalloc(p, &p->Z, (size_t)B * 4 * p->G * P * N))) return rc;
     if ((rc = dalloc(p, &p->status, 1))) return rc;
     if (p->debug) {
@@ -446,8 +462,8 @@ int ozfft_execute(ozfft_plan_t p, const void* in, void* out, void* stream)
     }
     if (p->debug)
         CUDA_TRY(cudaMemcpyAsync(p->dbg_X, p->X, sizeof(uint32_t) * B * 2 * K * p->P * N, cudaMemcpyDeviceToDevice, s));
-    schedule_kernel<<<(unsigned)((B * 4 + 127) / 128), 128, 0, s>>>(p->mu, B, K, p->L, p->alpha, p->wk, p->wsexp,
-                                                                     p->sched, p->kcnt);
+    schedule_kernel<<<(unsigned)((B + 127) / 128), 128, 0, s>>>(p->mu, B, K, p->L, p->alpha, p->wk, p->wsexp,
+                                                                 p->sched, p->kcnt, p->span);
     CUDA_TRY(cudaGetLastError());
     mark(p, OZFFT_PROF_SCHEDULE, s);
     if (p->geom_fwd.m1 > 0) {
@@ -462,7 +478,7 @@ int ozfft_execute(ozfft_plan_t p, const void* in, void* out, void* stream)
         CUDA_TRY(launch_ntt_inv_col(p->geom_inv, p->Z, p->twinv, s));
         mark(p, OZFFT_PROF_NTT_INV_COL, s);
     }
-    CrtArgs ca{p->Z, p->sched, p->chirp, (double2*)out, p->n, N, B, p->P, p->G, p->direction, p->status};
+    CrtArgs ca{p->Z, p->sched, p->span, p->chirp, (double2*)out, p->n, N, B, p->P, p->G, p->direction, p->status};
     CUDA_TRY(launch_crt_post(ca, s));
     mark(p, OZFFT_PROF_CRT, s);
     p->cur = nullptr;
@@ -737,6 +753,7 @@ static int noalloc_setup(NoallocState& st, int dev, int64_t n, int64_t N, int al
     p.X = (uint32_t*)noalloc_take(cur, sizeof(uint32_t) * 2 * K * P * NM);
     p.kcnt = (int32_t*)noalloc_take(cur, sizeof(int32_t) * 2);
     p.sched = (Sched*)noalloc_take(cur, sizeof(Sched) * 4);
+    p.span = (int32_t*)noalloc_take(cur, sizeof(int32_t) * 3);
     p.Z = (uint32_t*)noalloc_take(cur, sizeof(uint32_t) * 4 * K * K * P * NM);
     p.status = (int*)noalloc_take(cur, sizeof(int));
     if ((size_t)(cur - st.base) > NOALLOC_BYTES)

@@ -114,6 +114,23 @@ def test_multi_pass_sizes_bit_exact(oz, n, kind):
         assert np.array_equal(y[b].view(np.uint64), yo.view(np.uint64)), b
 
 
+def test_wide_scale_spans(oz):
+    """A dominant sample over a sea of tiny ones leaves split levels with gaps,
+    so the flush groups' scales span more than the register accumulator holds;
+    such signals take the shared-memory accumulation path, still bit-exact."""
+    n = 4096
+    xs = synth.complex_signal("uniform", n, 12, batch=3)
+    for b, tiny in enumerate((1e-50, 1e-100, 1e-200)):
+        xs[b, 1:] *= tiny
+        xs[b, 0] = 1.0
+    for P in (2, 3):
+        y, plan = run_gpu(oz, xs, nprimes=P)
+        assert plan.status() == oz.OK
+        for b in range(3):
+            yo, _ = oracle_vs(xs[b], plan)
+            assert np.array_equal(y[b].view(np.uint64), yo.view(np.uint64)), (P, b)
+
+
 def test_batch_mixed_distributions(oz):
     n = 2048
     xs = np.concatenate([synth.complex_signal(k, n, 7, phi=4.0) for k in
