@@ -105,6 +105,32 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
+# ----------------------------------------------------------------- ranks
+def init_dist(world):
+    """One process per GPU under torchrun (NCCL), gloo when no GPU is present."""
+    if world <= 1:
+        return None
+    import torch
+    import torch.distributed as dist
+    dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    return dist
+
+
+def max_over_ranks(dist, v, device):
+    """The slowest rank's time (the job's time); v unchanged on one process."""
+    if dist is None:
+        return v
+    import torch
+    t = torch.tensor([float(v)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(steps, per_rank_units, world, ms):
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return steps * per_rank_units * world / (ms / 1e3)
+
+
 # ----------------------------------------------------------------- reference arm
 def run_reference(a, rank, world):
     """The oracle, as it stands, timed on the host cores: one signal per step."""
@@ -146,10 +172,7 @@ def main():
     import numpy as np
     import torch
 
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    dist = init_dist(world)
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
@@ -164,12 +187,8 @@ def main():
         if dist:
             dist.barrier()
 
-    def max_over_ranks(v):
-        if not dist:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    def rank_max(v):
+        return max_over_ranks(dist, v, dev)
 
     B, n = a.batch, a.n
     x_host = synth.complex_signal("uniform", n, a.seed + 1000 * rank, batch=B)
@@ -199,8 +218,8 @@ def main():
     clk = clocks.stop()
     plan.set_profiling(False)
     prof = plan.profile()
-    ms = max_over_ranks(e0.elapsed_time(e1))
-    value = a.steps * B * world / (ms / 1e3)
+    ms = rank_max(e0.elapsed_time(e1))
+    value = job_value(a.steps, B, world, ms)
     stats = plan.stats()
     if plan.status() != ozfft.OK:
         raise RuntimeError("device status flagged the benchmark input")
@@ -224,8 +243,8 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize(dev)
         barrier()
-        pms = max_over_ranks(e0.elapsed_time(e1))
-        plain = {"value": psteps * B * world / (pms / 1e3), "unit": UNIT, "steps": psteps,
+        pms = rank_max(e0.elapsed_time(e1))
+        plain = {"value": job_value(psteps, B, world, pms), "unit": UNIT, "steps": psteps,
                  "ms_per_step": pms / psteps, "executions_per_step": B}
         del p1
 
@@ -240,8 +259,8 @@ def main():
         t0 = time.perf_counter()
         for _ in range(esteps):
             plan.execute_host(x_pin, out_pin)
-        dt = max_over_ranks(time.perf_counter() - t0)
-        e2e = {"value": esteps * B * world / dt, "unit": UNIT, "h2d_bytes_per_step": B * n * 16,
+        dt = rank_max(time.perf_counter() - t0)
+        e2e = {"value": job_value(esteps, B, world, 1e3 * dt), "unit": UNIT, "h2d_bytes_per_step": B * n * 16,
                "d2h_bytes_per_step": B * n * 16, "steps": esteps}
 
     if rank != 0:
