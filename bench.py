@@ -282,11 +282,13 @@ def main():
     slots = prof["slots"]
     dom = max(slots, key=lambda k: slots[k]["ms"])
     execs = max(1, prof["executions"])
+    launches_per_exec = max(1, slots[dom]["launches"] // execs)
     dom_ms = slots[dom]["ms"] / max(1, slots[dom]["launches"])
     pk = peaks()
     roof = None
     if alg.get(dom):
-        achieved = alg[dom] / (dom_ms / 1e3) / 1e9
+        alg_launch = alg[dom] / launches_per_exec          # the slot's bytes are per execution
+        achieved = alg_launch / (dom_ms / 1e3) / 1e9
         peak = pk["hbm_gbs"] if pk else 6800.0
         traffic = None
         tfile = os.path.join(ROOT, "profiles", "ncu_traffic.json")
@@ -298,7 +300,7 @@ def main():
         roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if pk else "fallback 6.8 TB/s",
-                "algorithmic_bytes_per_launch": alg[dom], "launch_ms": dom_ms}
+                "algorithmic_bytes_per_launch": alg_launch, "launch_ms": dom_ms}
     total_ntt = runtime_fwd + inv_vecs
     ntt_ms = sum(slots[k]["ms"] for k in slots if k.startswith("ntt")) / execs
     breakdown = {k: round(v["ms"] / execs, 4) for k, v in slots.items()}

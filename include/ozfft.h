@@ -69,6 +69,10 @@ typedef struct {
                          two >= 2n-1; §3.2) */
     int32_t debug;    /* nonzero: keep the slice residues of each execution for ozfft_debug_dump
                          (costs one extra copy per execution; for tests) */
+    int32_t chunk;    /* signals per inverse-stage chunk: the inverse NTTs and the CRT stage run
+                         chunk by chunk, which bounds the inverse-NTT buffer to chunk signals
+                         (default: the whole batch while that buffer fits in 16 GiB; debug plans
+                         always use the whole batch) */
 } ozfft_options;
 
 /* Create a plan for `batch` transforms of length n in `direction`, with default
@@ -175,7 +179,8 @@ const char* ozfft_last_error(void);
                                                        S = s_x + s_y (c_x c_y = 2^S) and each pair
                                                        is s*16 + t, in Alg. 8's flush order
      OZFFT_DUMP_ZRES      [4][G][P][N] uint32          inverse-NTT outputs of signal b, G = K*K
-                                                       (groups beyond ngroups hold no data)
+                                                       (groups beyond ngroups hold no data;
+                                                       kept for every signal by debug plans only)
    Returns the number of bytes written (or a negative OZFFT_ERR_* code); a
    NULL `dst` just returns the size.  Valid only after one ozfft_execute. */
 enum {

@@ -39,7 +39,7 @@
 
 namespace oz {
 
-constexpr int NTT_THREADS = 512;
+constexpr int NTT_THREADS = 128;   // eight CTAs per SM overlap their load, compute and store phases
 constexpr int TILE_LOG = 13;
 
 __device__ __forceinline__ int pad_idx(int i) { return i + (i >> 5); }
@@ -58,33 +58,32 @@ __device__ __forceinline__ void bfly_gs(uint32_t& a, uint32_t& b, uint2 w, uint3
 }
 
 // RL stages on v[0 .. 2^RL) in registers; the stage-j twiddles are
-// tw[(B0 << j) + q], q < 2^j (q = sub-block of the element).
+// tw[(B0 << j) + q], q < 2^j (q = sub-block of the element).  All 2^RL - 1 of
+// them are loaded before the first butterfly so their latencies overlap.
 template <bool INV, int RL>
 __device__ __forceinline__ void radix_group(uint32_t (&v)[1 << RL], const uint2* __restrict__ tw, int B0, uint32_t p)
 {
     constexpr int R = 1 << RL;
+    uint2 w[R];                      // w[(1 << j) + q]: stage j, sub-block q (w[0] unused)
+    w[1] = __ldg(tw + B0);
+#pragma unroll
+    for (int j = 1; j < RL; ++j)
+#pragma unroll
+        for (int q = 0; q < (1 << j); q += 2) {
+            const uint4 t = __ldg(reinterpret_cast<const uint4*>(tw + (B0 << j) + q));
+            w[(1 << j) + q] = make_uint2(t.x, t.y);
+            w[(1 << j) + q + 1] = make_uint2(t.z, t.w);
+        }
 #pragma unroll
     for (int jj = 0; jj < RL; ++jj) {
         const int j = INV ? RL - 1 - jj : jj;
         const int half = R >> (j + 1);
-        uint2 w[1 << (RL - 1)];
-        const uint2* base = tw + (B0 << j);
-        if (j == 0) {
-            w[0] = __ldg(base);
-        } else {
-#pragma unroll
-            for (int q = 0; q < (1 << j); q += 2) {
-                const uint4 t = __ldg(reinterpret_cast<const uint4*>(base + q));
-                w[q] = make_uint2(t.x, t.y);
-                w[q + 1] = make_uint2(t.z, t.w);
-            }
-        }
 #pragma unroll
         for (int u = 0; u < R; ++u) {
             if (u & half) continue;
             const int q = u >> (RL - j);
-            if (INV) bfly_gs(v[u], v[u + half], w[q], p);
-            else bfly_ct(v[u], v[u + half], w[q], p);
+            if (INV) bfly_gs(v[u], v[u + half], w[(1 << j) + q], p);
+            else bfly_ct(v[u], v[u + half], w[(1 << j) + q], p);
         }
     }
 }
@@ -196,7 +195,7 @@ constexpr int col_log_t(int m1) { return (TILE_LOG - m1) > 5 ? (TILE_LOG - m1) :
 
 // ---------------------------------------------------------------- column pass
 template <bool INV, int M1>
-__global__ void __launch_bounds__(NTT_THREADS, 2) ntt_col_kernel(NttGeom g, uint32_t* __restrict__ data,
+__global__ void __launch_bounds__(NTT_THREADS, 8) ntt_col_kernel(NttGeom g, uint32_t* __restrict__ data,
                                                                  const uint2* __restrict__ tw_all)
 {
     extern __shared__ uint32_t sm[];
@@ -292,7 +291,7 @@ __device__ __forceinline__ uint32_t mac_load1(const MacVec& m, const MacSrc& mac
 }
 
 template <bool INV, bool MAC, int M2>
-__global__ void __launch_bounds__(NTT_THREADS, 2) ntt_row_kernel(NttGeom g, uint32_t* __restrict__ data,
+__global__ void __launch_bounds__(NTT_THREADS, 8) ntt_row_kernel(NttGeom g, uint32_t* __restrict__ data,
                                                                  const uint2* __restrict__ tw_all, MacSrc mac)
 {
     extern __shared__ uint32_t sm[];

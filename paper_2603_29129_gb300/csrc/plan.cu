@@ -12,8 +12,12 @@
 //   X      [B][2][K][P][N] uint32              slice residues, then spectra (bit-reversed)
 //   kcnt   [B][2] int32, sched [B][4] Sched    live levels, flush schedules
 //   span   [B][3] int32                        min S, max S, any group (per signal)
-//   Z      [B][4][G][P][N] uint32              inverse NTT outputs (natural order)
+//   Z      [chunk][4][G][P][N] uint32          inverse NTT outputs of one chunk of signals
+//                                              (natural order); the inverse NTTs and the CRT
+//                                              stage run chunk by chunk (default: the whole
+//                                              batch while Z fits in 16 GiB)
 // Every array is allocated once per plan; an execution allocates nothing.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -45,6 +49,7 @@ static int fail(int code, const std::string& msg)
 struct ozfft_plan_s {
     int64_t n = 0, N = 0, B = 0;
     int direction = -1, K = 3, L = 1, P = 2, alpha = 0, G = 9, debug = 0;
+    int64_t chunk = 1;           // signals per inverse-stage chunk (Z holds one chunk)
     int device = 0;
     NttGeom geom_fwd{}, geom_inv{};
     int64_t launches = 0, bytes = 0;
@@ -275,7 +280,7 @@ static int plan_build(ozfft_plan_s* p)
     if ((rc = dalloc(p, &p->kcnt, (size_t)B * 2))) return rc;
     if ((rc = dalloc(p, &p->sched, (size_t)B * 4))) return rc;
     if ((rc = dalloc(p, &p->span, (size_t)B * 3))) return rc;
-    if ((rc = dalloc(p, &p->Z, (size_t)B * 4 * p->G * P * N))) return rc;
+    if ((rc = dalloc(p, &p->Z, (size_t)p->chunk * 4 * p->G * P * N))) return rc;
     if ((rc = dalloc(p, &p->status, 1))) return rc;
     if (p->debug) {
         if ((rc = dalloc(p, &p->dbg_r, (size_t)B * 2 * N))) return rc;
@@ -382,11 +387,12 @@ static int plan_build(ozfft_plan_s* p)
     p->geom_fwd.nvec = B * 2 * K * P;
     p->geom_fwd.kcnt = p->kcnt;
     p->geom_fwd.sched = p->sched;
-    p->geom_inv.nvec = B * 4 * p->G * P;
+    p->geom_inv.nvec = p->chunk * 4 * p->G * P;
     p->geom_inv.kcnt = p->kcnt;
     p->geom_inv.sched = p->sched;
-    p->launches = 1 /*premul*/ + K /*split*/ + 1 /*schedule*/ + ntt_launches(p->geom_fwd) + ntt_launches(p->geom_inv) +
-                  crt_launches();
+    const int64_t nchunks = (B + p->chunk - 1) / p->chunk;
+    p->launches = 1 /*premul*/ + K /*split*/ + 1 /*schedule*/ + ntt_launches(p->geom_fwd) +
+                  nchunks * (ntt_launches(p->geom_inv) + crt_launches());
     return OZFFT_OK;
 }
 
@@ -427,6 +433,12 @@ ozfft_plan_t ozfft_plan_ex(int64_t n, int64_t batch, int direction, const ozfft_
     p->G = K * K;
     p->alpha = alpha;
     p->debug = o.debug;
+    {
+        const int64_t zbytes = (int64_t)4 * p->G * P * N * 4;   // Z of one signal
+        int64_t c = o.chunk > 0 ? o.chunk : std::max<int64_t>(1, (int64_t(16) << 30) / zbytes);
+        if (p->debug) c = batch;                              // dumps read Z of any signal
+        p->chunk = std::min<int64_t>(c, batch);
+    }
     if (plan_build(p) != OZFFT_OK) {
         plan_free(p);
         return nullptr;
@@ -472,14 +484,24 @@ int ozfft_execute(ozfft_plan_t p, const void* in, void* out, void* stream)
     }
     CUDA_TRY(launch_ntt_fwd_row(p->geom_fwd, p->X, p->tw, s));
     mark(p, OZFFT_PROF_NTT_FWD_ROW, s);
-    CUDA_TRY(launch_ntt_inv_row(p->geom_inv, p->Z, p->twinv, MacSrc{p->X, p->Ym}, s));
-    mark(p, OZFFT_PROF_NTT_INV_ROW, s);
-    if (p->geom_inv.m1 > 0) {
-        CUDA_TRY(launch_ntt_inv_col(p->geom_inv, p->Z, p->twinv, s));
-        mark(p, OZFFT_PROF_NTT_INV_COL, s);
+    // inverse stages chunk by chunk: Z of one chunk stays in L2 between the passes
+    for (int64_t b0 = 0; b0 < B; b0 += p->chunk) {
+        const int64_t nb = std::min<int64_t>(p->chunk, B - b0);
+        NttGeom gi = p->geom_inv;
+        gi.nvec = nb * 4 * p->G * p->P;
+        gi.sched = p->sched + b0 * 4;
+        const MacSrc mac{p->X + b0 * 2 * K * p->P * N, p->Ym};
+        CUDA_TRY(launch_ntt_inv_row(gi, p->Z, p->twinv, mac, s));
+        mark(p, OZFFT_PROF_NTT_INV_ROW, s);
+        if (gi.m1 > 0) {
+            CUDA_TRY(launch_ntt_inv_col(gi, p->Z, p->twinv, s));
+            mark(p, OZFFT_PROF_NTT_INV_COL, s);
+        }
+        CrtArgs ca{p->Z, p->sched + b0 * 4, p->span + b0 * 3, p->chirp, (double2*)out + b0 * p->n, p->n, N, nb,
+                   p->P, p->G, p->direction, p->status};
+        CUDA_TRY(launch_crt_post(ca, s));
+        if (b0 + p->chunk < B) mark(p, OZFFT_PROF_CRT, s);
     }
-    CrtArgs ca{p->Z, p->sched, p->span, p->chirp, (double2*)out, p->n, N, B, p->P, p->G, p->direction, p->status};
-    CUDA_TRY(launch_crt_post(ca, s));
     mark(p, OZFFT_PROF_CRT, s);
     p->cur = nullptr;
     p->executed = true;
@@ -627,7 +649,10 @@ int64_t ozfft_debug_dump(ozfft_plan_t p, int stage, int64_t index, void* dst, vo
     case OZFFT_DUMP_XSPEC: src = p->X + b * 2 * K * P * N; bytes = 4 * 2 * K * P * N; bitrev_vectors = true; break;
     case OZFFT_DUMP_YSPEC: src = p->Ym; bytes = 4 * 2 * K * P * N; bitrev_vectors = true; break;
     case OZFFT_DUMP_SCHED: src = p->sched + b * 4; bytes = sizeof(Sched) * 4; break;
-    case OZFFT_DUMP_ZRES: src = p->Z + b * 4 * G * P * N; bytes = 4 * 4 * G * P * N; break;
+    case OZFFT_DUMP_ZRES:
+        src = (p->chunk == p->B) ? p->Z + b * 4 * G * P * N : nullptr;
+        bytes = 4 * 4 * G * P * N;
+        break;
     default: return -fail(OZFFT_ERR_ARG, "ozfft_debug_dump: unknown stage");
     }
     if (!src) return -fail(OZFFT_ERR_ARG, "ozfft_debug_dump: stage kept only by debug plans");
@@ -739,7 +764,7 @@ static int noalloc_setup(NoallocState& st, int dev, int64_t n, int64_t N, int al
     st.n = 0;
     ozfft_plan_s& p = st.plan;
     const int K = 3, P = 2, NM = (int)NOALLOC_MAX_N;
-    p.n = n; p.N = N; p.B = 1; p.K = K; p.L = 1; p.P = P; p.G = K * K; p.alpha = alpha; p.debug = 0;
+    p.n = n; p.N = N; p.B = 1; p.K = K; p.L = 1; p.P = P; p.G = K * K; p.alpha = alpha; p.debug = 0; p.chunk = 1;
     p.device = dev; p.profiling = false; p.bytes = 0;
     unsigned char* cur = st.base;
     p.chirp = (double2*)noalloc_take(cur, sizeof(double2) * NM);

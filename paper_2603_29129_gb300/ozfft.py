@@ -29,7 +29,7 @@ PROF_SLOTS = ("premul", "split", "schedule", "ntt_fwd_col", "ntt_fwd_row", "ntt_
 
 class Options(C.Structure):
     _fields_ = [("K", C.c_int32), ("L", C.c_int32), ("nprimes", C.c_int32), ("conv_len", C.c_int64),
-                ("debug", C.c_int32)]
+                ("debug", C.c_int32), ("chunk", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -97,11 +97,11 @@ def _stream_ptr(stream):
 class Plan:
     """A plan for `batch` transforms of length n (see ozfft_plan_ex)."""
 
-    def __init__(self, n, batch=1, direction=FORWARD, K=3, L=1, nprimes=2, conv_len=0, debug=False):
+    def __init__(self, n, batch=1, direction=FORWARD, K=3, L=1, nprimes=2, conv_len=0, debug=False, chunk=0):
         lib = load()
         self.n, self.batch, self.direction = int(n), int(batch), int(direction)
         self.K, self.L, self.nprimes = int(K), int(L), int(nprimes)
-        opt = Options(self.K, self.L, self.nprimes, int(conv_len), int(bool(debug)))
+        opt = Options(self.K, self.L, self.nprimes, int(conv_len), int(bool(debug)), int(chunk))
         self._h = lib.ozfft_plan_ex(self.n, self.batch, self.direction, C.byref(opt))
         if not self._h:
             raise OzfftError(-1, lib.ozfft_last_error().decode())
