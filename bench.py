@@ -100,7 +100,8 @@ def peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("k_ntt.cu", "oz_common.cuh", "oz_kernels.h"):
+    for f in ("ntt_impl.cuh", "k_ntt.cu", "k_ntt_row_inv.cu", "k_ntt_row_fwd.cu", "k_ntt_col.cu", "oz_common.cuh",
+              "oz_kernels.h"):
         h.update(open(os.path.join(ROOT, "paper_2603_29129_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 

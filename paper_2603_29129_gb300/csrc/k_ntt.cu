@@ -14,7 +14,7 @@ void ntt_configure(NttGeom& g, int64_t N)
     if (lg <= TILE_LOG) {          // one pass: whole vectors in a CTA tile
         g.m1 = 0;
         g.m2 = lg;
-    } else {                       // rows of 2^13 (2^14 for N = 2^24), columns of the rest
+    } else {                       // rows of 2^12 (2^13, 2^14 for N = 2^23, 2^24), columns of the rest
         g.m2 = TILE_LOG;
         g.m1 = lg - TILE_LOG;
         if (g.m1 > 10) { g.m1 = 10; g.m2 = lg - 10; }

@@ -40,7 +40,7 @@
 namespace oz {
 
 constexpr int NTT_THREADS = 128;   // eight CTAs per SM overlap their load, compute and store phases
-constexpr int TILE_LOG = 13;
+constexpr int TILE_LOG = 12;   // CTA tile of 4096 residues: ~13 CTAs fit an SM by shared memory
 
 __device__ __forceinline__ int pad_idx(int i) { return i + (i >> 5); }
 
