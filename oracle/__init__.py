@@ -22,6 +22,7 @@ LIB = os.path.join(HERE, "liboracle.so")
 KMAX = 64
 OK, ERR_ARG, ERR_LENGTH, ERR_ALLOC, ERR_NONFINITE, ERR_RANGE = 0, 1, 2, 3, 5, 6
 FORWARD, INVERSE = -1, 1
+ADJOINT, INVERSE_ADJOINT = 2, -2   # F^H x and (1/n) F x (reverse-mode adjoints)
 
 
 def build_command():

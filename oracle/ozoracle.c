@@ -42,6 +42,10 @@
  *       accumulation approximates; the oracle computes it with a two's-complement
  *       big integer in units of 2^-max(S).
  *   R8  inverse direction: conj -> forward -> conj -> round(v / n) (Eq. (4)).
+ *       Two more directions serve reverse-mode differentiation: the adjoint of
+ *       the forward transform, F^H g = conj(F conj g) (direction +2: R8 without
+ *       the division), and the adjoint of the inverse, (1/n) F g (direction -2:
+ *       the forward transform, then round(v / n)).
  *   R9  third prime (used only when three primes are requested): 15*2^27 + 1.
  */
 #include <math.h>
@@ -514,6 +518,11 @@ typedef struct {
     double* yprime;               /* [n][2] y' before the post-multiply */
 } or_trace;
 
+/* transform directions (R8): -1 forward, +1 inverse, +2 / -2 their adjoints */
+static int dir_ok(int d) { return d == -1 || d == 1 || d == 2 || d == -2; }
+static int dir_conj(int d) { return d > 0; }              /* exponent sign + */
+static int dir_scaled(int d) { return d == 1 || d == -2; } /* divide by n */
+
 /* vector index pairs of the four real convolutions (§4.5): RR, II, IR, RI */
 static const int CONV_X[4] = {0, 1, 1, 0};
 static const int CONV_W[4] = {2, 3, 2, 3};
@@ -524,7 +533,7 @@ int or_ozfft(int64_t n, int64_t N, int K, int L, int nprimes, int direction,
              const double* x, double* y, or_trace* tr)
 {
     if (n < 1 || N < n || (N & (N - 1)) || L < 1 || K < 0 || nprimes < 2 || nprimes > 3 ||
-        (direction != -1 && direction != 1))
+        !dir_ok(direction))
         return OR_ERR_ARG;
     if (!(N == n || N >= 2 * n - 1)) return OR_ERR_LENGTH;
     for (int i = 0; i < nprimes; ++i)
@@ -561,7 +570,7 @@ int or_ozfft(int64_t n, int64_t N, int K, int L, int nprimes, int direction,
     or_chirp(n, w);
     for (int64_t j = 0; j < n; ++j) {
         double a = x[2 * j], b = x[2 * j + 1];
-        if (direction == 1) b = -b;
+        if (dir_conj(direction)) b = -b;
         cmul(a, b, w[2 * j], w[2 * j + 1], &vec[j], &vec[szN + j]);
     }
     /* ZeroPad (x~') is implicit in calloc; ZeroPad+- of w* (§3.2) */
@@ -692,8 +701,8 @@ int or_ozfft(int64_t n, int64_t N, int K, int L, int nprimes, int direction,
         if (tr && tr->yprime) { tr->yprime[2 * j] = yr; tr->yprime[2 * j + 1] = yi; }
         double re, im;
         cmul(yr, yi, w[2 * j], w[2 * j + 1], &re, &im);
-        if (direction == 1) {
-            im = -im;
+        if (dir_conj(direction)) im = -im;
+        if (dir_scaled(direction)) {
             re = re / (double)n;
             im = im / (double)n;
         }
@@ -753,12 +762,13 @@ static void store_q(qreal v, double* hi, double* lo)
     *lo = (double)(v - (qreal)h);
 }
 
-/* Naive DFT (Eq. (3)) / inverse DFT (Eq. (4)) at the requested bins (all when
+/* Naive DFT (Eq. (3)) / inverse DFT (Eq. (4)) / their adjoints (direction +2:
+   exponent sign +, no division; -2: sign -, divided by n) at the requested bins (all when
    bins == NULL).  x interleaved (re, im); yhi, ylo interleaved per bin. */
 int or_dft_q(int64_t n, const double* x, int direction, int64_t nbins, const int64_t* bins,
              double* yhi, double* ylo)
 {
-    if (n < 1 || (direction != -1 && direction != 1)) return OR_ERR_ARG;
+    if (n < 1 || !dir_ok(direction)) return OR_ERR_ARG;
     qreal* tw = (qreal*)malloc(sizeof(qreal) * 2 * (size_t)n);
     if (!tw) return OR_ERR_ALLOC;
     for (int64_t m = 0; m < n; ++m) unit_q(m, n, direction, &tw[2 * m], &tw[2 * m + 1]);
@@ -772,7 +782,7 @@ int or_dft_q(int64_t n, const double* x, int direction, int64_t nbins, const int
             ar += xr * tw[2 * e] - xi * tw[2 * e + 1];
             ai += xr * tw[2 * e + 1] + xi * tw[2 * e];
         }
-        if (direction == 1) { ar /= (qreal)n; ai /= (qreal)n; }
+        if (dir_scaled(direction)) { ar /= (qreal)n; ai /= (qreal)n; }
         store_q(ar, &yhi[2 * b], &ylo[2 * b]);
         store_q(ai, &yhi[2 * b + 1], &ylo[2 * b + 1]);
     }
@@ -784,7 +794,7 @@ int or_dft_q(int64_t n, const double* x, int direction, int64_t nbins, const int
    checked against or_dft_q by the tests. */
 int or_fft_q(int64_t n, const double* x, int direction, double* yhi, double* ylo)
 {
-    if (n < 1 || (n & (n - 1)) || (direction != -1 && direction != 1)) return OR_ERR_ARG;
+    if (n < 1 || (n & (n - 1)) || !dir_ok(direction)) return OR_ERR_ARG;
     qreal* a = (qreal*)malloc(sizeof(qreal) * 2 * (size_t)n);
     qreal* tw = (qreal*)malloc(sizeof(qreal) * (size_t)n); /* (re, im) for m < n/2 */
     if (!a || !tw) { free(a); free(tw); return OR_ERR_ALLOC; }
@@ -813,7 +823,7 @@ int or_fft_q(int64_t n, const double* x, int direction, double* yhi, double* ylo
     }
     for (int64_t i = 0; i < n; ++i) {
         qreal re = a[2 * i], im = a[2 * i + 1];
-        if (direction == 1) { re /= (qreal)n; im /= (qreal)n; }
+        if (dir_scaled(direction)) { re /= (qreal)n; im /= (qreal)n; }
         store_q(re, &yhi[2 * i], &ylo[2 * i]);
         store_q(im, &yhi[2 * i + 1], &ylo[2 * i + 1]);
     }

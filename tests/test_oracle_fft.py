@@ -143,6 +143,46 @@ def test_method_inverse_and_roundtrip():
     assert err_vs_q(yi, x, oracle.INVERSE) <= 1e-15
 
 
+def test_dft_q_adjoint_directions():
+    """The adjoint directions of the binary128 DFT: F^H x (sign +, no division)
+    and (1/n) F x, against closed forms on a delta and against numpy's FFT."""
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.prec = 200
+    n, j0 = 12, 5
+    d = np.zeros(n, complex); d[j0] = 1.0
+    ang = [mpmath.mpf(2 * (j0 * k % n)) / n for k in range(n)]       # exp(+-i pi ang)
+    up = np.array([complex(float(mpmath.cospi(a)), float(mpmath.sinpi(a))) for a in ang])
+    hi, _ = oracle.dft_q(d, direction=oracle.ADJOINT)
+    assert np.max(np.abs(hi - up)) <= 2 ** -53
+    hi, _ = oracle.dft_q(d, direction=oracle.INVERSE_ADJOINT)
+    down = np.array([complex(float(mpmath.cospi(a) / n), float(-mpmath.sinpi(a) / n)) for a in ang])
+    assert np.max(np.abs(hi - down)) <= 2 ** -53 / n
+    x = synth.complex_signal("gaussian", 64, 8)[0]
+    assert np.allclose(oracle.dft_q(x, oracle.ADJOINT)[0], 64 * np.fft.ifft(x), rtol=0, atol=1e-13)
+    assert np.allclose(oracle.fft_q(x, oracle.ADJOINT)[0], 64 * np.fft.ifft(x), rtol=0, atol=1e-13)
+    assert np.allclose(oracle.dft_q(x, oracle.INVERSE_ADJOINT)[0], np.fft.fft(x) / 64, rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("n", [256, 1000])
+def test_method_adjoints(n):
+    """<F x, g> = <x, F^H g> and <F^-1 x, g> = <x, (1/n) F g> for the method's
+    transforms; each adjoint also meets the 1e-15 target against binary128."""
+    x = synth.complex_signal("uniform", n, 21)[0]
+    g = synth.complex_signal("gaussian", n, 22)[0]
+    fx, _ = oracle.ozfft(x)
+    ahg, _ = oracle.ozfft(g, direction=oracle.ADJOINT)
+    lhs, rhs = np.vdot(g, fx), np.vdot(ahg, x)
+    assert abs(lhs - rhs) <= 1e-14 * np.linalg.norm(fx) * np.linalg.norm(g)
+    ix, _ = oracle.ozfft(x, direction=oracle.INVERSE)
+    aig, _ = oracle.ozfft(g, direction=oracle.INVERSE_ADJOINT)
+    assert abs(np.vdot(g, ix) - np.vdot(aig, x)) <= 1e-14 * np.linalg.norm(ix) * np.linalg.norm(g)
+    assert err_vs_q(ahg, g, oracle.ADJOINT) <= 1e-15
+    assert err_vs_q(aig, g, oracle.INVERSE_ADJOINT) <= 1e-15
+    # the adjoint is the conjugated forward transform of the conjugate, exactly
+    cf, _ = oracle.ozfft(np.conj(g))
+    assert np.array_equal(np.conj(cf), ahg)
+
+
 def test_padding_invariance_power_of_two():
     """Reading D3: for power-of-two n the cyclic length N = n and the padded
     N = 2n give bit-identical results."""
