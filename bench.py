@@ -51,7 +51,18 @@ def parse():
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--cpu-signals", type=int, default=2, help="oracle transforms timed for cpu_baseline")
-    return ap.parse_args()
+    ap.add_argument("--workload", choices=("batch", "autograd"), default="batch",
+                    help="batch: the headline batched forward FFT; autograd: forward + backward of "
+                         "sum |FFT(x) w|^2 over 256 Gaussian signals of n = 2^16")
+    a = ap.parse_args()
+    if a.workload == "autograd":
+        if "--n" not in sys.argv:
+            a.n = 1 << 16
+        if "--batch" not in sys.argv:
+            a.batch = 256
+        if "--seed" not in sys.argv:
+            a.seed = 5
+    return a
 
 
 def workload(a):
@@ -160,6 +171,118 @@ def run_reference(a, rank, world):
           flush=True)
 
 
+# ----------------------------------------------------------------- autograd workload
+def run_autograd(a, rank, world, local):
+    """Forward + backward of loss = sum |FFT(x) . w|^2 (per-signal complex
+    Gaussian weights) through torch.autograd; the backward pass is the adjoint
+    transform F^H through the same kernels.  Compared with the plain pipeline:
+    per signal, one batch-1 forward execution and one batch-1 adjoint execution."""
+    import numpy as np
+    import torch
+    dist = init_dist(world)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2603_29129_gb300 import build as bld
+    if rank == 0:
+        bld.build()
+    if dist:
+        dist.barrier()
+    from paper_2603_29129_gb300 import autograd as ad
+    from paper_2603_29129_gb300 import ozfft, synth
+    B, n = a.batch, a.n
+    xh = synth.complex_signal("gaussian", n, a.seed + 1000 * rank, batch=B)
+    x = torch.from_numpy(xh).to(dev).requires_grad_()
+    w = torch.from_numpy(synth.complex_signal("gaussian", n, a.seed + 1 + 1000 * rank, batch=B)).to(dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        x.grad = None
+        loss = (ad.fft(x, K=a.K, L=a.L, nprimes=a.nprimes) * w).abs().square().sum()
+        loss.backward()
+        return loss
+
+    def timed(fn, steps):
+        for _ in range(a.warmup):
+            fn()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        if dist:
+            dist.barrier()
+        return max_over_ranks(dist, e0.elapsed_time(e1), dev)
+
+    clocks = ClockSampler(local)
+    time.sleep(0.25)
+    ms = timed(step, a.steps)
+    clk = clocks.stop()
+    fw = ozfft._plans[(n, B, ozfft.FORWARD, a.K, a.L, a.nprimes, dev.index)]
+    bw = ozfft._plans[(n, B, ozfft.ADJOINT, a.K, a.L, a.nprimes, dev.index)]
+    launches = fw.stats()["kernel_launches"] + bw.stats()["kernel_launches"]
+    value = job_value(a.steps, B, world, ms)
+
+    # plain: per signal one batch-1 forward and one batch-1 adjoint execution
+    p_f = ozfft.Plan(n, 1, ozfft.FORWARD, K=a.K, L=a.L, nprimes=a.nprimes)
+    p_b = ozfft.Plan(n, 1, ozfft.ADJOINT, K=a.K, L=a.L, nprimes=a.nprimes)
+    xd = x.detach()
+    yb = torch.empty_like(xd)
+    gb = torch.empty_like(xd)
+
+    def plain_step():
+        for i in range(B):
+            p_f.execute(xd[i:i + 1], yb[i:i + 1])
+        gy = 2 * (w.abs() ** 2) * yb
+        for i in range(B):
+            p_b.execute(gy[i:i + 1], gb[i:i + 1])
+
+    psteps = max(1, a.steps // 3)
+    pms = timed(plain_step, psteps)
+
+    # e2e: inputs from pinned host memory, gradient back to host memory, every step
+    xpin = torch.from_numpy(xh).pin_memory()
+    gpin = torch.empty_like(xpin).pin_memory()
+
+    def e2e_step():
+        x.data.copy_(xpin, non_blocking=True)
+        step()
+        gpin.copy_(x.grad, non_blocking=True)
+
+    esteps = max(1, a.steps // 3)
+    ems = timed(e2e_step, esteps)
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    # gradient check on signal 0 against torch's binary64 FFT on the CPU
+    xc = torch.from_numpy(xh[:1]).requires_grad_()
+    (torch.fft.fft(xc) * w[:1].cpu()).abs().square().sum().backward()
+    step()
+    g0 = x.grad[:1].cpu()
+    rel = (torch.linalg.vector_norm(g0 - xc.grad) / torch.linalg.vector_norm(xc.grad)).item()
+    cfg = {"workload": f"forward+backward of sum |FFT(x) w|^2, complex128 n=2^{n.bit_length() - 1} x {B} "
+                       f"signals, Gaussian parts, complex Gaussian w, K={a.K}, L={a.L}, {a.nprimes} primes",
+           "n": n, "batch_per_gpu": B, "K": a.K, "L": a.L, "nprimes": a.nprimes, "seed": a.seed,
+           "parallelism": f"replicas x{world}", "l2": "inputs (batch x n x 16 B) exceed L2 each step; no flush"}
+    line = {"metric": "FP64-accurate FFT forward+backward signals/s (autograd)", "value": value,
+            "unit": "signal/s", "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic", "config": cfg,
+            "plain": {"value": job_value(psteps, B, world, pms), "unit": "signal/s", "steps": psteps,
+                      "executions_per_step": 2 * B},
+            "e2e": {"value": job_value(esteps, B, world, ems), "unit": "signal/s", "steps": esteps,
+                    "h2d_bytes_per_step": B * n * 16, "d2h_bytes_per_step": B * n * 16},
+            "clocks": clk, "gpu_launches": int(launches * a.steps),
+            "accuracy": {"grad_rel_l2_vs_torch_cpu_signal0": rel}}
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
 # ----------------------------------------------------------------- our arm
 def main():
     a = parse()
@@ -168,6 +291,9 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if a.impl == "reference":
         run_reference(a, rank, world)
+        return
+    if a.workload == "autograd":
+        run_autograd(a, rank, world, local)
         return
 
     import numpy as np

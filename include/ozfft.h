@@ -46,7 +46,13 @@ extern "C" {
 
 typedef struct ozfft_plan_s* ozfft_plan_t;
 
-enum { OZFFT_FORWARD = -1, OZFFT_INVERSE = +1 };
+/* Directions.  FORWARD: y = F x, F(k,j) = exp(-2 pi i jk/n) (Eq. (3)); INVERSE:
+   y = (1/n) F^H x (Eq. (4)).  The two adjoints serve reverse-mode
+   differentiation (the gradient of a real loss through a linear map A is A^H
+   applied to the output gradient): ADJOINT: y = F^H x = conj(F conj x), the
+   inverse without its division by n; INVERSE_ADJOINT: y = (1/n) F x, the forward
+   transform with every component divided by n (one rounding). */
+enum { OZFFT_FORWARD = -1, OZFFT_INVERSE = +1, OZFFT_ADJOINT = +2, OZFFT_INVERSE_ADJOINT = -2 };
 
 enum {
     OZFFT_OK = 0,

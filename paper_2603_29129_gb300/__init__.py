@@ -5,4 +5,4 @@ a C ABI, declared in ``include/ozfft.h``); :mod:`.ozfft` is its ctypes binding.
 Importing this package does not load the library; the first call does, and it
 raises if the library is missing (there is no CPU fallback).
 """
-__all__ = ["ozfft", "synth"]
+__all__ = ["ozfft", "autograd", "synth"]

@@ -7,7 +7,8 @@
 // 1/(c_x c_y) = 2^-S_g (Alg. 8).  The real part of y' is the exact sum of the
 // RR terms minus the II terms and the imaginary part the exact sum of the IR and
 // RI terms, each rounded once to nearest binary64; then y = y' w (Alg. 1).  The
-// inverse direction conjugates and divides by n (Eq. (4)).
+// inverse direction conjugates and divides by n (Eq. (4)); the adjoint of the
+// forward transform (+2) only conjugates, that of the inverse (-2) only divides.
 //
 // The exact sums use integer arithmetic only (binary64 throughput is low on
 // this part).  A thread keeps its element's sum as int64 limbs, each holding a
@@ -288,8 +289,8 @@ __device__ __forceinline__ void post_store(const CrtArgs& a, int64_t b, int64_t 
     const double2 w = a.w[j];
     double re, im;
     cmul(yr, yi, w.x, w.y, re, im);
-    if (a.direction == 1) {
-        im = -im;
+    if (a.direction > 0) im = -im;                      // inverse, adjoint: conj
+    if (a.direction == 1 || a.direction == -2) {        // inverse, adjoint of the inverse: / n
         re = __ddiv_rn(re, (double)a.n);
         im = __ddiv_rn(im, (double)a.n);
     }

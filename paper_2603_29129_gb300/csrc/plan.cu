@@ -403,7 +403,8 @@ ozfft_plan_t ozfft_plan_ex(int64_t n, int64_t batch, int direction, const ozfft_
     ozfft_options o{};
     if (opt) o = *opt;
     const int K = o.K ? o.K : 3, L = o.L ? o.L : 1, P = o.nprimes ? o.nprimes : 2;
-    if (n < 1 || batch < 1 || (direction != OZFFT_FORWARD && direction != OZFFT_INVERSE) || K < 1 || K > MAX_K ||
+    if (n < 1 || batch < 1 || (direction != OZFFT_FORWARD && direction != OZFFT_INVERSE && direction != OZFFT_ADJOINT &&
+                               direction != OZFFT_INVERSE_ADJOINT) || K < 1 || K > MAX_K ||
         L < 1 || L > MAX_L || P < 2 || P > 3) {
         fail(OZFFT_ERR_ARG, "ozfft_plan: argument out of range");
         return nullptr;
@@ -464,7 +465,7 @@ int ozfft_execute(ozfft_plan_t p, const void* in, void* out, void* stream)
             p->cur = &p->pending.back();
         }
     }
-    CUDA_TRY(launch_premul((const double2*)in, p->chirp, p->n, N, B, p->direction == OZFFT_INVERSE, p->r, p->mu, K,
+    CUDA_TRY(launch_premul((const double2*)in, p->chirp, p->n, N, B, p->direction > 0, p->r, p->mu, K,
                            p->status, s));
     mark(p, OZFFT_PROF_PREMUL, s);
     if (p->debug) CUDA_TRY(cudaMemcpyAsync(p->dbg_r, p->r, sizeof(double) * B * 2 * N, cudaMemcpyDeviceToDevice, s));

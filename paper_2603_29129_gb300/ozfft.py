@@ -16,6 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libozfft.so")
 
 FORWARD, INVERSE = -1, 1
+ADJOINT, INVERSE_ADJOINT = 2, -2   # F^H x and (1/n) F x: the adjoints of FORWARD and INVERSE
 OK, ERR_ARG, ERR_LENGTH, ERR_ALLOC, ERR_CUDA, ERR_NONFINITE, ERR_RANGE, ERR_TIMEOUT = range(8)
 DUMP_CHIRP, DUMP_XPRIME, DUMP_MU, DUMP_XRES, DUMP_XSPEC, DUMP_YSPEC, DUMP_SCHED, DUMP_ZRES = range(8)
 MAX_GROUPS, MAX_L = 64, 8
@@ -206,19 +207,41 @@ def execute_noalloc(x, out, direction=FORWARD, stream=None):
 
 
 _plans = {}
+_plans_lock = threading.Lock()
 
 
-def fft(x, direction=FORWARD, K=3, L=1, nprimes=2, stream=None):
-    """FP64-accurate DFT of the last axis of a CUDA complex128 tensor (plans cached)."""
+def transform(x, direction=FORWARD, K=3, L=1, nprimes=2, stream=None):
+    """The transform of the last axis of a CUDA complex128 tensor in `direction`
+    (FORWARD, INVERSE, ADJOINT or INVERSE_ADJOINT), with plans cached per
+    (length, batch, direction, options, device)."""
     shape = x.shape
     n = shape[-1]
     batch = x.numel() // n
-    key = (n, batch, direction, K, L, nprimes, x.device.index)
-    p = _plans.get(key)
-    if p is None:
-        p = _plans[key] = Plan(n, batch, direction, K, L, nprimes)
+    key = (n, batch, int(direction), K, L, nprimes, x.device.index)
+    with _plans_lock:
+        p = _plans.get(key)
+        if p is None:
+            p = _plans[key] = Plan(n, batch, direction, K, L, nprimes)
     return p.execute(x.contiguous().reshape(batch, n), stream=stream).reshape(shape)
 
 
-def ifft(x, **kw):
-    return fft(x, direction=INVERSE, **kw)
+def fft(x, K=3, L=1, nprimes=2, stream=None):
+    """FP64-accurate DFT (Eq. (3)) of the last axis of a CUDA complex128 tensor.
+    Differentiable: with autograd recording and x requiring grad, the backward
+    pass runs the adjoint transform through the same kernels."""
+    if x.requires_grad:
+        import torch
+        if torch.is_grad_enabled():
+            from .autograd import OzFFTFunction
+            return OzFFTFunction.apply(x, FORWARD, K, L, nprimes)
+    return transform(x, FORWARD, K, L, nprimes, stream)
+
+
+def ifft(x, K=3, L=1, nprimes=2, stream=None):
+    """FP64-accurate inverse DFT (Eq. (4)); differentiable like fft."""
+    if x.requires_grad:
+        import torch
+        if torch.is_grad_enabled():
+            from .autograd import OzFFTFunction
+            return OzFFTFunction.apply(x, INVERSE, K, L, nprimes)
+    return transform(x, INVERSE, K, L, nprimes, stream)
