@@ -51,9 +51,10 @@ def parse():
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--cpu-signals", type=int, default=2, help="oracle transforms timed for cpu_baseline")
-    ap.add_argument("--workload", choices=("batch", "autograd"), default="batch",
+    ap.add_argument("--workload", choices=("batch", "autograd", "stress"), default="batch",
                     help="batch: the headline batched forward FFT; autograd: forward + backward of "
-                         "sum |FFT(x) w|^2 over 256 Gaussian signals of n = 2^16")
+                         "sum |FFT(x) w|^2 over 256 Gaussian signals of n = 2^16; stress: n = 2^20 and "
+                         "2^22, batch 8, 1%% spikes of 1e12, L = 1 (96 NTTs) vs L = 3 (64 NTTs)")
     a = ap.parse_args()
     if a.workload == "autograd":
         if "--n" not in sys.argv:
@@ -283,6 +284,82 @@ def run_autograd(a, rank, world, local):
         dist.destroy_process_group()
 
 
+# ----------------------------------------------------------------- stress workload
+def run_stress(a, rank, world, local):
+    """NTT-domain accumulation stress: batches of 8 signals of n = 2^20 and 2^22,
+    uniform [-1, 1) parts with 1% spikes of +-1e12 (every split vector needs all
+    K = 3 levels), the plain form (L = 1, 96 NTTs per transform) against the
+    accumulated form (L = 3, 64 NTTs); error of signal 0 against the binary128 FFT."""
+    import numpy as np
+    import torch
+    dist = init_dist(world)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2603_29129_gb300 import build as bld
+    if rank == 0:
+        bld.build()
+    if dist:
+        dist.barrier()
+    from paper_2603_29129_gb300 import ozfft, synth
+    import oracle
+    if rank == 0 and not a.skip_cpu:
+        oracle.build()
+    B = 8
+    stream = torch.cuda.current_stream(dev)
+    results = []
+    clocks = ClockSampler(local)
+    for lg in (20, 22):
+        n = 1 << lg
+        xh = synth.complex_signal("spikes", n, a.seed + 1000 * rank, batch=B)
+        x = torch.from_numpy(xh).to(dev)
+        y = torch.empty_like(x)
+        if rank == 0 and not a.skip_cpu:
+            hi, lo = oracle.fft_q(xh[0])
+        for L in (1, 3):
+            plan = ozfft.Plan(n, B, ozfft.FORWARD, K=a.K, L=L, nprimes=a.nprimes)
+            for _ in range(a.warmup):
+                plan.execute(x, y)
+            if dist:
+                dist.barrier()
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(a.steps):
+                plan.execute(x, y)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms = max_over_ranks(dist, e0.elapsed_time(e1), dev)
+            st = plan.stats()
+            ok = plan.status() == ozfft.OK
+            r = {"n": n, "L": L, "value": job_value(a.steps, B, world, ms), "unit": UNIT,
+                 "ms_per_step": ms / a.steps, "status_ok": ok, "alpha": st["alpha"],
+                 "ntt_per_transform_runtime": (st["ntt_forward_runtime"] + st["ntt_inverse"]) / B,
+                 "ntt_per_transform_total": (st["ntt_forward_runtime"] + st["ntt_inverse"]) / B
+                 + st["ntt_forward_plan"]}
+            if rank == 0 and not a.skip_cpu:
+                r["rel_l2_err_signal0_vs_binary128"] = oracle.rel_l2_error(y[0].cpu().numpy(), hi, lo)
+            results.append(r)
+            del plan
+    clk = clocks.stop()
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    tot_ms = sum(r["ms_per_step"] for r in results)
+    line = {"metric": "FP64-accurate Ozaki-NTT FFTs/s, accumulation stress (n=2^20, 2^22; L=1 vs L=3)",
+            "value": len(results) * B * world / (tot_ms / 1e3), "unit": UNIT, "n_gpus": world,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": tot_ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "complex128 n=2^20 and n=2^22 x 8 signals, uniform[-1,1) parts with 1% spikes "
+                                   "of +-1e12, forward, K=3, L=1 and L=3, two primes",
+                       "batch_per_gpu": B, "seed": a.seed, "parallelism": f"replicas x{world}",
+                       "l2": "inputs (8 x n x 16 B) exceed L2 each step; no flush"},
+            "results": results, "clocks": clk}
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
 # ----------------------------------------------------------------- our arm
 def main():
     a = parse()
@@ -294,6 +371,9 @@ def main():
         return
     if a.workload == "autograd":
         run_autograd(a, rank, world, local)
+        return
+    if a.workload == "stress":
+        run_stress(a, rank, world, local)
         return
 
     import numpy as np
