@@ -51,10 +51,16 @@ def parse():
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--cpu-signals", type=int, default=2, help="oracle transforms timed for cpu_baseline")
-    ap.add_argument("--workload", choices=("batch", "autograd", "stress"), default="batch",
+    ap.add_argument("--autotune", action="store_true", help="autotune the NTT column/row split at plan time")
+    ap.add_argument("--merge", action="store_true", help="merged schedules across the convolutions of a part")
+    ap.add_argument("--uneven-count", type=int, default=4096, help="signals of the uneven workload")
+    ap.add_argument("--plain-sample", type=int, default=256,
+                    help="signals of the uneven workload timed through per-signal plans")
+    ap.add_argument("--workload", choices=("batch", "autograd", "stress", "uneven"), default="batch",
                     help="batch: the headline batched forward FFT; autograd: forward + backward of "
                          "sum |FFT(x) w|^2 over 256 Gaussian signals of n = 2^16; stress: n = 2^20 and "
-                         "2^22, batch 8, 1%% spikes of 1e12, L = 1 (96 NTTs) vs L = 3 (64 NTTs)")
+                         "2^22, batch 8, 1%% spikes of 1e12, L = 1 (96 NTTs) vs L = 3 (64 NTTs); uneven: "
+                         "4096 signals of log-uniform lengths in [1000, 300000] in one plan")
     a = ap.parse_args()
     if a.workload == "autograd":
         if "--n" not in sys.argv:
@@ -70,6 +76,7 @@ def workload(a):
     return {"workload": f"complex128 n=2^{a.n.bit_length() - 1} x {a.batch} signals, uniform[-1,1) parts, "
                         f"forward, K={a.K}, L={a.L}, {a.nprimes} primes",
             "n": a.n, "batch_per_gpu": a.batch, "K": a.K, "L": a.L, "nprimes": a.nprimes, "seed": a.seed,
+            "autotune": a.autotune, "merge": a.merge,
             "l2": "inputs (batch x n x 16 B) exceed L2 each step; no flush"}
 
 
@@ -315,8 +322,8 @@ def run_stress(a, rank, world, local):
         y = torch.empty_like(x)
         if rank == 0 and not a.skip_cpu:
             hi, lo = oracle.fft_q(xh[0])
-        for L in (1, 3):
-            plan = ozfft.Plan(n, B, ozfft.FORWARD, K=a.K, L=L, nprimes=a.nprimes)
+        for L, merge in ((1, False), (3, False), (3, True)):
+            plan = ozfft.Plan(n, B, ozfft.FORWARD, K=a.K, L=L, nprimes=a.nprimes, merge=merge)
             for _ in range(a.warmup):
                 plan.execute(x, y)
             if dist:
@@ -331,7 +338,7 @@ def run_stress(a, rank, world, local):
             ms = max_over_ranks(dist, e0.elapsed_time(e1), dev)
             st = plan.stats()
             ok = plan.status() == ozfft.OK
-            r = {"n": n, "L": L, "value": job_value(a.steps, B, world, ms), "unit": UNIT,
+            r = {"n": n, "L": L, "merge": merge, "value": job_value(a.steps, B, world, ms), "unit": UNIT,
                  "ms_per_step": ms / a.steps, "status_ok": ok, "alpha": st["alpha"],
                  "ntt_per_transform_runtime": (st["ntt_forward_runtime"] + st["ntt_inverse"]) / B,
                  "ntt_per_transform_total": (st["ntt_forward_runtime"] + st["ntt_inverse"]) / B
@@ -360,6 +367,125 @@ def run_stress(a, rank, world, local):
         dist.destroy_process_group()
 
 
+# ----------------------------------------------------------------- uneven workload
+def run_uneven(a, rank, world, local):
+    """Signals of uneven lengths n = round(exp U[ln 1000, ln 300000]) (powers of
+    two redrawn), parts +-10^U[-8, 8], forward, in one ozfft_plan_many plan (length
+    classes batched, replayed as one CUDA graph, autotuned NTT splits), with L = 3
+    and L = 1; against the plain pipeline (one batch-1 plan per signal) on a
+    sample of the same signals."""
+    import numpy as np
+    import torch
+    dist = init_dist(world)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2603_29129_gb300 import build as bld
+    if rank == 0:
+        bld.build()
+    if dist:
+        dist.barrier()
+    from paper_2603_29129_gb300 import ozfft, synth
+    import oracle
+    if rank == 0 and not a.skip_cpu:
+        oracle.build()
+    cnt = a.uneven_count
+    lens = synth.uneven_lengths(cnt, 3 + 1000 * rank)
+    total = int(lens.sum())
+    xh = synth.complex_signal("loguniform", total, 3 + 1000 * rank)[0]
+    x = torch.from_numpy(xh).to(dev)
+    y = torch.empty_like(x)
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, steps):
+        for _ in range(a.warmup):
+            fn()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        if dist:
+            dist.barrier()
+        return max_over_ranks(dist, e0.elapsed_time(e1), dev)
+
+    out = {}
+    clocks = ClockSampler(local)
+    for L in (3, 1):
+        t0 = time.perf_counter()
+        plan = ozfft.PlanMany(lens, ozfft.FORWARD, K=a.K, L=L, nprimes=a.nprimes, autotune=True)
+        tplan = time.perf_counter() - t0
+        ms = timed(lambda: plan.execute(x, y), a.steps)
+        st = plan.stats()
+        r = {"value": job_value(a.steps, cnt, world, ms), "unit": "signal/s", "ms_per_step": ms / a.steps,
+             "bytes_per_s": 2 * 16 * total * world * a.steps / (ms / 1e3), "status_ok": plan.status() == ozfft.OK,
+             "plan_seconds": tplan, "workspace_GB": st["workspace_bytes"] / 1e9,
+             "ntt_runtime_per_signal": (st["ntt_forward_runtime"] + st["ntt_inverse"]) / cnt,
+             "gpu_launches_per_step": st["kernel_launches"]}
+        if rank == 0 and not a.skip_cpu:
+            yh = y.cpu().numpy()
+            xs, ys = plan.split(xh), plan.split(yh)
+            order = np.argsort(lens)
+            same, errs = True, []
+            for i in (int(order[0]), int(order[-1])):
+                yo, _ = oracle.ozfft(xs[i], K=a.K, L=L, nprimes=a.nprimes)
+                same = same and np.array_equal(yo.view(np.uint64), ys[i].view(np.uint64))
+            for i in range(0, cnt, max(1, cnt // 8)):
+                bins = np.array([0, len(xs[i]) // 3, len(xs[i]) - 1])
+                hi, lo = oracle.dft_q(xs[i], bins=bins)
+                errs.append(float(np.max(np.abs(ys[i][bins] - (hi + lo))) / np.linalg.norm(xs[i])))
+            r["bit_exact_vs_oracle"] = f"shortest and longest signal: {'yes' if same else 'NO'}"
+            r["max_sampled_bin_err_over_norm"] = max(errs)
+        out[f"L={L}"] = r
+        del plan
+    clk = clocks.stop()
+
+    # the plain pipeline: one batch-1 plan per signal, on a sample of the signals
+    m = min(a.plain_sample, cnt)
+    offs = np.concatenate([[0], np.cumsum(lens)])
+    plans = [ozfft.Plan(int(lens[i]), 1, ozfft.FORWARD, K=a.K, L=3, nprimes=a.nprimes) for i in range(m)]
+    xv = [x[offs[i]:offs[i + 1]] for i in range(m)]
+    yv = [y[offs[i]:offs[i + 1]] for i in range(m)]
+
+    def plain_step():
+        for i in range(m):
+            plans[i].execute(xv[i], yv[i])
+
+    pms = timed(plain_step, max(1, a.steps // 3))
+    psteps = max(1, a.steps // 3)
+    del plans
+    # the same sample through one uneven-length plan
+    sub = ozfft.PlanMany(lens[:m], ozfft.FORWARD, K=a.K, L=3, nprimes=a.nprimes, autotune=True)
+    xs_ = x[:offs[m]]
+    ys_ = y[:offs[m]]
+    sms = timed(lambda: sub.execute(xs_, ys_), psteps)
+    del sub
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    line = {"metric": "FP64-accurate Ozaki-NTT FFTs of uneven lengths, signals/s (one plan, CUDA graph)",
+            "value": out["L=3"]["value"], "unit": "signal/s", "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": out["L=3"]["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{cnt} complex128 signals, n log-uniform in [1000, 300000] (powers of two "
+                                   f"redrawn, seed 3), parts +-10^U[-8,8], forward, K={a.K}, L=3 (and L=1), "
+                                   f"{a.nprimes} primes", "total_elements": total,
+                       "parallelism": f"replicas x{world}",
+                       "l2": "inputs (total x 16 B) exceed L2 each step; no flush"},
+            "by_L": out,
+            "plain": {"signals": m, "value": job_value(psteps, m, world, pms), "unit": "signal/s",
+                      "executions_per_step": m},
+            "uneven_plan_same_sample": {"signals": m, "value": job_value(psteps, m, world, sms), "unit": "signal/s"},
+            "clocks": clk}
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
 # ----------------------------------------------------------------- our arm
 def main():
     a = parse()
@@ -374,6 +500,9 @@ def main():
         return
     if a.workload == "stress":
         run_stress(a, rank, world, local)
+        return
+    if a.workload == "uneven":
+        run_uneven(a, rank, world, local)
         return
 
     import numpy as np
@@ -403,7 +532,7 @@ def main():
     x = x_pin.to(dev)
     y = torch.empty_like(x)
     stream = torch.cuda.current_stream(dev)
-    plan = ozfft.Plan(n, B, ozfft.FORWARD, K=a.K, L=a.L, nprimes=a.nprimes)
+    plan = ozfft.Plan(n, B, ozfft.FORWARD, K=a.K, L=a.L, nprimes=a.nprimes, autotune=a.autotune, merge=a.merge)
 
     # ---- batched, device-resident (the headline value), with per-kernel events
     for _ in range(a.warmup):
@@ -434,7 +563,7 @@ def main():
     # ---- plain pipeline: one execution of a batch-1 plan per transform
     plain = None
     if not a.skip_plain:
-        p1 = ozfft.Plan(n, 1, ozfft.FORWARD, K=a.K, L=a.L, nprimes=a.nprimes)
+        p1 = ozfft.Plan(n, 1, ozfft.FORWARD, K=a.K, L=a.L, nprimes=a.nprimes, autotune=a.autotune, merge=a.merge)
         xs = [x[i:i + 1] for i in range(B)]
         ys = [y[i:i + 1] for i in range(B)]
         for _ in range(a.warmup):

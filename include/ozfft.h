@@ -79,6 +79,18 @@ typedef struct {
                          chunk by chunk, which bounds the inverse-NTT buffer to chunk signals
                          (default: the whole batch while that buffer fits in 16 GiB; debug plans
                          always use the whole batch) */
+    int32_t autotune; /* nonzero: at plan time, time every supported split of each NTT length
+                         into column and row passes (row tiles of 2^10 .. 2^14 residues) on the
+                         plan's own buffers and keep the fastest; results are bit-identical */
+    int32_t no_graph; /* plans over uneven lengths: nonzero runs the length classes on
+                         concurrent streams without capturing them in a CUDA graph */
+    int32_t merge;    /* nonzero: NTT-domain accumulation (§4.5) also across the two real
+                         convolutions that feed one output part (RR with -II, IR with RI): their
+                         equal-scale products share inverse NTTs, at most L per group.  With
+                         L >= 2 this cuts the inverse NTTs and CRT reads (L = 2: 36 instead of 48
+                         per transform and prime pair without gaps); the result is bit-identical
+                         to merge = 0 with the same L, since y' is the exactly rounded sum of the
+                         same products either way */
 } ozfft_options;
 
 /* Create a plan for `batch` transforms of length n in `direction`, with default
@@ -91,9 +103,27 @@ ozfft_plan_t ozfft_plan(int64_t n, int64_t batch, int direction);
 /* Same with explicit options (NULL = defaults). */
 ozfft_plan_t ozfft_plan_ex(int64_t n, int64_t batch, int direction, const ozfft_options* opt);
 
+/* A plan for `count` transforms of uneven lengths lengths[0..count) (each >= 1,
+   any mix of powers of two and other lengths), computed exactly as ozfft_plan_ex
+   would compute each signal alone (Alg. 1 around Alg. 8, §4.5; the arbitrary-
+   length case of §5.6).  Input and output are packed: signal i occupies the
+   complex128 elements [o_i, o_i + lengths[i]) with o_i = lengths[0] + ... +
+   lengths[i-1].  The signals are grouped by convolution length N; every group
+   runs batched (one launch per kernel and group, each signal's own chirp table,
+   w~* spectra and split width alpha), the groups run as concurrent branches of
+   one CUDA graph captured at plan time (or on concurrent streams with
+   opt->no_graph), and the inverse-NTT buffers of all groups together are
+   bounded by 16 GiB unless opt->chunk sets the signals per chunk.  opt->conv_len
+   and opt->debug must be 0.  ozfft_execute, ozfft_execute_host, ozfft_get_status,
+   ozfft_get_stats (n = total elements, N = the largest N, batch = count, alpha =
+   the smallest alpha) and ozfft_destroy accept the plan; profiling and
+   ozfft_debug_dump do not.  Returns NULL on error (see ozfft_last_error). */
+ozfft_plan_t ozfft_plan_many(const int64_t* lengths, int64_t count, int direction, const ozfft_options* opt);
+
 /* Transform `batch` signals: in and out are device pointers to [batch][n]
-   complex128 (in == out is allowed).  Enqueued on `stream`; nothing waits for
-   the host.  A plan must not be executed on two streams at the same time. */
+   complex128 (the packed signals of an ozfft_plan_many plan); in == out is
+   allowed.  Enqueued on `stream`; nothing waits for the host.  A plan must not
+   be executed on two streams at the same time. */
 int ozfft_execute(ozfft_plan_t plan, const void* in, void* out, void* stream);
 
 /* Same transform with HOST buffers: copies `in` to the device, transforms,

@@ -284,27 +284,48 @@ __device__ __forceinline__ bool reg_path(const CrtArgs& a, int64_t b)
     return a.P == 2 && limbs_for(a.span[b * 3], a.span[b * 3 + 1]) <= REG_LIMBS;
 }
 
-__device__ __forceinline__ void post_store(const CrtArgs& a, int64_t b, int64_t j, double yr, double yi)
+// a signal's length, chirp table and output row: the plan's (plain plans, the
+// kernel parameters themselves) or the signal's descriptor (uneven lengths)
+struct SigOut {
+    int64_t n;
+    const double2* w;
+    double2* out;
+};
+
+template <bool SD>
+__device__ __forceinline__ SigOut sig_out(const CrtArgs& a, int64_t b)
 {
-    const double2 w = a.w[j];
+    if (SD) {
+        double2* out = a.io ? a.io->out : a.out;
+        const SigDesc d = a.sd[b];
+        return {d.n, a.w + d.chirp_off, out + d.io_off};
+    }
+    return {a.n, a.w, a.out + b * a.n};
+}
+
+__device__ __forceinline__ void post_store(const CrtArgs& a, const SigOut& so, int64_t j, double yr, double yi)
+{
+    const double2 w = so.w[j];
     double re, im;
     cmul(yr, yi, w.x, w.y, re, im);
     if (a.direction > 0) im = -im;                      // inverse, adjoint: conj
     if (a.direction == 1 || a.direction == -2) {        // inverse, adjoint of the inverse: / n
-        re = __ddiv_rn(re, (double)a.n);
-        im = __ddiv_rn(im, (double)a.n);
+        re = __ddiv_rn(re, (double)so.n);
+        im = __ddiv_rn(im, (double)so.n);
     }
-    a.out[b * a.n + j] = make_double2(re, im);
+    so.out[j] = make_double2(re, im);
 }
 
 // register path: one output element per thread, integer-only accumulation
+template <bool SD>
 __global__ void __launch_bounds__(FAST_THREADS) crt_reg_kernel(CrtArgs a)
 {
     const int64_t chunks = (a.n + CRT_CHUNK - 1) / CRT_CHUNK;
     const int64_t b = blockIdx.x / chunks;
     if (!reg_path(a, b)) return;
+    const SigOut so = sig_out<SD>(a, b);
     const int64_t j0 = (blockIdx.x % chunks) * (int64_t)CRT_CHUNK;
-    const int64_t j1 = min(a.n, j0 + CRT_CHUNK);
+    const int64_t j1 = min(so.n, j0 + CRT_CHUNK);
     const Sched* sc = a.sched + b * 4;
     const int smax = a.span[b * 3 + 1], any = a.span[b * 3 + 2];
     for (int64_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
@@ -330,18 +351,19 @@ __global__ void __launch_bounds__(FAST_THREADS) crt_reg_kernel(CrtArgs a)
                             z1 = __ldg(zp + (int64_t)(g + 1) * 2 * a.N + a.N);
                         }
                         long long z = garner2(c0, c1);
-                        if (c == 1) z = -z;   // II enters the real part with a minus sign
+                        if (c == 1 && !a.merged) z = -z;   // II enters the real part with a minus sign
                         acc_add3(acc, z, smax - S.S[g]);
                     }
                 }
                 yp[part] = acc_to_double(acc, -smax);
             }
         }
-        post_store(a, b, j, yp[0], yp[1]);
+        post_store(a, so, j, yp[0], yp[1]);
     }
 }
 
 // shared-memory path: any prime count and scale span, one limb column per thread
+template <bool SD>
 __global__ void __launch_bounds__(WIDE_THREADS) crt_wide_kernel(CrtArgs a)
 {
     extern __shared__ long long acc_dyn[];
@@ -353,8 +375,9 @@ __global__ void __launch_bounds__(WIDE_THREADS) crt_wide_kernel(CrtArgs a)
             item += ((chunks - 1 - item % chunks) / gridDim.x) * gridDim.x;
             continue;
         }
+        const SigOut so = sig_out<SD>(a, b);
         const int64_t j0 = (item % chunks) * (int64_t)CRT_CHUNK;
-        const int64_t j1 = min(a.n, j0 + CRT_CHUNK);
+        const int64_t j1 = min(so.n, j0 + CRT_CHUNK);
         const Sched* sc = a.sched + b * 4;
         const int smin = a.span[b * 3 + 0], smax = a.span[b * 3 + 1], any = a.span[b * 3 + 2];
         const int nl = limbs_for(smin, smax);
@@ -378,7 +401,7 @@ __global__ void __launch_bounds__(WIDE_THREADS) crt_wide_kernel(CrtArgs a)
                             z[1] = zp[a.N];
                             z[2] = a.P > 2 ? zp[2 * a.N] : 0u;
                             i128p v = garner(z, a.P);
-                            if (c == 1) {   // II enters the real part with a minus sign
+                            if (c == 1 && !a.merged) {   // II enters the real part with a minus sign
                                 v.lo = ~v.lo + 1ull;
                                 v.hi = (long long)(~(unsigned long long)v.hi + (v.lo == 0 ? 1ull : 0ull));
                             }
@@ -388,7 +411,7 @@ __global__ void __launch_bounds__(WIDE_THREADS) crt_wide_kernel(CrtArgs a)
                     yp[part] = limbs_to_double(col, stride, nl, -smax);
                 }
             }
-            post_store(a, b, j, yp[0], yp[1]);
+            post_store(a, so, j, yp[0], yp[1]);
         }
     }
 }
@@ -408,7 +431,7 @@ static uint64_t host_powmod(uint64_t b, uint64_t e, uint64_t m)
 
 int crt_launches() { return 2; }
 
-cudaError_t launch_crt_post(const CrtArgs& a, cudaStream_t s)
+cudaError_t crt_init()
 {
     if (!s_garner_ready) {
         GarnerConst gc;
@@ -422,20 +445,32 @@ cudaError_t launch_crt_post(const CrtArgs& a, cudaStream_t s)
         if (e != cudaSuccess) return e;
         s_garner_ready = true;
     }
+    return cudaSuccess;
+}
+
+cudaError_t launch_crt_post(const CrtArgs& a, cudaStream_t s)
+{
+    cudaError_t e = crt_init();
+    if (e != cudaSuccess) return e;
     const int64_t chunks = (a.n + CRT_CHUNK - 1) / CRT_CHUNK;
-    crt_reg_kernel<<<(unsigned)(a.B * chunks), FAST_THREADS, 0, s>>>(a);
-    cudaError_t e = cudaGetLastError();
+    const bool sd = a.sd != nullptr;
+    if (sd) crt_reg_kernel<true><<<(unsigned)(a.B * chunks), FAST_THREADS, 0, s>>>(a);
+    else crt_reg_kernel<false><<<(unsigned)(a.B * chunks), FAST_THREADS, 0, s>>>(a);
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     // signals with three primes or a wide scale span: small blocks, limb columns in shared memory
     const size_t smem = sizeof(long long) * WIDE_LIMBS * WIDE_THREADS;
     static bool attr = false;
     if (!attr) {
-        e = cudaFuncSetAttribute(crt_wide_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaFuncSetAttribute(crt_wide_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(crt_wide_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         attr = true;
     }
     const int64_t grid = a.B * chunks < 1024 ? a.B * chunks : 1024;
-    crt_wide_kernel<<<(unsigned)grid, WIDE_THREADS, smem, s>>>(a);
+    if (sd) crt_wide_kernel<true><<<(unsigned)grid, WIDE_THREADS, smem, s>>>(a);
+    else crt_wide_kernel<false><<<(unsigned)grid, WIDE_THREADS, smem, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -120,46 +120,67 @@ __device__ __forceinline__ void block_umax_to(uint64_t* dst, uint64_t v)
     }
 }
 
+// w~* of every signal: vector v = 2 b + part holds Re (part 0) or Im (part 1)
+// of ZeroPad+-(conj w_b, N) (cyclic, w~* = conj w, when N = n)
 __global__ void __launch_bounds__(SPLIT_THREADS) wstar_kernel(const double2* __restrict__ w, int64_t n, int64_t N,
+                                                              const SigDesc* __restrict__ sd,
                                                               double* __restrict__ r, uint64_t* __restrict__ mu, int K)
 {
     const int64_t chunks = (N + CHUNK - 1) / CHUNK;
-    const int v = (int)(blockIdx.x / chunks);
+    const int64_t v = blockIdx.x / chunks;
+    const int part = (int)(v & 1);
     const int64_t j0 = (blockIdx.x % chunks) * CHUNK;
     const int64_t j1 = min(N, j0 + CHUNK);
+    int64_t nb = n;
+    if (sd) {
+        const SigDesc d = sd[v >> 1];
+        nb = d.n;
+        w += d.chirp_off;
+    }
     uint64_t m = 0;
     for (int64_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
         int64_t src = -1;
-        if (j < n) src = j;
-        else if (N != n && j >= N - n + 1) src = N - j;
+        if (j < nb) src = j;
+        else if (N != nb && j >= N - nb + 1) src = N - j;
         double val = 0.0;
         if (src >= 0) {
             const double2 ws = w[src];
-            val = v == 0 ? ws.x : -ws.y;   // conj(w)
+            val = part == 0 ? ws.x : -ws.y;   // conj(w)
         }
-        r[(int64_t)v * N + j] = val;
+        r[v * N + j] = val;
         m = umax64(m, (uint64_t)__double_as_longlong(val) & 0x7fffffffffffffffull);
     }
-    block_umax_to(&mu[(int64_t)v * (K + 1) + 0], m);
+    block_umax_to(&mu[v * (K + 1) + 0], m);
 }
 
 __global__ void __launch_bounds__(SPLIT_THREADS) premul_kernel(const double2* __restrict__ x,
                                                                const double2* __restrict__ w, int64_t n, int64_t N,
-                                                               int conj_in, double* __restrict__ r,
+                                                               int conj_in, const SigDesc* __restrict__ sd,
+                                                               const IoPtrs* __restrict__ io, double* __restrict__ r,
                                                                uint64_t* __restrict__ mu, int K, int* status)
 {
     const int64_t chunks = (N + CHUNK - 1) / CHUNK;
     const int64_t b = blockIdx.x / chunks;
     const int64_t j0 = (blockIdx.x % chunks) * CHUNK;
     const int64_t j1 = min(N, j0 + CHUNK);
+    if (io) x = io->in;
+    int64_t nb = n;
+    if (sd) {
+        const SigDesc d = sd[b];
+        nb = d.n;
+        x += d.io_off;
+        w += d.chirp_off;
+    } else {
+        x += b * n;
+    }
     uint64_t mr = 0, mi = 0;   // bit patterns of |.|: non-negative doubles order like their bits
     bool bad = false;
     double* rr = r + (2 * b) * N;
     double* ri = rr + N;
     for (int64_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
         double re = 0.0, im = 0.0;
-        if (j < n) {
-            const double2 xv = x[b * n + j];
+        if (j < nb) {
+            const double2 xv = x[j];
             const double2 wv = w[j];
             const double xi = conj_in ? -xv.y : xv.y;
             if (!isfinite(xv.x) || !isfinite(xv.y)) bad = true;
@@ -174,6 +195,12 @@ __global__ void __launch_bounds__(SPLIT_THREADS) premul_kernel(const double2* __
     block_umax_to(&mu[(2 * b) * (K + 1)], mr);
     __syncthreads();
     block_umax_to(&mu[(2 * b + 1) * (K + 1)], mi);
+}
+
+__global__ void set_io_kernel(IoPtrs* io, const double2* in, double2* out)
+{
+    io->in = in;
+    io->out = out;
 }
 
 // One level of Alg. 3 on one element, from its bit pattern, in integer
@@ -229,13 +256,15 @@ __device__ __forceinline__ void split_level_int(uint64_t rb, int e, int alpha, l
 // Level k of Alg. 3 for every vector: q = s 2^(alpha - e) with |q| <= 2^alpha,
 // residues q mod p written per prime, the residual written back for the next
 // level and its maximum reduced into mu[v][k+1].
+template <bool SD>
 __global__ void __launch_bounds__(SPLIT_THREADS) split_kernel(int k, double* __restrict__ r,
                                                               uint64_t* __restrict__ mu, int64_t N, int K,
-                                                              int alpha, int P, uint32_t* __restrict__ X,
-                                                              int write_r, int* status)
+                                                              int alpha, const SigDesc* __restrict__ sd, int P,
+                                                              uint32_t* __restrict__ X, int write_r, int* status)
 {
     const int64_t chunks = (N + CHUNK - 1) / CHUNK;
     const int64_t v = blockIdx.x / chunks;
+    if (SD) alpha = sd[v >> 1].alpha;                     // vector v = 2 b + part
     const int64_t j0 = (blockIdx.x % chunks) * CHUNK;
     const int64_t j1 = min(N, j0 + CHUNK);
     const uint64_t mub = mu[v * (K + 1) + k];
@@ -277,23 +306,33 @@ cudaError_t launch_chirp(double2* w, int64_t n, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_wstar(const double2* w, int64_t n, int64_t N, double* r, uint64_t* mu, int K, int*, cudaStream_t s)
+cudaError_t launch_wstar(const double2* w, int64_t n, int64_t N, int64_t B, const SigDesc* sd, double* r, uint64_t* mu,
+                         int K, int*, cudaStream_t s)
 {
-    wstar_kernel<<<grid_for(2, N), SPLIT_THREADS, 0, s>>>(w, n, N, r, mu, K);
+    wstar_kernel<<<grid_for(2 * B, N), SPLIT_THREADS, 0, s>>>(w, n, N, sd, r, mu, K);
     return cudaGetLastError();
 }
 
-cudaError_t launch_premul(const double2* x, const double2* w, int64_t n, int64_t N, int64_t B, int conj_in, double* r,
-                          uint64_t* mu, int K, int* status, cudaStream_t s)
+cudaError_t launch_premul(const double2* x, const double2* w, int64_t n, int64_t N, int64_t B, int conj_in,
+                          const SigDesc* sd, const IoPtrs* io, double* r, uint64_t* mu, int K, int* status,
+                          cudaStream_t s)
 {
-    premul_kernel<<<grid_for(B, N), SPLIT_THREADS, 0, s>>>(x, w, n, N, conj_in, r, mu, K, status);
+    premul_kernel<<<grid_for(B, N), SPLIT_THREADS, 0, s>>>(x, w, n, N, conj_in, sd, io, r, mu, K, status);
     return cudaGetLastError();
 }
 
 cudaError_t launch_split_level(int k, double* r, const uint64_t*, uint64_t* mu, int64_t N, int64_t nvec, int K,
-                               int alpha, int P, uint32_t* X, int write_r, int* status, cudaStream_t s)
+                               int alpha, const SigDesc* sd, int P, uint32_t* X, int write_r, int* status,
+                               cudaStream_t s)
 {
-    split_kernel<<<grid_for(nvec, N), SPLIT_THREADS, 0, s>>>(k, r, mu, N, K, alpha, P, X, write_r, status);
+    if (sd) split_kernel<true><<<grid_for(nvec, N), SPLIT_THREADS, 0, s>>>(k, r, mu, N, K, alpha, sd, P, X, write_r, status);
+    else split_kernel<false><<<grid_for(nvec, N), SPLIT_THREADS, 0, s>>>(k, r, mu, N, K, alpha, sd, P, X, write_r, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_io(IoPtrs* io, const void* in, void* out, cudaStream_t s)
+{
+    set_io_kernel<<<1, 1, 0, s>>>(io, (const double2*)in, (double2*)out);
     return cudaGetLastError();
 }
 

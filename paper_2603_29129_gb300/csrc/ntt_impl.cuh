@@ -225,15 +225,22 @@ __global__ void __launch_bounds__(NTT_THREADS, 8) ntt_col_kernel(NttGeom g, uint
 
 // ------------------------------------------------------------------- row pass
 // Decoded flush group of one inverse vector (for the fused MAC): X_s lives at
-// xbase + s * step and Ym_t at ybase + t * step (step = P N elements).
+// xbase + s * step and Ym_t at ybase + t * step (step = P N elements); Ym is
+// shared by the batch, or per signal (ym_stride apart) in a plan over uneven
+// lengths.  In a merged schedule a group holds products of both convolutions
+// of one output part (RR and II, or IR and RI): each product names its
+// convolution, which picks Re or Im of x~' and of w~* (vstride apart), and
+// the II products enter with a minus sign.
 struct MacVec {
     int n;                     // products (0: empty group)
-    uint32_t st[2];            // (s, t) nibbles of up to 8 products
-    int64_t xbase, ybase, step;
+    uint32_t st0, st1;         // (s, t) bytes of products 0..3 and 4..7
+    uint32_t cv;               // merged groups: convolution of each product, 2 bits each
+    int64_t xbase, ybase, step, vstride;
     uint32_t p, pn;
+    bool merged;
 };
 
-__device__ __forceinline__ MacVec mac_decode(const NttGeom& g, unsigned vec)
+__device__ __forceinline__ MacVec mac_decode(const NttGeom& g, unsigned vec, int64_t ym_stride)
 {
     MacVec m;
     const int pi = (int)(vec % (unsigned)g.P);
@@ -243,51 +250,85 @@ __device__ __forceinline__ MacVec mac_decode(const NttGeom& g, unsigned vec)
     const int conv = (int)(bc & 3u);
     const unsigned b = bc >> 2;
     const Sched& S = g.sched[bc];
-    const int vx = (conv == 0 || conv == 3) ? 0 : 1;   // RR, RI use Re x'; II, IR use Im x'
-    const int vw = (conv == 0 || conv == 2) ? 0 : 1;   // RR, IR use Re w*; II, RI use Im w*
+    m.merged = g.merged != 0;
+    const int vx = m.merged ? 0 : ((conv == 0 || conv == 3) ? 0 : 1);   // RR, RI use Re x'; II, IR use Im x'
+    const int vw = m.merged ? 0 : ((conv == 0 || conv == 2) ? 0 : 1);   // RR, IR use Re w*; II, RI use Im w*
     m.n = grp < S.ngroups ? S.size[grp] : 0;
-    m.st[0] = m.st[1] = 0u;
-    for (int k = 0; k < m.n; ++k) m.st[k >> 2] |= (uint32_t)(S.pair[grp][k] & 0xff) << (8 * (k & 3));
+    m.st0 = m.st1 = m.cv = 0u;
+    for (int k = 0; k < m.n; ++k) {
+        const int32_t pr = S.pair[grp][k];
+        const uint32_t byte = (uint32_t)(pr & 0xff) << (8 * (k & 3));
+        if (k < 4) m.st0 |= byte;
+        else m.st1 |= byte;
+        m.cv |= (uint32_t)((pr >> 8) & 3) << (2 * k);
+    }
     m.step = (int64_t)g.P * g.N;
+    m.vstride = (int64_t)g.K * g.P * g.N;
     m.xbase = (((int64_t)b * 2 + vx) * g.K * g.P + pi) * g.N;
-    m.ybase = ((int64_t)vw * g.K * g.P + pi) * g.N;
+    m.ybase = ((int64_t)vw * g.K * g.P + pi) * g.N + (int64_t)b * ym_stride;
     m.p = prime_of(pi);
     m.pn = pneg_inv_of(pi);
     return m;
 }
 
-__device__ __forceinline__ void mac_offsets(const MacVec& m, int k, int64_t& xo, int64_t& yo)
+// offsets of product k's X_s and Ym_t; in a merged group also the Re/Im choice
+// of its convolution, and whether it enters with a minus sign (II)
+template <bool MERGED>
+__device__ __forceinline__ bool mac_offsets(const MacVec& m, int k, int64_t& xo, int64_t& yo)
 {
-    const uint32_t pr = (m.st[k >> 2] >> (8 * (k & 3))) & 0xffu;
+    const uint32_t pr = ((k < 4 ? m.st0 : m.st1) >> (8 * (k & 3))) & 0xffu;
     xo = m.xbase + (int64_t)(pr >> 4) * m.step;
     yo = m.ybase + (int64_t)(pr & 15u) * m.step;
+    if (!MERGED) return false;
+    const uint32_t c = (m.cv >> (2 * k)) & 3u;
+    if (c == 1u || c == 2u) xo += m.vstride;   // II, IR: Im x'
+    if (c == 1u || c == 3u) yo += m.vstride;   // II, RI: Im w*
+    return c == 1u;                            // II enters the real part with a minus sign
+}
+
+template <bool MERGED>
+__device__ __forceinline__ uint4 mac_sum4(const MacVec& m, const MacSrc& mac, int64_t j)
+{
+    uint32_t a0 = 0u, a1 = 0u, a2 = 0u, a3 = 0u;
+    for (int k = 0; k < m.n; ++k) {
+        int64_t xo, yo;
+        const bool neg = mac_offsets<MERGED>(m, k, xo, yo);
+        const uint4 x = __ldg(reinterpret_cast<const uint4*>(mac.X + xo + j));
+        const uint4 y = __ldg(reinterpret_cast<const uint4*>(mac.Ym + yo + j));
+        const uint32_t t0 = mont_mul(x.x, y.x, m.p, m.pn), t1 = mont_mul(x.y, y.y, m.p, m.pn);
+        const uint32_t t2 = mont_mul(x.z, y.z, m.p, m.pn), t3 = mont_mul(x.w, y.w, m.p, m.pn);
+        if (MERGED && neg) {
+            a0 = mod_sub(a0, t0, m.p); a1 = mod_sub(a1, t1, m.p);
+            a2 = mod_sub(a2, t2, m.p); a3 = mod_sub(a3, t3, m.p);
+        } else {
+            a0 = mod_add(a0, t0, m.p); a1 = mod_add(a1, t1, m.p);
+            a2 = mod_add(a2, t2, m.p); a3 = mod_add(a3, t3, m.p);
+        }
+    }
+    return make_uint4(a0, a1, a2, a3);
 }
 
 __device__ __forceinline__ uint4 mac_load4(const MacVec& m, const MacSrc& mac, int64_t j)
 {
-    uint32_t acc[4] = {0u, 0u, 0u, 0u};
-    for (int k = 0; k < m.n; ++k) {
-        int64_t xo, yo;
-        mac_offsets(m, k, xo, yo);
-        const uint4 x = __ldg(reinterpret_cast<const uint4*>(mac.X + xo + j));
-        const uint4 y = __ldg(reinterpret_cast<const uint4*>(mac.Ym + yo + j));
-        acc[0] = mod_add(acc[0], mont_mul(x.x, y.x, m.p, m.pn), m.p);
-        acc[1] = mod_add(acc[1], mont_mul(x.y, y.y, m.p, m.pn), m.p);
-        acc[2] = mod_add(acc[2], mont_mul(x.z, y.z, m.p, m.pn), m.p);
-        acc[3] = mod_add(acc[3], mont_mul(x.w, y.w, m.p, m.pn), m.p);
-    }
-    return make_uint4(acc[0], acc[1], acc[2], acc[3]);
+    return m.merged ? mac_sum4<true>(m, mac, j) : mac_sum4<false>(m, mac, j);
 }
 
-__device__ __forceinline__ uint32_t mac_load1(const MacVec& m, const MacSrc& mac, int64_t j)
+template <bool MERGED>
+__device__ __forceinline__ uint32_t mac_sum1(const MacVec& m, const MacSrc& mac, int64_t j)
 {
     uint32_t acc = 0u;
     for (int k = 0; k < m.n; ++k) {
         int64_t xo, yo;
-        mac_offsets(m, k, xo, yo);
-        acc = mod_add(acc, mont_mul(__ldg(mac.X + xo + j), __ldg(mac.Ym + yo + j), m.p, m.pn), m.p);
+        const bool neg = mac_offsets<MERGED>(m, k, xo, yo);
+        const uint32_t t = mont_mul(__ldg(mac.X + xo + j), __ldg(mac.Ym + yo + j), m.p, m.pn);
+        acc = (MERGED && neg) ? mod_sub(acc, t, m.p) : mod_add(acc, t, m.p);
     }
     return acc;
+}
+
+__device__ __forceinline__ uint32_t mac_load1(const MacVec& m, const MacSrc& mac, int64_t j)
+{
+    return m.merged ? mac_sum1<true>(m, mac, j) : mac_sum1<false>(m, mac, j);
 }
 
 template <bool INV, bool MAC, int M2>
@@ -311,7 +352,7 @@ __global__ void __launch_bounds__(NTT_THREADS, 8) ntt_row_kernel(NttGeom g, uint
         const int64_t j0 = gbase - ((int64_t)vec << g.lgN);   // offset inside the vector
         if (nel >= 4) {
             if (MAC) {
-                const MacVec mv = mac_decode(g, vec);
+                const MacVec mv = mac_decode(g, vec, mac.ym_stride);
                 for (int q = threadIdx.x; q < (nel >> 2); q += blockDim.x) {
                     const uint4 t = mac_load4(mv, mac, j0 + 4 * q);
                     uint32_t* s = sm + pad_idx(4 * q);
@@ -325,7 +366,7 @@ __global__ void __launch_bounds__(NTT_THREADS, 8) ntt_row_kernel(NttGeom g, uint
                 }
             }
         } else {
-            const MacVec mv = MAC ? mac_decode(g, vec) : MacVec{};
+            const MacVec mv = MAC ? mac_decode(g, vec, mac.ym_stride) : MacVec{};
             for (int i = threadIdx.x; i < nel; i += blockDim.x)
                 sm[pad_idx(i)] = MAC ? mac_load1(mv, mac, j0 + i) : data[gbase + i];
         }
@@ -342,7 +383,7 @@ __global__ void __launch_bounds__(NTT_THREADS, 8) ntt_row_kernel(NttGeom g, uint
         for (int r = 0; r < rows; ++r) {
             const unsigned vec = (unsigned)(row0 + r);
             if (MAC) {
-                const MacVec mv = mac_decode(g, vec);
+                const MacVec mv = mac_decode(g, vec, mac.ym_stride);
                 for (int l = threadIdx.x; l < M; l += blockDim.x) sm[pad_idx((r << M2) + l)] = mac_load1(mv, mac, l);
             } else {
                 for (int l = threadIdx.x; l < M; l += blockDim.x)

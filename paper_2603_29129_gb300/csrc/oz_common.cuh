@@ -32,7 +32,7 @@ struct Sched {
     int32_t ngroups;
     int32_t S[MAX_GROUPS];           // s_x + s_y: the group's products carry 1/(c_x c_y) = 2^-S
     int32_t size[MAX_GROUPS];        // products in the group (<= L)
-    int32_t pair[MAX_GROUPS][MAX_L]; // s * 16 + t
+    int32_t pair[MAX_GROUPS][MAX_L]; // s * 16 + t; merged schedules add conv * 256
 };
 
 // The moduli: p0, p1 of §5.1 and a third NTT-friendly prime 15 * 2^27 + 1.

@@ -8,6 +8,26 @@
 
 namespace oz {
 
+// Per-signal layout of a plan over signals of uneven lengths.  Such a plan is
+// cut into length classes (one convolution length N each); a class's kernels
+// read its signals' descriptors.  Plans whose signals all have one length pass
+// null and use the plan's n.
+struct SigDesc {
+    int64_t n;          // signal length
+    int64_t io_off;     // first element of the signal in the packed input and output
+    int64_t chirp_off;  // first entry of its chirp table w(0..n) in the class's chirp pool
+    int32_t alpha;      // split width of this n (§4.4)
+    int32_t pad;
+};
+
+// Input and output base pointers held in device memory, so that a captured
+// CUDA graph reads the buffers of the current execution (null: use the
+// pointers passed to the launch).
+struct IoPtrs {
+    const double2* in;
+    double2* out;
+};
+
 // Geometry of one batched NTT launch (forward or inverse).
 struct NttGeom {
     int64_t N;          // transform length 2^lgN
@@ -18,16 +38,21 @@ struct NttGeom {
     int P, K, G;        // primes, split cap, flush-group capacity
     const int32_t* kcnt;   // [B][2] live split levels of x~' (forward skip test)
     const Sched* sched;    // [B][4] flush schedules (inverse skip test and MAC)
+    int merged;            // schedules merge the two convolutions of each output part
 };
 
 // Inputs of the multiply-accumulate fused into the inverse NTT's load.
 struct MacSrc {
     const uint32_t* X;   // [B][2][K][P][N] forward spectra of x~' slices
-    const uint32_t* Ym;  // [2][K][P][N]   w~* spectra * N^-1 * 2^32 mod p
+    const uint32_t* Ym;  // [2][K][P][N]   w~* spectra * N^-1 * 2^32 mod p (per signal when ym_stride > 0)
+    int64_t ym_stride;   // elements between consecutive signals' Ym (0: one Ym for the whole batch)
 };
 
 // k_ntt.cu
 void ntt_configure(NttGeom& g, int64_t N);   // fills lgN, m1, m2, T, rows_per_cta
+// the same with the row pass forced to 2^m2 residues (autotuning); false when
+// no kernel instantiation covers that split
+bool ntt_configure_split(NttGeom& g, int64_t N, int m2);
 int64_t ntt_launches(const NttGeom& g);        // kernels per transform direction
 // one pass each; a transform is col+row (forward) or row+col (inverse), the
 // column pass only when g.m1 > 0
@@ -38,27 +63,35 @@ cudaError_t launch_ntt_inv_col(const NttGeom& g, uint32_t* Z, const uint2* twinv
 cudaError_t launch_ntt_forward(const NttGeom& g, uint32_t* X, const uint2* tw, cudaStream_t s);
 
 // k_split.cu
+// sd (optional, [B]): per-signal lengths, offsets and split widths; io
+// (optional): device-held input/output pointers
 cudaError_t launch_chirp(double2* w, int64_t n, cudaStream_t s);
-cudaError_t launch_wstar(const double2* w, int64_t n, int64_t N, double* r, uint64_t* mu, int K, int* status,
-                         cudaStream_t s);
+cudaError_t launch_wstar(const double2* w, int64_t n, int64_t N, int64_t B, const SigDesc* sd, double* r,
+                         uint64_t* mu, int K, int* status, cudaStream_t s);
 cudaError_t launch_premul(const double2* x, const double2* w, int64_t n, int64_t N, int64_t B, int conj_in,
-                          double* r, uint64_t* mu, int K, int* status, cudaStream_t s);
+                          const SigDesc* sd, const IoPtrs* io, double* r, uint64_t* mu, int K, int* status,
+                          cudaStream_t s);
 cudaError_t launch_split_level(int k, double* r, const uint64_t* mu_in, uint64_t* mu_out, int64_t N,
-                               int64_t nvec, int K, int alpha, int P, uint32_t* X, int write_r, int* status,
-                               cudaStream_t s);
+                               int64_t nvec, int K, int alpha, const SigDesc* sd, int P, uint32_t* X, int write_r,
+                               int* status, cudaStream_t s);
+cudaError_t launch_set_io(IoPtrs* io, const void* in, void* out, cudaStream_t s);
 
 // k_crt.cu
 struct CrtArgs {
     const uint32_t* Z;     // [B][4][G][P][N] inverse NTT outputs (natural order)
     const Sched* sched;    // [B][4]
     const int32_t* span;   // [B][3] min S, max S, any group
-    const double2* w;      // [n] chirp
-    double2* out;          // [B][n]
-    int64_t n, N, B;
+    const double2* w;      // [n] chirp (a chirp pool with per-signal offsets when sd is set)
+    double2* out;          // [B][n] (packed per-signal offsets when sd is set)
+    int64_t n, N, B;       // n: the signals' length (their largest when sd is set)
     int P, G, direction;
     int* status;           // data-dependent status bits
+    const SigDesc* sd;     // [B] per-signal lengths and offsets, or null
+    const IoPtrs* io;      // device-held output pointer, or null
+    int merged;            // merged schedules: the MAC already applied the sign of II
 };
 int crt_launches();        // kernels per launch_crt_post
+cudaError_t crt_init();    // uploads the Garner constants (once; call before any stream capture)
 cudaError_t launch_crt_post(const CrtArgs& a, cudaStream_t s);
 
 }  // namespace oz

@@ -48,7 +48,7 @@ static int fail(int code, const std::string& msg)
 
 struct ozfft_plan_s {
     int64_t n = 0, N = 0, B = 0;
-    int direction = -1, K = 3, L = 1, P = 2, alpha = 0, G = 9, debug = 0;
+    int direction = -1, K = 3, L = 1, P = 2, alpha = 0, G = 9, debug = 0, merge = 0;
     int64_t chunk = 1;           // signals per inverse-stage chunk (Z holds one chunk)
     int device = 0;
     NttGeom geom_fwd{}, geom_inv{};
@@ -74,6 +74,22 @@ struct ozfft_plan_s {
     double2* stage_in = nullptr; // host-buffer execution staging [B][n]
     double2* stage_out = nullptr;
     bool executed = false;
+    int64_t total = 0;           // complex elements per execution (B n, or the packed lengths)
+    int64_t fwd_plan = 0;        // forward NTTs of the w~* slices
+    // one length class of a plan over uneven lengths: per-signal layout
+    std::vector<SigDesc> sd_host;
+    SigDesc* sd = nullptr;       // [B] device
+    int64_t ym_stride = 0;       // Ym per signal (elements), 0: one Ym for the batch
+    const IoPtrs* io_ref = nullptr;  // the parent's device-held in/out pointers
+    // a plan over uneven lengths: its length classes and their execution
+    std::vector<ozfft_plan_s*> classes;
+    IoPtrs* io = nullptr;        // device
+    std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> joins;
+    cudaEvent_t fork = nullptr;
+    cudaStream_t capture = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
     // per-kernel timing: each execution leaves a start event and one event per kernel
     bool profiling = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -162,15 +178,32 @@ static int ceil_log2_h(double mu)
 
 // ------------------------------------------------------------ small kernels
 // Alg. 8 flush schedules of every signal's four real convolutions: the x~'
-// split levels and scales come from mu, those of w~* from the plan.  One
-// thread per signal; it also records the signal's scale span over all groups
-// (span[b] = {min S, max S, any group}) for the exact accumulation.
+// split levels and scales come from mu, those of w~* from the plan (per
+// signal in a length class of a plan over uneven lengths, where sd gives each
+// signal's alpha).  One thread per signal; it also records the signal's scale
+// span over all groups (span[b] = {min S, max S, any group}) for the exact
+// accumulation.
+//
+// Merged schedules (merge != 0) extend Alg. 8's accumulation across the two
+// convolutions that feed one output part (RR and II into the real part, IR and
+// RI into the imaginary part): the identity that lets products of equal scale
+// share an inverse NTT holds for any products whose results are summed, so the
+// products of both convolutions are ordered by scale (anti-diagonal order
+// within a scale) and cut into groups of at most L equal-scale products, II
+// products carrying a minus sign.  Part q keeps its groups in the slots of
+// convolutions 2q (first G groups) and 2q + 1 (the rest).
 __global__ void schedule_kernel(const uint64_t* __restrict__ mu, int64_t B, int K, int L, int alpha,
-                                const int32_t* __restrict__ wk, const int32_t* __restrict__ wsexp,
-                                Sched* __restrict__ sched, int32_t* __restrict__ kcnt, int32_t* __restrict__ span)
+                                const SigDesc* __restrict__ sd, const int32_t* __restrict__ wk,
+                                const int32_t* __restrict__ wsexp, Sched* __restrict__ sched,
+                                int32_t* __restrict__ kcnt, int32_t* __restrict__ span, int merge)
 {
     const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (b >= B) return;
+    if (sd) {
+        alpha = sd[b].alpha;
+        wk += 2 * b;
+        wsexp += 2 * K * b;
+    }
     int sx[2][MAX_K];
     int kxv[2];
     for (int v = 0; v < 2; ++v) {
@@ -184,6 +217,54 @@ __global__ void schedule_kernel(const uint64_t* __restrict__ mu, int64_t B, int 
         kcnt[b * 2 + v] = kx;
     }
     int smin = 0, smax = 0, any = 0;
+    if (merge) {
+        const int G = K * K;
+        for (int part = 0; part < 2; ++part) {
+            int ps[2 * MAX_K * MAX_K], pp[2 * MAX_K * MAX_K];
+            int np = 0;
+            for (int k = 2 * K - 2; k >= 0; --k)
+                for (int c = 2 * part; c < 2 * part + 2; ++c) {
+                    const int vx = (c == 0 || c == 3) ? 0 : 1;
+                    const int vw = (c == 0 || c == 2) ? 0 : 1;
+                    const int kx = kxv[vx], ky = wk[vw];
+                    const int s0 = max(0, k - ky + 1), s1 = min(kx - 1, k);
+                    for (int s = s0; s <= s1; ++s) {
+                        const int t = k - s;
+                        const int sc = sx[vx][s] + wsexp[vw * K + t];
+                        int i = np++;   // stable insertion by descending scale
+                        while (i > 0 && ps[i - 1] < sc) {
+                            ps[i] = ps[i - 1];
+                            pp[i] = pp[i - 1];
+                            --i;
+                        }
+                        ps[i] = sc;
+                        pp[i] = c * 256 + s * 16 + t;
+                    }
+                }
+            int g = 0, l = 0;
+            for (int i = 0; i < np; ++i) {
+                if (i > 0 && (l >= L || ps[i] != ps[i - 1])) {
+                    ++g;
+                    l = 0;
+                }
+                Sched& S = sched[b * 4 + 2 * part + g / G];
+                S.S[g % G] = ps[i];
+                S.pair[g % G][l] = pp[i];
+                ++l;
+                S.size[g % G] = l;
+                smin = any ? min(smin, ps[i]) : ps[i];
+                smax = any ? max(smax, ps[i]) : ps[i];
+                any = 1;
+            }
+            const int ng = np > 0 ? g + 1 : 0;
+            sched[b * 4 + 2 * part].ngroups = min(ng, G);
+            sched[b * 4 + 2 * part + 1].ngroups = max(ng - G, 0);
+        }
+        span[b * 3 + 0] = smin;
+        span[b * 3 + 1] = smax;
+        span[b * 3 + 2] = any;
+        return;
+    }
     for (int c = 0; c < 4; ++c) {
         const int vx = (c == 0 || c == 3) ? 0 : 1;
         const int vw = (c == 0 || c == 2) ? 0 : 1;
@@ -234,9 +315,16 @@ __global__ void ymont_kernel(uint32_t* Y, int64_t N, int64_t total, int P, uint3
 static void plan_free(ozfft_plan_s* p)
 {
     void* ptrs[] = {p->chirp, p->tw, p->twinv, p->Ym, p->wk, p->wsexp, p->r, p->mu, p->X, p->kcnt, p->sched,
-                    p->span, p->Z, p->status, p->dbg_r, p->dbg_X, p->stage_in, p->stage_out};
+                    p->span, p->Z, p->status, p->dbg_r, p->dbg_X, p->stage_in, p->stage_out, p->sd, p->io};
     for (void* q : ptrs)
         if (q) cudaFree(q);
+    for (ozfft_plan_s* c : p->classes) plan_free(c);
+    if (p->gexec) cudaGraphExecDestroy(p->gexec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    for (cudaStream_t st : p->streams) cudaStreamDestroy(st);
+    for (cudaEvent_t e : p->joins) cudaEventDestroy(e);
+    if (p->fork) cudaEventDestroy(p->fork);
+    if (p->capture) cudaStreamDestroy(p->capture);
     for (auto& r : p->pending) {
         p->ev_pool.push_back(r.start);
         for (auto& m : r.marks) p->ev_pool.push_back(m.second);
@@ -260,20 +348,74 @@ static int dalloc(ozfft_plan_s* p, T** ptr, size_t count)
     return OZFFT_OK;
 }
 
+// twiddle tables, one per prime and direction: w_N = g^((p-1)/N) (inverse:
+// w_N^-1); entry 2^s + i = w^((N/2^(s+1)) bitrev_s(i)) with its Shoup
+// quotient, for the block-i butterflies of stage s (k_ntt.cu)
+static int build_twiddles(ozfft_plan_s* p)
+{
+    const int64_t N = p->N;
+    const int P = p->P;
+    std::vector<uint2> t((size_t)P * N), ti((size_t)P * N);
+    std::vector<uint64_t> pw(N > 1 ? N / 2 : 1), pwi(N > 1 ? N / 2 : 1);
+    int lg = 0;
+    while ((int64_t(1) << lg) < N) ++lg;
+    for (int i = 0; i < P; ++i) {
+        const uint64_t pr = prime_of(i);
+        const uint64_t w = powmod_h(primitive_root_h(pr), (pr - 1) / (uint64_t)N, pr);
+        const uint64_t wi = powmod_h(w, pr - 2, pr);
+        pw[0] = pwi[0] = 1;
+        for (int64_t e = 1; e < N / 2; ++e) {
+            pw[e] = mulmod_h(pw[e - 1], w, pr);
+            pwi[e] = mulmod_h(pwi[e - 1], wi, pr);
+        }
+        auto entry = [&](uint64_t a) { return make_uint2((uint32_t)a, (uint32_t)((a << 32) / pr)); };
+        uint2* ti_ = &ti[(size_t)i * N];
+        uint2* t_ = &t[(size_t)i * N];
+        t_[0] = ti_[0] = entry(1);
+        for (int s = 0; s < lg; ++s) {
+            const int64_t m = int64_t(1) << s;
+            for (int64_t b = 0; b < m; ++b) {
+                int64_t r = 0;
+                for (int k = 0; k < s; ++k)
+                    if (b >> k & 1) r |= int64_t(1) << (s - 1 - k);
+                const int64_t e = (N / (2 * m)) * r;
+                t_[m + b] = entry(pw[e]);
+                ti_[m + b] = entry(pwi[e]);
+            }
+        }
+    }
+    CUDA_TRY(cudaMemcpy(p->tw, t.data(), sizeof(uint2) * t.size(), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(p->twinv, ti.data(), sizeof(uint2) * ti.size(), cudaMemcpyHostToDevice));
+    return OZFFT_OK;
+}
+
+// Tables and workspace of a plan.  A length class of a plan over uneven
+// lengths (sd_host set) has one chirp table, w~* split and w~* spectra per
+// signal; a plain plan has one of each for the batch.
 static int plan_build(ozfft_plan_s* p)
 {
     const int64_t N = p->N, B = p->B;
     const int K = p->K, P = p->P;
+    const bool uneven = !p->sd_host.empty();
+    const int64_t BW = uneven ? B : 1;           // signals with their own w~*
     int rc;
     CUDA_TRY(cudaGetDevice(&p->device));
     for (int i = 0; i < P; ++i)
         if ((uint32_t)(prime_of(i) * pneg_inv_of(i)) != 0xffffffffu) return fail(OZFFT_ERR_ARG, "Montgomery constant");
-    if ((rc = dalloc(p, &p->chirp, p->n))) return rc;
+    int64_t nchirp = p->n;
+    if (uneven) {
+        nchirp = 0;
+        for (const SigDesc& d : p->sd_host) nchirp += d.n;
+        if ((rc = dalloc(p, &p->sd, (size_t)B))) return rc;
+        CUDA_TRY(cudaMemcpy(p->sd, p->sd_host.data(), sizeof(SigDesc) * B, cudaMemcpyHostToDevice));
+        p->ym_stride = (int64_t)2 * K * P * N;
+    }
+    if ((rc = dalloc(p, &p->chirp, nchirp))) return rc;
     if ((rc = dalloc(p, &p->tw, (size_t)P * N))) return rc;
     if ((rc = dalloc(p, &p->twinv, (size_t)P * N))) return rc;
-    if ((rc = dalloc(p, &p->Ym, (size_t)2 * K * P * N))) return rc;
-    if ((rc = dalloc(p, &p->wk, 2))) return rc;
-    if ((rc = dalloc(p, &p->wsexp, (size_t)2 * K))) return rc;
+    if ((rc = dalloc(p, &p->Ym, (size_t)BW * 2 * K * P * N))) return rc;
+    if ((rc = dalloc(p, &p->wk, (size_t)BW * 2))) return rc;
+    if ((rc = dalloc(p, &p->wsexp, (size_t)BW * 2 * K))) return rc;
     if ((rc = dalloc(p, &p->r, (size_t)B * 2 * N))) return rc;
     if ((rc = dalloc(p, &p->mu, (size_t)B * 2 * (K + 1)))) return rc;
     if ((rc = dalloc(p, &p->X, (size_t)B * 2 * K * P * N))) return rc;
@@ -289,84 +431,54 @@ static int plan_build(ozfft_plan_s* p)
     CUDA_TRY(cudaMemset(p->status, 0, sizeof(int)));
     CUDA_TRY(cudaMemset(p->sched, 0, sizeof(Sched) * B * 4));
     CUDA_TRY(cudaMemset(p->kcnt, 0, sizeof(int32_t) * B * 2));
-
-    // twiddle tables, one per prime and direction: w_N = g^((p-1)/N) (inverse:
-    // w_N^-1); entry 2^s + i = w^((N/2^(s+1)) bitrev_s(i)) with its Shoup
-    // quotient, for the block-i butterflies of stage s (k_ntt.cu)
-    {
-        std::vector<uint2> t((size_t)P * N), ti((size_t)P * N);
-        std::vector<uint64_t> pw(N > 1 ? N / 2 : 1), pwi(N > 1 ? N / 2 : 1);
-        int lg = 0;
-        while ((int64_t(1) << lg) < N) ++lg;
-        for (int i = 0; i < P; ++i) {
-            const uint64_t pr = prime_of(i);
-            const uint64_t w = powmod_h(primitive_root_h(pr), (pr - 1) / (uint64_t)N, pr);
-            const uint64_t wi = powmod_h(w, pr - 2, pr);
-            pw[0] = pwi[0] = 1;
-            for (int64_t e = 1; e < N / 2; ++e) {
-                pw[e] = mulmod_h(pw[e - 1], w, pr);
-                pwi[e] = mulmod_h(pwi[e - 1], wi, pr);
-            }
-            auto entry = [&](uint64_t a) { return make_uint2((uint32_t)a, (uint32_t)((a << 32) / pr)); };
-            uint2* ti_ = &ti[(size_t)i * N];
-            uint2* t_ = &t[(size_t)i * N];
-            t_[0] = ti_[0] = entry(1);
-            for (int s = 0; s < lg; ++s) {
-                const int64_t m = int64_t(1) << s;
-                for (int64_t b = 0; b < m; ++b) {
-                    int64_t r = 0;
-                    for (int k = 0; k < s; ++k)
-                        if (b >> k & 1) r |= int64_t(1) << (s - 1 - k);
-                    const int64_t e = (N / (2 * m)) * r;
-                    t_[m + b] = entry(pw[e]);
-                    ti_[m + b] = entry(pwi[e]);
-                }
-            }
-        }
-        CUDA_TRY(cudaMemcpy(p->tw, t.data(), sizeof(uint2) * t.size(), cudaMemcpyHostToDevice));
-        CUDA_TRY(cudaMemcpy(p->twinv, ti.data(), sizeof(uint2) * ti.size(), cudaMemcpyHostToDevice));
-    }
+    if ((rc = build_twiddles(p))) return rc;
 
     ntt_configure(p->geom_fwd, N);
     p->geom_fwd.P = P;
     p->geom_fwd.K = K;
     p->geom_fwd.G = p->G;
+    p->geom_fwd.merged = p->merge;
     p->geom_inv = p->geom_fwd;
 
-    // chirp, then w~* split + forward NTTs (§4.5: precomputed once)
+    // chirp tables, then w~* split + forward NTTs (§4.5: precomputed once); the
+    // split runs in r and mu, which executions overwrite
     cudaStream_t s = 0;
-    CUDA_TRY(launch_chirp(p->chirp, p->n, s));
+    if (uneven) {
+        for (const SigDesc& d : p->sd_host) CUDA_TRY(launch_chirp(p->chirp + d.chirp_off, d.n, s));
+    } else {
+        CUDA_TRY(launch_chirp(p->chirp, p->n, s));
+    }
     {
-        double* rw = nullptr;
-        uint64_t* wmu = nullptr;
-        if ((rc = dalloc(p, &rw, (size_t)2 * N))) return rc;
-        if ((rc = dalloc(p, &wmu, (size_t)2 * (K + 1)))) { cudaFree(rw); return rc; }
-        p->bytes -= (int64_t)(sizeof(double) * 2 * N + sizeof(uint64_t) * 2 * (K + 1));
-        cudaError_t e = cudaMemset(wmu, 0, sizeof(uint64_t) * 2 * (K + 1));
-        if (e == cudaSuccess) e = launch_wstar(p->chirp, p->n, N, rw, wmu, K, p->status, s);
-        for (int k = 0; k < K && e == cudaSuccess; ++k)
-            e = launch_split_level(k, rw, wmu, wmu, N, 2, K, p->alpha, P, p->Ym, k + 1 < K, p->status, s);
-        std::vector<uint64_t> hmu(2 * (K + 1));
-        if (e == cudaSuccess) e = cudaMemcpy(hmu.data(), wmu, sizeof(uint64_t) * hmu.size(), cudaMemcpyDeviceToHost);
-        cudaFree(rw);
-        cudaFree(wmu);
-        if (e != cudaSuccess) return fail(OZFFT_ERR_CUDA, std::string("w* split: ") + cudaGetErrorString(e));
-        std::vector<int32_t> sexp(2 * K, 0);
-        for (int v = 0; v < 2; ++v) {
-            int k = 0;
-            for (; k < K; ++k) {
-                double m;
-                std::memcpy(&m, &hmu[v * (K + 1) + k], sizeof m);
-                if (!(m > 0.0)) break;
-                if (ceil_log2_h(m) + 53 - p->alpha > 1023) return fail(OZFFT_ERR_RANGE, "w* scale");
-                sexp[v * K + k] = p->alpha - ceil_log2_h(m);
+        CUDA_TRY(cudaMemset(p->mu, 0, sizeof(uint64_t) * BW * 2 * (K + 1)));
+        CUDA_TRY(launch_wstar(p->chirp, p->n, N, BW, p->sd, p->r, p->mu, K, p->status, s));
+        for (int k = 0; k < K; ++k)
+            CUDA_TRY(launch_split_level(k, p->r, p->mu, p->mu, N, BW * 2, K, p->alpha, p->sd, P, p->Ym, k + 1 < K,
+                                        p->status, s));
+        std::vector<uint64_t> hmu((size_t)BW * 2 * (K + 1));
+        CUDA_TRY(cudaMemcpy(hmu.data(), p->mu, sizeof(uint64_t) * hmu.size(), cudaMemcpyDeviceToHost));
+        std::vector<int32_t> sexp((size_t)BW * 2 * K, 0), wk((size_t)BW * 2, 0);
+        p->fwd_plan = 0;
+        for (int64_t b = 0; b < BW; ++b) {
+            const int alpha = uneven ? p->sd_host[b].alpha : p->alpha;
+            for (int v = 0; v < 2; ++v) {
+                int k = 0;
+                for (; k < K; ++k) {
+                    double m;
+                    std::memcpy(&m, &hmu[(b * 2 + v) * (K + 1) + k], sizeof m);
+                    if (!(m > 0.0)) break;
+                    if (ceil_log2_h(m) + 53 - alpha > 1023) return fail(OZFFT_ERR_RANGE, "w* scale");
+                    sexp[(b * 2 + v) * K + k] = alpha - ceil_log2_h(m);
+                }
+                wk[b * 2 + v] = k;
+                p->fwd_plan += (int64_t)k * P;
             }
-            p->wk_host[v] = k;
         }
-        CUDA_TRY(cudaMemcpy(p->wk, p->wk_host, sizeof(int32_t) * 2, cudaMemcpyHostToDevice));
-        CUDA_TRY(cudaMemcpy(p->wsexp, sexp.data(), sizeof(int32_t) * 2 * K, cudaMemcpyHostToDevice));
+        p->wk_host[0] = wk[0];
+        p->wk_host[1] = wk[1];
+        CUDA_TRY(cudaMemcpy(p->wk, wk.data(), sizeof(int32_t) * wk.size(), cudaMemcpyHostToDevice));
+        CUDA_TRY(cudaMemcpy(p->wsexp, sexp.data(), sizeof(int32_t) * sexp.size(), cudaMemcpyHostToDevice));
         NttGeom gw = p->geom_fwd;
-        gw.nvec = (int64_t)2 * K * P;
+        gw.nvec = BW * 2 * K * P;
         gw.kcnt = p->wk;
         CUDA_TRY(launch_ntt_forward(gw, p->Ym, p->tw, s));
         uint32_t c[3] = {0, 0, 0};
@@ -375,7 +487,7 @@ static int plan_build(ozfft_plan_s* p)
             const uint64_t ninv = powmod_h((uint64_t)N % pr, pr - 2, pr);
             c[i] = (uint32_t)mulmod_h(ninv, mulmod_h(1ull << 32, 1ull << 32, pr), pr);
         }
-        const int64_t total = (int64_t)2 * K * P * N;
+        const int64_t total = BW * 2 * K * P * N;
         ymont_kernel<<<(unsigned)std::min<int64_t>((total + 255) / 256, 65535), 256, 0, s>>>(p->Ym, N, total, P, c[0],
                                                                                            c[1], c[2]);
         CUDA_TRY(cudaGetLastError());
@@ -393,6 +505,184 @@ static int plan_build(ozfft_plan_s* p)
     const int64_t nchunks = (B + p->chunk - 1) / p->chunk;
     p->launches = 1 /*premul*/ + K /*split*/ + 1 /*schedule*/ + ntt_launches(p->geom_fwd) +
                   nchunks * (ntt_launches(p->geom_inv) + crt_launches());
+    CUDA_TRY(crt_init());
+    return OZFFT_OK;
+}
+
+// Autotuning (ozfft_options.autotune): time every supported split of the
+// plan's NTT length into column and row passes, forward and inverse, on the
+// plan's own buffers with every vector live, and keep the fastest of each.
+// The split changes only the order in which the same butterflies run, so the
+// results are bit-identical.
+static int autotune_ntt(ozfft_plan_s* p)
+{
+    const int lg = p->geom_fwd.lgN;
+    std::vector<int> cands;
+    for (int m2 = 10; m2 <= 14; ++m2) {
+        NttGeom g{};
+        if (ntt_configure_split(g, p->N, m2)) cands.push_back(m2);
+    }
+    if (lg <= 14) {
+        NttGeom g{};
+        if (ntt_configure_split(g, p->N, lg) && std::find(cands.begin(), cands.end(), lg) == cands.end())
+            cands.push_back(lg);
+    }
+    if (cands.size() < 2) return OZFFT_OK;
+    const int64_t B = p->B, K = p->K, G = p->G;
+    // every vector live: K levels, G groups of one product (s, t) each
+    std::vector<int32_t> kc((size_t)B * 2, (int32_t)K);
+    std::vector<Sched> sc((size_t)B * 4);
+    for (Sched& S : sc) {
+        std::memset(&S, 0, sizeof S);
+        S.ngroups = (int32_t)G;
+        for (int g = 0; g < G; ++g) {
+            S.size[g] = 1;
+            S.pair[g][0] = (g / (int)K) * 16 + g % (int)K;
+        }
+    }
+    CUDA_TRY(cudaMemcpy(p->kcnt, kc.data(), sizeof(int32_t) * kc.size(), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(p->sched, sc.data(), sizeof(Sched) * sc.size(), cudaMemcpyHostToDevice));
+    cudaEvent_t e0, e1;
+    CUDA_TRY(cudaEventCreate(&e0));
+    CUDA_TRY(cudaEventCreate(&e1));
+    float best_f = 1e30f, best_i = 1e30f;
+    int m2f = p->geom_fwd.m2, m2i = p->geom_inv.m2;
+    cudaError_t err = cudaSuccess;
+    for (int m2 : cands) {
+        NttGeom gf = p->geom_fwd, gi = p->geom_inv;
+        ntt_configure_split(gf, p->N, m2);
+        ntt_configure_split(gi, p->N, m2);
+        gf.nvec = p->geom_fwd.nvec; gf.P = p->P; gf.K = p->K; gf.G = p->G; gf.kcnt = p->kcnt; gf.sched = p->sched;
+        gi.nvec = p->geom_inv.nvec; gi.P = p->P; gi.K = p->K; gi.G = p->G; gi.kcnt = p->kcnt; gi.sched = p->sched;
+        const MacSrc mac{p->X, p->Ym, p->ym_stride};
+        float tf = 1e30f, ti = 1e30f;
+        for (int rep = 0; rep < 3 && err == cudaSuccess; ++rep) {
+            float ms = 0.f;
+            err = cudaEventRecord(e0, 0);
+            if (err == cudaSuccess) err = launch_ntt_forward(gf, p->X, p->tw, 0);
+            if (err == cudaSuccess) err = cudaEventRecord(e1, 0);
+            if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+            if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0) tf = std::min(tf, ms);
+            if (err == cudaSuccess) err = cudaEventRecord(e0, 0);
+            if (err == cudaSuccess) err = launch_ntt_inv_row(gi, p->Z, p->twinv, mac, 0);
+            if (err == cudaSuccess && gi.m1 > 0) err = launch_ntt_inv_col(gi, p->Z, p->twinv, 0);
+            if (err == cudaSuccess) err = cudaEventRecord(e1, 0);
+            if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+            if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0) ti = std::min(ti, ms);
+        }
+        if (err != cudaSuccess) break;
+        if (tf < best_f) { best_f = tf; m2f = m2; }
+        if (ti < best_i) { best_i = ti; m2i = m2; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (err != cudaSuccess) return fail(OZFFT_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(err));
+    CUDA_TRY(cudaMemset(p->kcnt, 0, sizeof(int32_t) * B * 2));
+    CUDA_TRY(cudaMemset(p->sched, 0, sizeof(Sched) * B * 4));
+    NttGeom gf = p->geom_fwd, gi = p->geom_inv;
+    ntt_configure_split(p->geom_fwd, p->N, m2f);
+    ntt_configure_split(p->geom_inv, p->N, m2i);
+    p->geom_fwd.nvec = gf.nvec; p->geom_fwd.P = gf.P; p->geom_fwd.K = gf.K; p->geom_fwd.G = gf.G;
+    p->geom_fwd.kcnt = gf.kcnt; p->geom_fwd.sched = gf.sched;
+    p->geom_inv.nvec = gi.nvec; p->geom_inv.P = gi.P; p->geom_inv.K = gi.K; p->geom_inv.G = gi.G;
+    p->geom_inv.kcnt = gi.kcnt; p->geom_inv.sched = gi.sched;
+    const int64_t nchunks = (B + p->chunk - 1) / p->chunk;
+    p->launches = 1 + K + 1 + ntt_launches(p->geom_fwd) + nchunks * (ntt_launches(p->geom_inv) + crt_launches());
+    return OZFFT_OK;
+}
+
+// One execution of a plan (or of one length class of a plan over uneven
+// lengths, whose input and output pointers come from io_ref): every kernel is
+// enqueued on s.
+static int run_plan(ozfft_plan_s* p, const void* in, void* out, cudaStream_t s)
+{
+    const int64_t N = p->N, B = p->B;
+    const int K = p->K;
+    CUDA_TRY(cudaMemsetAsync(p->mu, 0, sizeof(uint64_t) * B * 2 * (K + 1), s));
+    p->cur = nullptr;
+    if (p->profiling) {
+        cudaEvent_t e0 = take_event(p);
+        if (e0) {
+            cudaEventRecord(e0, s);
+            p->pending.push_back({e0, {}});
+            p->cur = &p->pending.back();
+        }
+    }
+    CUDA_TRY(launch_premul((const double2*)in, p->chirp, p->n, N, B, p->direction > 0, p->sd, p->io_ref, p->r, p->mu,
+                           K, p->status, s));
+    mark(p, OZFFT_PROF_PREMUL, s);
+    if (p->debug) CUDA_TRY(cudaMemcpyAsync(p->dbg_r, p->r, sizeof(double) * B * 2 * N, cudaMemcpyDeviceToDevice, s));
+    for (int k = 0; k < K; ++k) {
+        CUDA_TRY(launch_split_level(k, p->r, p->mu, p->mu, N, B * 2, K, p->alpha, p->sd, p->P, p->X, k + 1 < K,
+                                    p->status, s));
+        mark(p, OZFFT_PROF_SPLIT, s);
+    }
+    if (p->debug)
+        CUDA_TRY(cudaMemcpyAsync(p->dbg_X, p->X, sizeof(uint32_t) * B * 2 * K * p->P * N, cudaMemcpyDeviceToDevice, s));
+    schedule_kernel<<<(unsigned)((B + 127) / 128), 128, 0, s>>>(p->mu, B, K, p->L, p->alpha, p->sd, p->wk, p->wsexp,
+                                                                 p->sched, p->kcnt, p->span, p->merge);
+    CUDA_TRY(cudaGetLastError());
+    mark(p, OZFFT_PROF_SCHEDULE, s);
+    if (p->geom_fwd.m1 > 0) {
+        CUDA_TRY(launch_ntt_fwd_col(p->geom_fwd, p->X, p->tw, s));
+        mark(p, OZFFT_PROF_NTT_FWD_COL, s);
+    }
+    CUDA_TRY(launch_ntt_fwd_row(p->geom_fwd, p->X, p->tw, s));
+    mark(p, OZFFT_PROF_NTT_FWD_ROW, s);
+    // inverse stages chunk by chunk: Z of one chunk stays in L2 between the passes
+    for (int64_t b0 = 0; b0 < B; b0 += p->chunk) {
+        const int64_t nb = std::min<int64_t>(p->chunk, B - b0);
+        NttGeom gi = p->geom_inv;
+        gi.nvec = nb * 4 * p->G * p->P;
+        gi.sched = p->sched + b0 * 4;
+        const MacSrc mac{p->X + b0 * 2 * K * p->P * N, p->Ym + b0 * p->ym_stride, p->ym_stride};
+        CUDA_TRY(launch_ntt_inv_row(gi, p->Z, p->twinv, mac, s));
+        mark(p, OZFFT_PROF_NTT_INV_ROW, s);
+        if (gi.m1 > 0) {
+            CUDA_TRY(launch_ntt_inv_col(gi, p->Z, p->twinv, s));
+            mark(p, OZFFT_PROF_NTT_INV_COL, s);
+        }
+        CrtArgs ca{p->Z, p->sched + b0 * 4, p->span + b0 * 3, p->chirp,
+                   p->sd ? (double2*)out : (double2*)out + b0 * p->n, p->n, N, nb,
+                   p->P, p->G, p->direction, p->status, p->sd ? p->sd + b0 : nullptr, p->io_ref, p->merge};
+        CUDA_TRY(launch_crt_post(ca, s));
+        if (b0 + p->chunk < B) mark(p, OZFFT_PROF_CRT, s);
+    }
+    mark(p, OZFFT_PROF_CRT, s);
+    p->cur = nullptr;
+    p->executed = true;
+    return OZFFT_OK;
+}
+
+// The length classes of a plan over uneven lengths, forked from s onto their
+// own streams and joined back (captured once into the plan's graph, or run
+// directly with no_graph).
+static int run_classes(ozfft_plan_s* p, cudaStream_t s)
+{
+    CUDA_TRY(cudaEventRecord(p->fork, s));
+    for (size_t c = 0; c < p->classes.size(); ++c) {
+        CUDA_TRY(cudaStreamWaitEvent(p->streams[c], p->fork, 0));
+        const int rc = run_plan(p->classes[c], nullptr, nullptr, p->streams[c]);
+        if (rc) return rc;
+        CUDA_TRY(cudaEventRecord(p->joins[c], p->streams[c]));
+        CUDA_TRY(cudaStreamWaitEvent(s, p->joins[c], 0));
+    }
+    return OZFFT_OK;
+}
+
+static int run_many(ozfft_plan_s* p, const void* in, void* out, cudaStream_t s)
+{
+    CUDA_TRY(launch_set_io(p->io, in, out, s));
+    if (p->gexec) {
+        CUDA_TRY(cudaGraphLaunch(p->gexec, s));
+    } else {
+        const int rc = run_classes(p, s);
+        if (rc) return rc;
+    }
+    for (ozfft_plan_s* c : p->classes) c->executed = true;
+    p->executed = true;
     return OZFFT_OK;
 }
 
@@ -434,13 +724,15 @@ ozfft_plan_t ozfft_plan_ex(int64_t n, int64_t batch, int direction, const ozfft_
     p->G = K * K;
     p->alpha = alpha;
     p->debug = o.debug;
+    p->merge = o.merge != 0;
     {
         const int64_t zbytes = (int64_t)4 * p->G * P * N * 4;   // Z of one signal
         int64_t c = o.chunk > 0 ? o.chunk : std::max<int64_t>(1, (int64_t(16) << 30) / zbytes);
         if (p->debug) c = batch;                              // dumps read Z of any signal
         p->chunk = std::min<int64_t>(c, batch);
     }
-    if (plan_build(p) != OZFFT_OK) {
+    p->total = n * batch;
+    if (plan_build(p) != OZFFT_OK || (o.autotune && autotune_ntt(p) != OZFFT_OK)) {
         plan_free(p);
         return nullptr;
     }
@@ -449,69 +741,155 @@ ozfft_plan_t ozfft_plan_ex(int64_t n, int64_t batch, int direction, const ozfft_
 
 ozfft_plan_t ozfft_plan(int64_t n, int64_t batch, int direction) { return ozfft_plan_ex(n, batch, direction, nullptr); }
 
+static int64_t default_conv_len(int64_t n)
+{
+    if ((n & (n - 1)) == 0) return n;
+    int64_t N = 1;
+    while (N < 2 * n - 1) N <<= 1;
+    return N;
+}
+
+ozfft_plan_t ozfft_plan_many(const int64_t* lengths, int64_t count, int direction, const ozfft_options* opt)
+{
+    ozfft_options o{};
+    if (opt) o = *opt;
+    const int K = o.K ? o.K : 3, L = o.L ? o.L : 1, P = o.nprimes ? o.nprimes : 2;
+    if (!lengths || count < 1 || (direction != OZFFT_FORWARD && direction != OZFFT_INVERSE &&
+                                  direction != OZFFT_ADJOINT && direction != OZFFT_INVERSE_ADJOINT) ||
+        K < 1 || K > MAX_K || L < 1 || L > MAX_L || P < 2 || P > 3 || o.conv_len != 0 || o.debug != 0 || o.chunk < 0) {
+        fail(OZFFT_ERR_ARG, "ozfft_plan_many: argument out of range");
+        return nullptr;
+    }
+    // length classes by convolution length, largest first (their work dominates)
+    std::vector<std::pair<int64_t, std::vector<int64_t>>> cls;
+    {
+        std::vector<int64_t> Ns(count);
+        for (int64_t i = 0; i < count; ++i) {
+            const int64_t n = lengths[i];
+            if (n < 1 || n > (int64_t(1) << 24)) {
+                fail(OZFFT_ERR_LENGTH, "ozfft_plan_many: length " + std::to_string(n) + " out of range");
+                return nullptr;
+            }
+            Ns[i] = default_conv_len(n);
+            if (Ns[i] > (int64_t(1) << 24) || alpha_h(n, L, P) < 1) {
+                fail(OZFFT_ERR_LENGTH, "ozfft_plan_many: length " + std::to_string(n) + " unsupported");
+                return nullptr;
+            }
+        }
+        std::vector<int64_t> order(count);
+        for (int64_t i = 0; i < count; ++i) order[i] = i;
+        std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return Ns[a] > Ns[b]; });
+        for (int64_t i : order) {
+            if (cls.empty() || cls.back().first != Ns[i]) cls.push_back({Ns[i], {}});
+            cls.back().second.push_back(i);
+        }
+    }
+    std::vector<int64_t> off(count + 1, 0);
+    for (int64_t i = 0; i < count; ++i) off[i + 1] = off[i] + lengths[i];
+    // inverse-NTT buffers: the same fraction of every class's signals per chunk,
+    // all classes together within 16 GiB (or opt->chunk signals per chunk)
+    const int G = K * K;
+    double zdemand = 0;
+    for (auto& c : cls) zdemand += (double)c.second.size() * 4.0 * G * P * c.first * 4.0;
+    const double frac = std::min(1.0, (double)(int64_t(16) << 30) / zdemand);
+
+    ozfft_plan_s* p = new ozfft_plan_s;
+    p->B = count;
+    p->n = off[count];
+    p->total = off[count];
+    p->N = cls.front().first;
+    p->direction = direction;
+    p->K = K;
+    p->L = L;
+    p->P = P;
+    p->G = G;
+    p->alpha = 64;
+    p->chunk = 0;
+    auto bail = [&](int code, const std::string& msg) {
+        if (code) fail(code, msg);
+        plan_free(p);
+        return (ozfft_plan_t) nullptr;
+    };
+    if (cudaGetDevice(&p->device) != cudaSuccess) return bail(OZFFT_ERR_CUDA, "ozfft_plan_many: no device");
+    if (dalloc(p, &p->io, 1)) return bail(0, "");
+    for (auto& c : cls) {
+        ozfft_plan_s* q = new ozfft_plan_s;
+        p->classes.push_back(q);
+        q->N = c.first;
+        q->B = (int64_t)c.second.size();
+        q->direction = direction;
+        q->K = K;
+        q->L = L;
+        q->P = P;
+        q->G = G;
+        q->merge = o.merge != 0;
+        q->io_ref = p->io;
+        int64_t chirp_off = 0;
+        for (int64_t i : c.second) {
+            SigDesc d{};
+            d.n = lengths[i];
+            d.io_off = off[i];
+            d.chirp_off = chirp_off;
+            d.alpha = alpha_h(lengths[i], L, P);
+            chirp_off += d.n;
+            q->sd_host.push_back(d);
+            q->n = std::max(q->n, d.n);
+            q->alpha = std::max(q->alpha, d.alpha);
+            p->alpha = std::min(p->alpha, d.alpha);
+        }
+        q->total = chirp_off;
+        q->chunk = o.chunk > 0 ? std::min<int64_t>(o.chunk, q->B)
+                               : std::max<int64_t>(1, std::min<int64_t>(q->B, (int64_t)(q->B * frac)));
+        if (plan_build(q) != OZFFT_OK || (o.autotune && autotune_ntt(q) != OZFFT_OK)) return bail(0, "");
+        p->bytes += q->bytes;
+        p->launches += q->launches;
+        p->fwd_plan += q->fwd_plan;
+        p->chunk = std::max(p->chunk, q->chunk);
+        cudaStream_t st = nullptr;
+        cudaEvent_t ev = nullptr;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess)
+            return bail(OZFFT_ERR_CUDA, "ozfft_plan_many: stream");
+        p->streams.push_back(st);
+        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess)
+            return bail(OZFFT_ERR_CUDA, "ozfft_plan_many: event");
+        p->joins.push_back(ev);
+    }
+    p->launches += 1;   // the in/out pointer update
+    if (cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming) != cudaSuccess)
+        return bail(OZFFT_ERR_CUDA, "ozfft_plan_many: event");
+    if (cudaMalloc((void**)&p->status, sizeof(int)) != cudaSuccess || cudaMemset(p->status, 0, sizeof(int)) != cudaSuccess)
+        return bail(OZFFT_ERR_ALLOC, "ozfft_plan_many: status word");
+    if (!o.no_graph) {
+        // capture every class's kernels once; executions replay the graph
+        if (cudaStreamCreateWithFlags(&p->capture, cudaStreamNonBlocking) != cudaSuccess)
+            return bail(OZFFT_ERR_CUDA, "ozfft_plan_many: stream");
+        if (cudaStreamBeginCapture(p->capture, cudaStreamCaptureModeRelaxed) != cudaSuccess)
+            return bail(OZFFT_ERR_CUDA, "ozfft_plan_many: begin capture");
+        const int rc = run_classes(p, p->capture);
+        cudaGraph_t g = nullptr;
+        const cudaError_t ce = cudaStreamEndCapture(p->capture, &g);
+        p->graph = g;
+        if (rc || ce != cudaSuccess)
+            return bail(rc ? 0 : OZFFT_ERR_CUDA,
+                        std::string("ozfft_plan_many: capture: ") + cudaGetErrorString(ce));
+        if (cudaGraphInstantiate(&p->gexec, p->graph, 0) != cudaSuccess)
+            return bail(OZFFT_ERR_CUDA, "ozfft_plan_many: graph instantiation");
+    }
+    for (ozfft_plan_s* q : p->classes) q->executed = false;
+    return p;
+}
+
 int ozfft_execute(ozfft_plan_t p, const void* in, void* out, void* stream)
 {
     if (!p || !in || !out) return fail(OZFFT_ERR_ARG, "ozfft_execute: null argument");
-    cudaStream_t s = (cudaStream_t)stream;
-    const int64_t N = p->N, B = p->B;
-    const int K = p->K;
-    CUDA_TRY(cudaMemsetAsync(p->mu, 0, sizeof(uint64_t) * B * 2 * (K + 1), s));
-    p->cur = nullptr;
-    if (p->profiling) {
-        cudaEvent_t e0 = take_event(p);
-        if (e0) {
-            cudaEventRecord(e0, s);
-            p->pending.push_back({e0, {}});
-            p->cur = &p->pending.back();
-        }
-    }
-    CUDA_TRY(launch_premul((const double2*)in, p->chirp, p->n, N, B, p->direction > 0, p->r, p->mu, K,
-                           p->status, s));
-    mark(p, OZFFT_PROF_PREMUL, s);
-    if (p->debug) CUDA_TRY(cudaMemcpyAsync(p->dbg_r, p->r, sizeof(double) * B * 2 * N, cudaMemcpyDeviceToDevice, s));
-    for (int k = 0; k < K; ++k) {
-        CUDA_TRY(launch_split_level(k, p->r, p->mu, p->mu, N, B * 2, K, p->alpha, p->P, p->X, k + 1 < K, p->status, s));
-        mark(p, OZFFT_PROF_SPLIT, s);
-    }
-    if (p->debug)
-        CUDA_TRY(cudaMemcpyAsync(p->dbg_X, p->X, sizeof(uint32_t) * B * 2 * K * p->P * N, cudaMemcpyDeviceToDevice, s));
-    schedule_kernel<<<(unsigned)((B + 127) / 128), 128, 0, s>>>(p->mu, B, K, p->L, p->alpha, p->wk, p->wsexp,
-                                                                 p->sched, p->kcnt, p->span);
-    CUDA_TRY(cudaGetLastError());
-    mark(p, OZFFT_PROF_SCHEDULE, s);
-    if (p->geom_fwd.m1 > 0) {
-        CUDA_TRY(launch_ntt_fwd_col(p->geom_fwd, p->X, p->tw, s));
-        mark(p, OZFFT_PROF_NTT_FWD_COL, s);
-    }
-    CUDA_TRY(launch_ntt_fwd_row(p->geom_fwd, p->X, p->tw, s));
-    mark(p, OZFFT_PROF_NTT_FWD_ROW, s);
-    // inverse stages chunk by chunk: Z of one chunk stays in L2 between the passes
-    for (int64_t b0 = 0; b0 < B; b0 += p->chunk) {
-        const int64_t nb = std::min<int64_t>(p->chunk, B - b0);
-        NttGeom gi = p->geom_inv;
-        gi.nvec = nb * 4 * p->G * p->P;
-        gi.sched = p->sched + b0 * 4;
-        const MacSrc mac{p->X + b0 * 2 * K * p->P * N, p->Ym};
-        CUDA_TRY(launch_ntt_inv_row(gi, p->Z, p->twinv, mac, s));
-        mark(p, OZFFT_PROF_NTT_INV_ROW, s);
-        if (gi.m1 > 0) {
-            CUDA_TRY(launch_ntt_inv_col(gi, p->Z, p->twinv, s));
-            mark(p, OZFFT_PROF_NTT_INV_COL, s);
-        }
-        CrtArgs ca{p->Z, p->sched + b0 * 4, p->span + b0 * 3, p->chirp, (double2*)out + b0 * p->n, p->n, N, nb,
-                   p->P, p->G, p->direction, p->status};
-        CUDA_TRY(launch_crt_post(ca, s));
-        if (b0 + p->chunk < B) mark(p, OZFFT_PROF_CRT, s);
-    }
-    mark(p, OZFFT_PROF_CRT, s);
-    p->cur = nullptr;
-    p->executed = true;
-    return OZFFT_OK;
+    if (!p->classes.empty()) return run_many(p, in, out, (cudaStream_t)stream);
+    return run_plan(p, in, out, (cudaStream_t)stream);
 }
 
 int ozfft_set_profiling(ozfft_plan_t p, int enable)
 {
     if (!p) return fail(OZFFT_ERR_ARG, "ozfft_set_profiling: null plan");
+    if (!p->classes.empty()) return fail(OZFFT_ERR_ARG, "ozfft_set_profiling: not available for uneven-length plans");
     p->profiling = enable != 0;
     return OZFFT_OK;
 }
@@ -519,6 +897,7 @@ int ozfft_set_profiling(ozfft_plan_t p, int enable)
 int ozfft_get_profile(ozfft_plan_t p, void* stream, ozfft_profile* out)
 {
     if (!p || !out) return fail(OZFFT_ERR_ARG, "ozfft_get_profile: null argument");
+    if (!p->classes.empty()) return fail(OZFFT_ERR_ARG, "ozfft_get_profile: not available for uneven-length plans");
     std::memset(out, 0, sizeof(*out));
     CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
     for (auto& r : p->pending) {
@@ -543,11 +922,11 @@ int ozfft_execute_host(ozfft_plan_t p, const void* in, void* out, void* stream)
 {
     if (!p || !in || !out) return fail(OZFFT_ERR_ARG, "ozfft_execute_host: null argument");
     cudaStream_t s = (cudaStream_t)stream;
-    const size_t bytes = sizeof(double2) * p->n * p->B;
+    const size_t bytes = sizeof(double2) * p->total;
     if (!p->stage_in) {
         int rc;
-        if ((rc = dalloc(p, &p->stage_in, p->n * p->B))) return rc;
-        if ((rc = dalloc(p, &p->stage_out, p->n * p->B))) return rc;
+        if ((rc = dalloc(p, &p->stage_in, p->total))) return rc;
+        if ((rc = dalloc(p, &p->stage_out, p->total))) return rc;
     }
     CUDA_TRY(cudaMemcpyAsync(p->stage_in, in, bytes, cudaMemcpyHostToDevice, s));
     int rc = ozfft_execute(p, p->stage_in, p->stage_out, stream);
@@ -565,6 +944,12 @@ int ozfft_get_status(ozfft_plan_t p, void* stream)
     CUDA_TRY(cudaStreamSynchronize(s));
     CUDA_TRY(cudaMemcpy(&st, p->status, sizeof(int), cudaMemcpyDeviceToHost));
     CUDA_TRY(cudaMemset(p->status, 0, sizeof(int)));
+    for (ozfft_plan_s* c : p->classes) {   // a plan over uneven lengths: every class's word
+        int sc = 0;
+        CUDA_TRY(cudaMemcpy(&sc, c->status, sizeof(int), cudaMemcpyDeviceToHost));
+        CUDA_TRY(cudaMemset(c->status, 0, sizeof(int)));
+        st |= sc;
+    }
     if (st & ST_NONFINITE) return OZFFT_ERR_NONFINITE;
     if (st & ST_RANGE) return OZFFT_ERR_RANGE;
     return OZFFT_OK;
@@ -584,17 +969,20 @@ int ozfft_get_stats(ozfft_plan_t p, void* stream, ozfft_stats* out)
     out->direction = p->direction;
     out->wstar_levels[0] = p->wk_host[0];
     out->wstar_levels[1] = p->wk_host[1];
-    out->ntt_forward_plan = (int64_t)(p->wk_host[0] + p->wk_host[1]) * p->P;
+    out->ntt_forward_plan = p->fwd_plan;
     out->kernel_launches = p->launches;
     out->workspace_bytes = p->bytes;
-    if (p->executed) {
-        CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
-        std::vector<int32_t> kc(p->B * 2);
-        std::vector<Sched> sc(p->B * 4);
-        CUDA_TRY(cudaMemcpy(kc.data(), p->kcnt, sizeof(int32_t) * kc.size(), cudaMemcpyDeviceToHost));
-        CUDA_TRY(cudaMemcpy(sc.data(), p->sched, sizeof(Sched) * sc.size(), cudaMemcpyDeviceToHost));
-        for (int32_t k : kc) out->ntt_forward_runtime += (int64_t)k * p->P;
-        for (const Sched& s : sc) out->ntt_inverse += (int64_t)s.ngroups * p->P;
+    std::vector<ozfft_plan_s*> parts = p->classes;
+    if (parts.empty()) parts.push_back(p);
+    if (p->executed) CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    for (ozfft_plan_s* q : parts) {
+        if (!q->executed) continue;
+        std::vector<int32_t> kc(q->B * 2);
+        std::vector<Sched> sc(q->B * 4);
+        CUDA_TRY(cudaMemcpy(kc.data(), q->kcnt, sizeof(int32_t) * kc.size(), cudaMemcpyDeviceToHost));
+        CUDA_TRY(cudaMemcpy(sc.data(), q->sched, sizeof(Sched) * sc.size(), cudaMemcpyDeviceToHost));
+        for (int32_t k : kc) out->ntt_forward_runtime += (int64_t)k * q->P;
+        for (const Sched& s : sc) out->ntt_inverse += (int64_t)s.ngroups * q->P;
     }
     return OZFFT_OK;
 }
@@ -635,6 +1023,7 @@ static int64_t bitrev(int64_t v, int lg)
 int64_t ozfft_debug_dump(ozfft_plan_t p, int stage, int64_t index, void* dst, void* stream)
 {
     if (!p) return -fail(OZFFT_ERR_ARG, "ozfft_debug_dump: null plan");
+    if (!p->classes.empty()) return -fail(OZFFT_ERR_ARG, "ozfft_debug_dump: not available for uneven-length plans");
     const int64_t N = p->N, K = p->K, P = p->P, G = p->G;
     const int64_t b = index;
     const bool per_signal = stage != OZFFT_DUMP_CHIRP && stage != OZFFT_DUMP_YSPEC;
@@ -797,8 +1186,9 @@ static int noalloc_setup(NoallocState& st, int dev, int64_t n, int64_t N, int al
     CUDA_TRY(launch_chirp(p.chirp, n, 0));
     CUDA_TRY(cudaMemset(p.status, 0, sizeof(int)));
     CUDA_TRY(cudaMemset(p.mu, 0, sizeof(uint64_t) * 2 * (K + 1)));
-    CUDA_TRY(launch_wstar(p.chirp, n, N, p.r, p.mu, K, p.status, 0));
-    for (int k = 0; k < K; ++k) CUDA_TRY(launch_split_level(k, p.r, p.mu, p.mu, N, 2, K, alpha, P, p.Ym, k + 1 < K, p.status, 0));
+    CUDA_TRY(launch_wstar(p.chirp, n, N, 1, nullptr, p.r, p.mu, K, p.status, 0));
+    for (int k = 0; k < K; ++k)
+        CUDA_TRY(launch_split_level(k, p.r, p.mu, p.mu, N, 2, K, alpha, nullptr, P, p.Ym, k + 1 < K, p.status, 0));
     uint64_t hmu[2 * (MAX_K + 1)];
     CUDA_TRY(cudaMemcpy(hmu, p.mu, sizeof(uint64_t) * 2 * (K + 1), cudaMemcpyDeviceToHost));
     int32_t sexp[2 * MAX_K] = {0};

@@ -24,13 +24,14 @@ MAX_GROUPS, MAX_L = 64, 8
 # every symbol include/ozfft.h declares
 EXPORTS = ("ozfft_plan", "ozfft_plan_ex", "ozfft_execute", "ozfft_execute_host", "ozfft_get_status",
            "ozfft_get_stats", "ozfft_set_profiling", "ozfft_get_profile", "ozfft_destroy", "ozfft_error_string",
-           "ozfft_last_error", "ozfft_debug_dump", "ozfft_execute_noalloc")
+           "ozfft_last_error", "ozfft_debug_dump", "ozfft_execute_noalloc", "ozfft_plan_many")
 PROF_SLOTS = ("premul", "split", "schedule", "ntt_fwd_col", "ntt_fwd_row", "ntt_inv_row", "ntt_inv_col", "crt")
 
 
 class Options(C.Structure):
     _fields_ = [("K", C.c_int32), ("L", C.c_int32), ("nprimes", C.c_int32), ("conv_len", C.c_int64),
-                ("debug", C.c_int32), ("chunk", C.c_int32)]
+                ("debug", C.c_int32), ("chunk", C.c_int32), ("autotune", C.c_int32), ("no_graph", C.c_int32),
+                ("merge", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -78,6 +79,8 @@ def load(path: str = LIB_PATH):
             L.ozfft_debug_dump.restype = i64; L.ozfft_debug_dump.argtypes = [P, C.c_int, i64, P, P]
             L.ozfft_execute_noalloc.restype = C.c_int
             L.ozfft_execute_noalloc.argtypes = [i64, C.c_int, P, P, P]
+            L.ozfft_plan_many.restype = P
+            L.ozfft_plan_many.argtypes = [C.POINTER(i64), i64, C.c_int, C.POINTER(Options)]
             _lib = L
     return _lib
 
@@ -98,16 +101,19 @@ def _stream_ptr(stream):
 class Plan:
     """A plan for `batch` transforms of length n (see ozfft_plan_ex)."""
 
-    def __init__(self, n, batch=1, direction=FORWARD, K=3, L=1, nprimes=2, conv_len=0, debug=False, chunk=0):
+    def __init__(self, n, batch=1, direction=FORWARD, K=3, L=1, nprimes=2, conv_len=0, debug=False, chunk=0,
+                 autotune=False, merge=False):
         lib = load()
         self.n, self.batch, self.direction = int(n), int(batch), int(direction)
-        self.K, self.L, self.nprimes = int(K), int(L), int(nprimes)
-        opt = Options(self.K, self.L, self.nprimes, int(conv_len), int(bool(debug)), int(chunk))
+        self.K, self.L, self.nprimes, self.merge = int(K), int(L), int(nprimes), bool(merge)
+        opt = Options(self.K, self.L, self.nprimes, int(conv_len), int(bool(debug)), int(chunk), int(bool(autotune)), 0,
+                      int(self.merge))
         self._h = lib.ozfft_plan_ex(self.n, self.batch, self.direction, C.byref(opt))
         if not self._h:
             raise OzfftError(-1, lib.ozfft_last_error().decode())
         st = self.stats()
         self.N, self.alpha = st["N"], st["alpha"]
+        self.total = self.n * self.batch
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -123,10 +129,12 @@ class Plan:
         import torch
         if x.dtype != torch.complex128 or not x.is_cuda or not x.is_contiguous():
             raise OzfftError(ERR_ARG, "input must be a contiguous CUDA complex128 tensor")
-        if x.numel() != self.n * self.batch:
-            raise OzfftError(ERR_ARG, f"input has {x.numel()} elements, plan wants {self.n * self.batch}")
+        if x.numel() != self.total:
+            raise OzfftError(ERR_ARG, f"input has {x.numel()} elements, plan wants {self.total}")
         if out is None:
             out = torch.empty_like(x)
+        elif out.numel() != self.total or out.dtype != torch.complex128 or not out.is_cuda or not out.is_contiguous():
+            raise OzfftError(ERR_ARG, "output must be a contiguous CUDA complex128 tensor of the input's size")
         _check(load().ozfft_execute(self._h, x.data_ptr(), out.data_ptr(), _stream_ptr(stream)))
         return out
 
@@ -134,7 +142,10 @@ class Plan:
         _check(load().ozfft_execute(self._h, in_ptr, out_ptr, stream_ptr))
 
     def execute_host(self, x, out, stream=None):
-        """x, out: host buffers (numpy complex128 arrays or pinned CPU tensors) of batch*n elements."""
+        """x, out: host buffers (numpy complex128 arrays or pinned CPU tensors) of `total` elements."""
+        for a in (x, out):
+            if (a.size if isinstance(a, np.ndarray) else a.numel()) != self.total:
+                raise OzfftError(ERR_ARG, f"host buffers must hold {self.total} elements")
         xp = x.ctypes.data if isinstance(x, np.ndarray) else x.data_ptr()
         op = out.ctypes.data if isinstance(out, np.ndarray) else out.data_ptr()
         _check(load().ozfft_execute_host(self._h, xp, op, _stream_ptr(stream)))
@@ -193,6 +204,33 @@ class Plan:
         if stage == DUMP_ZRES:
             return buf.view(np.uint32).reshape(4, G, P, N)
         return buf
+
+
+class PlanMany(Plan):
+    """A plan over signals of uneven lengths (ozfft_plan_many): the input and
+    output are packed, signal i at elements [offsets[i], offsets[i+1])."""
+
+    def __init__(self, lengths, direction=FORWARD, K=3, L=1, nprimes=2, chunk=0, autotune=False, graph=True,
+                 merge=False):
+        lib = load()
+        lens = np.ascontiguousarray(np.asarray(lengths, dtype=np.int64))
+        self.lengths = lens
+        self.offsets = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+        self.direction, self.K, self.L, self.nprimes = int(direction), int(K), int(L), int(nprimes)
+        self.merge = bool(merge)
+        opt = Options(self.K, self.L, self.nprimes, 0, 0, int(chunk), int(bool(autotune)), int(not graph),
+                      int(self.merge))
+        self._h = lib.ozfft_plan_many(lens.ctypes.data_as(C.POINTER(C.c_int64)), lens.size, self.direction,
+                                      C.byref(opt))
+        if not self._h:
+            raise OzfftError(-1, lib.ozfft_last_error().decode())
+        st = self.stats()
+        self.n, self.batch, self.N, self.alpha = int(self.offsets[-1]), lens.size, st["N"], st["alpha"]
+        self.total = self.n
+
+    def split(self, y):
+        """The packed output as a list of per-signal views."""
+        return [y[self.offsets[i]:self.offsets[i + 1]] for i in range(self.batch)]
 
 
 def execute_noalloc(x, out, direction=FORWARD, stream=None):
