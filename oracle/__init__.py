@@ -88,6 +88,14 @@ def lib():
             L.or_dft_q.restype = C.c_int; L.or_dft_q.argtypes = [i64, P, C.c_int, i64, P, P, P]
             L.or_fft_q.restype = C.c_int; L.or_fft_q.argtypes = [i64, P, C.c_int, P, P]
             L.or_sincospi_q.restype = None; L.or_sincospi_q.argtypes = [u64, u64, P]
+            L.or_alpha_ts.restype = C.c_int; L.or_alpha_ts.argtypes = [i64, C.c_int]
+            L.or_ts_from_double.restype = None; L.or_ts_from_double.argtypes = [P, i64, P]
+            L.or_ts_to_double.restype = None; L.or_ts_to_double.argtypes = [P, i64, P]
+            L.or_ts_op.restype = None; L.or_ts_op.argtypes = [C.c_int, P, P, i64, P]
+            L.or_ts_split.restype = C.c_int
+            L.or_ts_split.argtypes = [P, i64, C.c_int, C.c_int, C.c_int, P, P, P]
+            L.or_ozfft_ts.restype = C.c_int
+            L.or_ozfft_ts.argtypes = [i64, i64, C.c_int, C.c_int, C.c_int, P, P, P]
             _lib = L
     return _lib
 
@@ -255,6 +263,87 @@ def ozfft(x, N=None, K=3, L=1, nprimes=2, direction=FORWARD, trace=None):
     info.update(keep)
     if st:
         raise OracleError(st, "ozfft")
+    return y, info
+
+
+# --- TS (triple-single) variant ----------------------------------------------
+def alpha_ts(n, L):
+    return int(lib().or_alpha_ts(n, L))
+
+
+def ts_from_double(x):
+    """binary64 values -> [cnt, 3] float32 TS words (reading T1)."""
+    x = np.ascontiguousarray(x, dtype=np.float64).ravel()
+    out = np.empty((x.size, 3), dtype=np.float32)
+    lib().or_ts_from_double(_p(x), x.size, _p(out))
+    return out
+
+
+def ts_to_double(t):
+    t = np.ascontiguousarray(t, dtype=np.float32).reshape(-1, 3)
+    out = np.empty(t.shape[0], dtype=np.float64)
+    lib().or_ts_to_double(_p(t), t.shape[0], _p(out))
+    return out
+
+
+def ts_op(op, a, b):
+    """TSAdd ('add'), TSSub ('sub') or TSMul ('mul') of [cnt, 3] float32 arrays."""
+    a = np.ascontiguousarray(a, dtype=np.float32).reshape(-1, 3)
+    b = np.ascontiguousarray(b, dtype=np.float32).reshape(-1, 3)
+    out = np.empty_like(a)
+    lib().or_ts_op({"add": 0, "sub": 1, "mul": 2}[op], _p(a), _p(b), a.shape[0], _p(out))
+    return out
+
+
+def ts_split(v, alpha, K=0):
+    """Alg. 6 on a TS vector v [3, N] (word planes).  Returns (q [k, N] int64, sexp)."""
+    v = np.ascontiguousarray(v, dtype=np.float32)
+    N = v.shape[1]
+    kdim = K if K > 0 else KMAX
+    q = np.zeros((kdim, N), dtype=np.int64)
+    sexp = np.zeros(KMAX, dtype=np.int32)
+    k = C.c_int32(0)
+    st = lib().or_ts_split(_p(v), N, alpha, K, kdim, _p(q), _p(sexp), C.byref(k))
+    if st:
+        raise OracleError(st, "ts_split")
+    return q[:k.value], [int(e) for e in sexp[:k.value]]
+
+
+def ozfft_ts(x, N=None, K=3, L=1, direction=FORWARD, trace=None):
+    """The TS variant (Alg. 4 around Alg. 8, readings T1-T4), two primes.
+    Returns (y, info) like ozfft."""
+    x = np.ascontiguousarray(x, dtype=np.complex128)
+    n = x.size
+    if N is None:
+        N = n if (n & (n - 1)) == 0 else 1 << (2 * n - 2).bit_length()
+    y = np.empty(n, dtype=np.complex128)
+    tr = Trace()
+    keep = {}
+    trace = set(trace or ())
+    kdim = K if K > 0 else KMAX
+    gdim = kdim * kdim
+    tr.kdim, tr.gdim = kdim, gdim
+    if "xprime" in trace:
+        keep["xprime"] = np.zeros((2, N)); tr.xprime = keep["xprime"].ctypes.data
+    if "q" in trace:
+        keep["q"] = np.zeros((4, kdim, N), dtype=np.int64); tr.q = keep["q"].ctypes.data
+    if "spec" in trace:
+        keep["spec"] = np.zeros((4, kdim, 2, N), dtype=np.uint32); tr.spec = keep["spec"].ctypes.data
+    if "groups" in trace:
+        keep["gS"] = np.zeros((4, gdim), dtype=np.int32); tr.gS = keep["gS"].ctypes.data
+        keep["gsize"] = np.zeros((4, gdim), dtype=np.int32); tr.gsize = keep["gsize"].ctypes.data
+        keep["gpairs"] = np.zeros((4, gdim, kdim, 2), dtype=np.int32); tr.gpairs = keep["gpairs"].ctypes.data
+    if "zres" in trace:
+        keep["zres"] = np.zeros((4, gdim, 2, N), dtype=np.uint32); tr.zres = keep["zres"].ctypes.data
+    if "yprime" in trace:
+        keep["yprime"] = np.zeros(n, dtype=np.complex128); tr.yprime = keep["yprime"].ctypes.data
+    st = lib().or_ozfft_ts(n, N, K, L, direction, _p(x), _p(y), C.byref(tr))
+    info = {"status": st, "alpha": tr.alpha, "rho": tr.rho, "N": N, "kcount": list(tr.kcount),
+            "sexp": [list(tr.sexp[v])[: tr.kcount[v]] for v in range(4)], "ngroups": list(tr.ngroups),
+            "n_fwd_runtime": tr.n_fwd_runtime, "n_fwd_plan": tr.n_fwd_plan, "n_inv": tr.n_inv}
+    info.update(keep)
+    if st:
+        raise OracleError(st, "ozfft_ts")
     return y, info
 
 

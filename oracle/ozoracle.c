@@ -840,3 +840,421 @@ void or_sincospi_q(uint64_t a, uint64_t d, double* out /* s_hi, s_lo, c_hi, c_lo
     store_q(s, &out[0], &out[1]);
     store_q(c, &out[2], &out[3]);
 }
+
+/* ========================================================================= */
+/* TS (triple-single) variant of the method (§4.1, Alg. 4, Alg. 6, Alg. 8).   */
+/*                                                                           */
+/* A TS number is a triple of binary32 values x0 + x1 + x2 (§4.1).  TSAdd and */
+/* TSMul follow the triple-word arithmetic of Fabiano, Muller and Picot      */
+/* (2019) in the form written here: exact transformations (2Sum, Fast2Sum,    */
+/* 2Prod with an FMA) produce the partial terms, VecSum adds them without     */
+/* error into a decreasing sequence, and the VecSumErrBranch renormalisation  */
+/* keeps three words.  Readings for this variant:                            */
+/*   T1  TS(x) of a binary64 x: x0 = RN32(x), x1 = RN32(x - x0),              */
+/*       x2 = RN32(x - x0 - x1) (differences exact in binary64), so every      */
+/*       binary64 in the binary32 exponent range converts exactly.           */
+/*   T2  rho = 24 - alpha with alpha = min(alpha of R5, 23), so rho >= 1 and  */
+/*       the split of Alg. 6 stays error free in binary32.                   */
+/*   T3  z' / c of Alg. 8: the CRT integer (|z'| < p0 p1 / 2 < 2^62) is       */
+/*       converted to TS exactly (three words of <= 24 bits) and each word   */
+/*       scaled by 2^-S by binary32 multiplications by powers of two.         */
+/*   T4  Alg. 8 runs once per real convolution (RR, II, IR, RI) with its own  */
+/*       TS accumulator, groups in schedule order; Re y' = TSSub(RR, II),    */
+/*       Im y' = TSAdd(IR, RI); y = y' (.) w in TS (Alg. 4); the binary64    */
+/*       result is (double(y0) + double(y1)) + double(y2), i.e. the exact sum */
+/*       rounded once; the inverse direction conjugates and divides by n in   */
+/*       binary64 (R8).  Two primes only.                                    */
+/* ========================================================================= */
+typedef struct { float w[3]; } ts3;
+
+static void f_two_sum(float a, float b, float* s, float* e)
+{
+    float ss = a + b;
+    float bb = ss - a;
+    float aa = ss - bb;
+    *s = ss;
+    *e = (a - aa) + (b - bb);
+}
+
+static void f_fast_two_sum(float a, float b, float* s, float* e)
+{
+    float ss = a + b;
+    *s = ss;
+    *e = b - (ss - a);
+}
+
+static void f_two_prod(float a, float b, float* p, float* e)
+{
+    float pp = a * b;
+    *p = pp;
+    *e = fmaf(a, b, -pp);
+}
+
+/* VecSum: x[0..n) -> x[0] = RN of the running sum from the last term up,
+   x[1..n) the exact errors, x[0] + ... + x[n-1] unchanged */
+static void f_vec_sum(float* x, int n)
+{
+    float s = x[n - 1];
+    for (int i = n - 2; i >= 0; --i) {
+        float e;
+        f_two_sum(x[i], s, &s, &e);
+        x[i + 1] = e;
+    }
+    x[0] = s;
+}
+
+/* VecSumErrBranch: renormalise e[0..n) into m words r (zeros where unused) */
+static void f_vec_sum_err_branch(const float* e, int n, int m, float* r)
+{
+    for (int k = 0; k < m; ++k) r[k] = 0.0f;
+    int j = 0;
+    float eps = e[0];
+    for (int i = 1; i < n; ++i) {
+        float s, t;
+        f_fast_two_sum(eps, e[i], &s, &t);
+        if (t != 0.0f) {
+            r[j] = s;
+            if (j == m - 1) return;
+            ++j;
+            eps = t;
+        } else {
+            eps = s;
+        }
+    }
+    r[j] = eps;
+}
+
+static ts3 ts_make(float a, float b, float c)
+{
+    ts3 t;
+    t.w[0] = a;
+    t.w[1] = b;
+    t.w[2] = c;
+    return t;
+}
+
+static ts3 ts_neg(ts3 a) { return ts_make(-a.w[0], -a.w[1], -a.w[2]); }
+
+/* TSAdd: the six words merged by decreasing magnitude, VecSum, renormalised */
+static ts3 ts_add(ts3 a, ts3 b)
+{
+    float z[6], r[3];
+    int i = 0, j = 0;
+    for (int k = 0; k < 6; ++k) {
+        if (j >= 3 || (i < 3 && fabsf(a.w[i]) >= fabsf(b.w[j]))) z[k] = a.w[i++];
+        else z[k] = b.w[j++];
+    }
+    f_vec_sum(z, 6);
+    f_vec_sum_err_branch(z, 6, 3, r);
+    return ts_make(r[0], r[1], r[2]);
+}
+
+static ts3 ts_sub(ts3 a, ts3 b) { return ts_add(a, ts_neg(b)); }
+
+/* TSMul: the products of weight 1 and 2^-24 exactly (2Prod), those of weight
+   2^-48 rounded, a1 b2 + a2 b1 + a2 b2 dropped; VecSum, renormalised */
+static ts3 ts_mul(ts3 a, ts3 b)
+{
+    float z00, e00, z01, e01, z10, e10, r[3];
+    f_two_prod(a.w[0], b.w[0], &z00, &e00);
+    f_two_prod(a.w[0], b.w[1], &z01, &e01);
+    f_two_prod(a.w[1], b.w[0], &z10, &e10);
+    float t[9] = {z00, z01, z10, e00, a.w[0] * b.w[2], a.w[1] * b.w[1], a.w[2] * b.w[0], e01, e10};
+    f_vec_sum(t, 9);
+    f_vec_sum_err_branch(t, 9, 3, r);
+    return ts_make(r[0], r[1], r[2]);
+}
+
+static ts3 ts_from_double(double x)    /* T1 */
+{
+    float a = (float)x;
+    double r1 = x - (double)a;
+    float b = (float)r1;
+    float c = (float)(r1 - (double)b);
+    return ts_make(a, b, c);
+}
+
+static double ts_to_double(ts3 a) { return ((double)a.w[0] + (double)a.w[1]) + (double)a.w[2]; }
+
+/* exact x 2^e in binary32 steps (each a product by a normal power of two) */
+static float f_scale_pow2(float x, int e)
+{
+    while (e > 127) { x *= 0x1p127f; e -= 127; }
+    while (e < -126) { x *= 0x1p-126f; e += 126; }
+    union { uint32_t u; float f; } p;
+    p.u = (uint32_t)(e + 127) << 23;
+    return x * p.f;
+}
+
+static ts3 ts_from_int_scaled(int64_t z, int S)   /* T3: z * 2^-S */
+{
+    float a = (float)z;
+    int64_t r1 = z - (int64_t)a;
+    float b = (float)r1;
+    int64_t r2 = r1 - (int64_t)b;
+    float c = (float)r2;
+    return ts_make(f_scale_pow2(a, -S), f_scale_pow2(b, -S), f_scale_pow2(c, -S));
+}
+
+/* exact ceil(log2 m) of a positive binary32 (R4) */
+static int ceil_log2_f(float m)
+{
+    int E;
+    float f = frexpf(m, &E);
+    return f == 0.5f ? E - 1 : E;
+}
+
+int or_alpha_ts(int64_t n, int L)    /* T2 */
+{
+    int a = or_alpha(n, L, 2);
+    return a > 23 ? 23 : a;
+}
+
+/* vector helpers exposed for the tests: cnt TS numbers as [cnt][3] floats */
+void or_ts_from_double(const double* x, int64_t cnt, float* out)
+{
+    for (int64_t i = 0; i < cnt; ++i) {
+        ts3 t = ts_from_double(x[i]);
+        memcpy(&out[3 * i], t.w, sizeof t.w);
+    }
+}
+
+void or_ts_to_double(const float* a, int64_t cnt, double* out)
+{
+    for (int64_t i = 0; i < cnt; ++i) out[i] = ts_to_double(ts_make(a[3 * i], a[3 * i + 1], a[3 * i + 2]));
+}
+
+void or_ts_op(int op, const float* a, const float* b, int64_t cnt, float* out)   /* 0 add, 1 sub, 2 mul */
+{
+    for (int64_t i = 0; i < cnt; ++i) {
+        ts3 x = ts_make(a[3 * i], a[3 * i + 1], a[3 * i + 2]);
+        ts3 y = ts_make(b[3 * i], b[3 * i + 1], b[3 * i + 2]);
+        ts3 r = op == 0 ? ts_add(x, y) : op == 1 ? ts_sub(x, y) : ts_mul(x, y);
+        memcpy(&out[3 * i], r.w, sizeof r.w);
+    }
+}
+
+/* Alg. 6 on one TS vector v[3][N] (planes of words 0, 1, 2): level k takes
+   mu = ||r0||_inf, sigma = 2^(ceil(log2 mu) + rho), x^(k) = fl32((r0 + sigma)
+   - sigma), then r0, r1 <- FastTwoSum(r0 - x^(k), r1) and r1, r2 <-
+   FastTwoSum(r1, r2); the integer q^(k) = c^(k) x^(k) with c^(k) = (u32
+   sigma)^-1 = 2^sexp[k].  Layout of q as or_split. */
+int or_ts_split(const float* v, int64_t N, int alpha, int Kcap, int kdim, int64_t* q, int32_t* sexp, int32_t* kout)
+{
+    if (alpha < 1 || alpha > 23) return OR_ERR_ARG;
+    const int rho = 24 - alpha;
+    float* r = (float*)malloc(sizeof(float) * 3 * (size_t)(N > 0 ? N : 1));
+    if (!r) return OR_ERR_ALLOC;
+    for (int64_t j = 0; j < 3 * N; ++j) {
+        if (!isfinite(v[j])) { free(r); return OR_ERR_NONFINITE; }
+        r[j] = v[j];
+    }
+    float* r0 = r;
+    float* r1 = r + N;
+    float* r2 = r + 2 * N;
+    int kmax = (Kcap <= 0 || Kcap > OR_KMAX) ? OR_KMAX : Kcap;
+    int k = 0, status = OR_OK;
+    for (; k < kmax; ++k) {
+        float mu = 0.0f;
+        for (int64_t j = 0; j < N; ++j) mu = fmaxf(mu, fabsf(r0[j]));
+        if (mu == 0.0f) break;
+        const int e = ceil_log2_f(mu);
+        if (e + rho > 127 || e + rho < -126) { status = OR_ERR_RANGE; break; }
+        const float sigma = f_scale_pow2(1.0f, e + rho);
+        for (int64_t j = 0; j < N; ++j) {
+            float s = (r0[j] + sigma) - sigma;
+            float a, b, c, d;
+            f_fast_two_sum(r0[j] - s, r1[j], &a, &b);
+            f_fast_two_sum(b, r2[j], &c, &d);
+            r0[j] = a;
+            r1[j] = c;
+            r2[j] = d;
+            if (k < kdim && q) q[(int64_t)k * N + j] = (int64_t)f_scale_pow2(s, alpha - e);
+        }
+        if (sexp && k < kdim) sexp[k] = alpha - e;
+    }
+    free(r);
+    *kout = k;
+    return status;
+}
+
+/* The TS variant of the whole method (T1-T4): Alg. 4 around Alg. 8, two primes. */
+int or_ozfft_ts(int64_t n, int64_t N, int K, int L, int direction, const double* x, double* y, or_trace* tr)
+{
+    const int nprimes = 2;
+    if (n < 1 || N < n || (N & (N - 1)) || L < 1 || K < 0 || !dir_ok(direction)) return OR_ERR_ARG;
+    if (!(N == n || N >= 2 * n - 1)) return OR_ERR_LENGTH;
+    for (int i = 0; i < nprimes; ++i)
+        if ((OR_PRIMES[i] - 1) % (uint64_t)N) return OR_ERR_LENGTH;
+    const int alpha = or_alpha_ts(n, L);
+    if (alpha < 1) return OR_ERR_LENGTH;
+    const size_t szN = (size_t)N;
+    const int kcap = K == 0 ? OR_KMAX : (K > OR_KMAX ? OR_KMAX : K);
+    int status = OR_OK, kq = 1;
+    double* w = (double*)malloc(sizeof(double) * 2 * (size_t)n);
+    float* tv = (float*)calloc(4 * 3 * szN, sizeof(float));   /* [v][word][N]: Re x', Im x', Re w*, Im w* */
+    ts3* wt = (ts3*)malloc(sizeof(ts3) * (size_t)n);             /* TS(w) */
+    ts3* acc = (ts3*)calloc(4 * (size_t)n, sizeof(ts3));        /* Alg. 8 accumulators of RR, II, IR, RI */
+    uint32_t* res = (uint32_t*)malloc(sizeof(uint32_t) * szN);
+    uint32_t* Z = (uint32_t*)malloc(sizeof(uint32_t) * nprimes * szN);
+    uint32_t* zr = (uint32_t*)malloc(sizeof(uint32_t) * nprimes * szN);
+    int64_t* q = NULL;
+    uint32_t* spec = NULL;
+    int32_t *gS = NULL, *gsz = NULL, *gp = NULL;
+    int32_t kcount[4] = {0, 0, 0, 0};
+    int32_t sexp[4][OR_KMAX];
+    int64_t nfr = 0, nfp = 0, ninv = 0;
+    if (!w || !tv || !wt || !acc || !res || !Z || !zr) { status = OR_ERR_ALLOC; goto done; }
+
+    /* Alg. 4 steps 1-2: TS conversion (T1) and x' = x (.) w in TS */
+    or_chirp(n, w);
+    for (int64_t j = 0; j < n; ++j) {
+        double xr = x[2 * j], xi = x[2 * j + 1];
+        if (!isfinite(xr) || !isfinite(xi)) { status = OR_ERR_NONFINITE; goto done; }
+        if (dir_conj(direction)) xi = -xi;
+        ts3 a = ts_from_double(xr), b = ts_from_double(xi);
+        ts3 c = ts_from_double(w[2 * j]), d = ts_from_double(w[2 * j + 1]);
+        wt[j] = c;   /* real part; the imaginary part is rebuilt from w below */
+        ts3 re = ts_sub(ts_mul(a, c), ts_mul(b, d));
+        ts3 im = ts_add(ts_mul(a, d), ts_mul(b, c));
+        for (int k = 0; k < 3; ++k) {
+            if (!isfinite(re.w[k]) || !isfinite(im.w[k])) { status = OR_ERR_RANGE; goto done; }
+            tv[(0 * 3 + k) * szN + j] = re.w[k];
+            tv[(1 * 3 + k) * szN + j] = im.w[k];
+        }
+    }
+    /* w~* = ZeroPad+-(conj w) in TS (exact, T1) */
+    for (int64_t j = 0; j < N; ++j) {
+        int64_t src = -1;
+        if (j < n) src = j;
+        else if (N != n && j >= N - n + 1) src = N - j;
+        if (src < 0) continue;
+        ts3 a = ts_from_double(w[2 * src]), b = ts_from_double(-w[2 * src + 1]);
+        for (int k = 0; k < 3; ++k) {
+            tv[(2 * 3 + k) * szN + j] = a.w[k];
+            tv[(3 * 3 + k) * szN + j] = b.w[k];
+        }
+    }
+    if (tr && tr->xprime)   /* x~' rounded to binary64, for inspection */
+        for (int v = 0; v < 2; ++v)
+            for (int64_t j = 0; j < N; ++j)
+                tr->xprime[(size_t)v * szN + j] = ts_to_double(ts_make(tv[(v * 3) * szN + j], tv[(v * 3 + 1) * szN + j],
+                                                                      tv[(v * 3 + 2) * szN + j]));
+
+    /* Alg. 6 on the four TS vectors: level counts first, then the integers */
+    for (int v = 0; v < 4 && status == OR_OK; ++v)
+        status = or_ts_split(&tv[(size_t)v * 3 * szN], N, alpha, kcap, OR_KMAX, NULL, sexp[v], &kcount[v]);
+    if (status != OR_OK) goto done;
+    for (int v = 0; v < 4; ++v) kq = kcount[v] > kq ? kcount[v] : kq;
+    q = (int64_t*)malloc(sizeof(int64_t) * 4 * (size_t)kq * szN);
+    spec = (uint32_t*)malloc(sizeof(uint32_t) * 4 * (size_t)kq * nprimes * szN);
+    gS = (int32_t*)malloc(sizeof(int32_t) * 4 * (size_t)kq * kq);
+    gsz = (int32_t*)malloc(sizeof(int32_t) * 4 * (size_t)kq * kq);
+    gp = (int32_t*)malloc(sizeof(int32_t) * 4 * (size_t)kq * kq * kq * 2);
+    if (!q || !spec || !gS || !gsz || !gp) { status = OR_ERR_ALLOC; goto done; }
+    for (int v = 0; v < 4 && status == OR_OK; ++v) {
+        int32_t kv;
+        status = or_ts_split(&tv[(size_t)v * 3 * szN], N, alpha, kcap, kq, &q[(size_t)v * kq * szN], sexp[v], &kv);
+    }
+    if (status != OR_OK) goto done;
+
+    /* residues and forward NTTs (Alg. 6 tail), as in the binary64 variant */
+    for (int v = 0; v < 4; ++v)
+        for (int k = 0; k < kcount[v]; ++k)
+            for (int i = 0; i < nprimes; ++i) {
+                int64_t p = (int64_t)OR_PRIMES[i];
+                const int64_t* qk = &q[((size_t)v * kq + k) * szN];
+                for (int64_t j = 0; j < N; ++j) {
+                    int64_t a = qk[j] % p;
+                    res[j] = (uint32_t)(a < 0 ? a + p : a);
+                }
+                or_ntt(res, &spec[(((size_t)v * kq + k) * nprimes + i) * szN], N, (uint64_t)p, 0);
+                if (v < 2) ++nfr; else ++nfp;
+            }
+
+    /* Alg. 8 per real convolution, accumulating z'/c with TSAdd (T3, T4) */
+    const size_t gstride = (size_t)kq * kq;
+    for (int c = 0; c < 4; ++c) {
+        int vx = CONV_X[c], vw = CONV_W[c];
+        int ng = or_schedule(kcount[vx], sexp[vx], kcount[vw], sexp[vw], L, kq * kq, kq, &gS[c * gstride],
+                             &gsz[c * gstride], &gp[c * gstride * kq * 2]);
+        if (ng < 0) { status = OR_ERR_ARG; goto done; }
+        if (tr) tr->ngroups[c] = ng;
+        const int32_t* cp = &gp[c * gstride * kq * 2];
+        for (int g = 0; g < ng; ++g) {
+            for (int i = 0; i < nprimes; ++i) {
+                uint64_t p = OR_PRIMES[i];
+                uint32_t* Zi = &Z[(size_t)i * szN];
+                memset(Zi, 0, sizeof(uint32_t) * szN);
+                for (int m = 0; m < gsz[c * gstride + g]; ++m) {
+                    int s = cp[((size_t)g * kq + m) * 2], t = cp[((size_t)g * kq + m) * 2 + 1];
+                    const uint32_t* X = &spec[(((size_t)vx * kq + s) * nprimes + i) * szN];
+                    const uint32_t* Y = &spec[(((size_t)vw * kq + t) * nprimes + i) * szN];
+                    for (int64_t j = 0; j < N; ++j) Zi[j] = (uint32_t)((Zi[j] + mulmod(X[j], Y[j], p)) % p);
+                }
+                or_ntt(Zi, &zr[(size_t)i * szN], N, p, 1);
+                ++ninv;
+            }
+            const int S = gS[c * gstride + g];
+            uint32_t z3[3] = {0, 0, 0};
+            for (int64_t j = 0; j < n; ++j) {
+                for (int i = 0; i < nprimes; ++i) z3[i] = zr[(size_t)i * szN + j];
+                const i128 zc = garner(z3, nprimes);
+                acc[(size_t)c * n + j] = ts_add(acc[(size_t)c * n + j], ts_from_int_scaled((int64_t)zc, S));
+            }
+            if (tr && g < tr->gdim) {
+                if (tr->gS) tr->gS[c * tr->gdim + g] = S;
+                if (tr->gsize) tr->gsize[c * tr->gdim + g] = gsz[c * gstride + g];
+                if (tr->gpairs)
+                    for (int m = 0; m < gsz[c * gstride + g] && m < tr->kdim; ++m) {
+                        tr->gpairs[(((size_t)c * tr->gdim + g) * tr->kdim + m) * 2] = cp[((size_t)g * kq + m) * 2];
+                        tr->gpairs[(((size_t)c * tr->gdim + g) * tr->kdim + m) * 2 + 1] =
+                            cp[((size_t)g * kq + m) * 2 + 1];
+                    }
+                if (tr->zres)
+                    memcpy(&tr->zres[((size_t)c * tr->gdim + g) * nprimes * szN], zr,
+                           sizeof(uint32_t) * nprimes * szN);
+            }
+        }
+    }
+
+    /* y' = (RR - II) + i (IR + RI), y = y' (.) w in TS, then binary64 (T4) */
+    for (int64_t j = 0; j < n; ++j) {
+        ts3 yr = ts_sub(acc[j], acc[(size_t)n + j]);
+        ts3 yi = ts_add(acc[2 * (size_t)n + j], acc[3 * (size_t)n + j]);
+        if (tr && tr->yprime) { tr->yprime[2 * j] = ts_to_double(yr); tr->yprime[2 * j + 1] = ts_to_double(yi); }
+        ts3 c = wt[j], d = ts_from_double(w[2 * j + 1]);
+        ts3 re = ts_sub(ts_mul(yr, c), ts_mul(yi, d));
+        ts3 im = ts_add(ts_mul(yr, d), ts_mul(yi, c));
+        double a = ts_to_double(re), b = ts_to_double(im);
+        if (dir_conj(direction)) b = -b;
+        if (dir_scaled(direction)) { a = a / (double)n; b = b / (double)n; }
+        y[2 * j] = a;
+        y[2 * j + 1] = b;
+    }
+
+done:
+    if (tr) {
+        tr->alpha = alpha;
+        tr->rho = 24 - alpha;
+        for (int v = 0; v < 4; ++v) {
+            tr->kcount[v] = kcount[v];
+            for (int k = 0; k < kcount[v] && k < OR_KMAX; ++k) tr->sexp[v][k] = sexp[v][k];
+        }
+        tr->n_fwd_runtime = nfr;
+        tr->n_fwd_plan = nfp;
+        tr->n_inv = ninv;
+        if (tr->q && q)
+            for (int v = 0; v < 4; ++v)
+                for (int k = 0; k < kcount[v] && k < tr->kdim; ++k)
+                    memcpy(&tr->q[((size_t)v * tr->kdim + k) * szN], &q[((size_t)v * kq + k) * szN], sizeof(int64_t) * szN);
+        if (tr->spec && spec)
+            for (int v = 0; v < 4; ++v)
+                for (int k = 0; k < kcount[v] && k < tr->kdim; ++k)
+                    memcpy(&tr->spec[(((size_t)v * tr->kdim + k) * nprimes) * szN],
+                           &spec[(((size_t)v * kq + k) * nprimes) * szN], sizeof(uint32_t) * nprimes * szN);
+    }
+    free(w); free(tv); free(wt); free(acc); free(res); free(Z); free(zr);
+    free(q); free(spec); free(gS); free(gsz); free(gp);
+    return status;
+}
