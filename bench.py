@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--cpu-signals", type=int, default=2, help="oracle transforms timed for cpu_baseline")
     ap.add_argument("--autotune", action="store_true", help="autotune the NTT column/row split at plan time")
     ap.add_argument("--merge", action="store_true", help="merged schedules across the convolutions of a part")
+    ap.add_argument("--ts", action="store_true", help="the TS (triple-single) variant of the method")
     ap.add_argument("--uneven-count", type=int, default=4096, help="signals of the uneven workload")
     ap.add_argument("--plain-sample", type=int, default=256,
                     help="signals of the uneven workload timed through per-signal plans")
@@ -76,7 +77,7 @@ def workload(a):
     return {"workload": f"complex128 n=2^{a.n.bit_length() - 1} x {a.batch} signals, uniform[-1,1) parts, "
                         f"forward, K={a.K}, L={a.L}, {a.nprimes} primes",
             "n": a.n, "batch_per_gpu": a.batch, "K": a.K, "L": a.L, "nprimes": a.nprimes, "seed": a.seed,
-            "autotune": a.autotune, "merge": a.merge,
+            "autotune": a.autotune, "merge": a.merge, "ts": a.ts,
             "l2": "inputs (batch x n x 16 B) exceed L2 each step; no flush"}
 
 
@@ -532,7 +533,8 @@ def main():
     x = x_pin.to(dev)
     y = torch.empty_like(x)
     stream = torch.cuda.current_stream(dev)
-    plan = ozfft.Plan(n, B, ozfft.FORWARD, K=a.K, L=a.L, nprimes=a.nprimes, autotune=a.autotune, merge=a.merge)
+    plan = ozfft.Plan(n, B, ozfft.FORWARD, K=a.K, L=a.L, nprimes=a.nprimes, autotune=a.autotune, merge=a.merge,
+                      ts=a.ts)
 
     # ---- batched, device-resident (the headline value), with per-kernel events
     for _ in range(a.warmup):
@@ -563,7 +565,8 @@ def main():
     # ---- plain pipeline: one execution of a batch-1 plan per transform
     plain = None
     if not a.skip_plain:
-        p1 = ozfft.Plan(n, 1, ozfft.FORWARD, K=a.K, L=a.L, nprimes=a.nprimes, autotune=a.autotune, merge=a.merge)
+        p1 = ozfft.Plan(n, 1, ozfft.FORWARD, K=a.K, L=a.L, nprimes=a.nprimes, autotune=a.autotune, merge=a.merge,
+                        ts=a.ts)
         xs = [x[i:i + 1] for i in range(B)]
         ys = [y[i:i + 1] for i in range(B)]
         for _ in range(a.warmup):
@@ -653,7 +656,8 @@ def main():
         t0 = time.perf_counter()
         same = True
         for i in range(a.cpu_signals):
-            yo, _ = oracle.ozfft(x_host[i], K=a.K, L=a.L, nprimes=a.nprimes)
+            yo, _ = (oracle.ozfft_ts(x_host[i], K=a.K, L=a.L) if a.ts
+                     else oracle.ozfft(x_host[i], K=a.K, L=a.L, nprimes=a.nprimes))
             same = same and np.array_equal(yo.view(np.uint64), y[i].cpu().numpy().view(np.uint64))
         dt = time.perf_counter() - t0
         acc["bit_exact_vs_oracle"] = f"{a.cpu_signals} signals: {'yes' if same else 'NO'}"

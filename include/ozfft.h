@@ -91,6 +91,12 @@ typedef struct {
                          per transform and prime pair without gaps); the result is bit-identical
                          to merge = 0 with the same L, since y' is the exactly rounded sum of the
                          same products either way */
+    int32_t ts;       /* nonzero: the TS (triple-single) variant of §4.1 (Alg. 4, Alg. 6, Alg. 8):
+                         chirp products and the split in TS arithmetic (three binary32 words,
+                         rho = 24 - alpha, alpha capped at 23), the rescaled CRT integers
+                         accumulated per real convolution with TSAdd, the post-multiply in TS and
+                         the result rounded to binary64.  Two primes, plain plans only; inputs
+                         must stay inside the binary32 exponent range (else OZFFT_ERR_RANGE) */
 } ozfft_options;
 
 /* Create a plan for `batch` transforms of length n in `direction`, with default

@@ -25,7 +25,7 @@
  * Readings of points the paper leaves open (all repeated in the design notes):
  *   R1  precision: the FFT input, the chirp products and the split are binary64
  *       (u = 2^-53, rho = 53 - alpha); the paper's TS (3 x binary32) variant is
- *       not this oracle's subject.
+ *       the separate or_ozfft_ts at the end of this file (readings T1-T4).
  *   R2  chirp table: w(j) = exp(-i*pi*r/n), r = j^2 mod 2n, correctly rounded to
  *       binary64 (§4.2 assumes correctly rounded tables); evaluated in binary128
  *       after an exact octant reduction of r/n; components equal to zero are +0.

@@ -21,6 +21,7 @@
 // thread in shared memory.
 #include "oz_common.cuh"
 #include "oz_kernels.h"
+#include "ts_arith.cuh"
 
 namespace oz {
 
@@ -471,6 +472,54 @@ cudaError_t launch_crt_post(const CrtArgs& a, cudaStream_t s)
     const int64_t grid = a.B * chunks < 1024 ? a.B * chunks : 1024;
     if (sd) crt_wide_kernel<true><<<(unsigned)grid, WIDE_THREADS, smem, s>>>(a);
     else crt_wide_kernel<false><<<(unsigned)grid, WIDE_THREADS, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+// TS variant (Alg. 8 per real convolution, TS accumulation): for each output
+// element, each convolution's groups in schedule order add z'/c = z' 2^-S to
+// a TS accumulator with TSAdd; Re y' = TSSub(RR, II), Im y' = TSAdd(IR, RI);
+// y = y' (.) w in TS (Alg. 4 step 4), then binary64 (the exact sum of the three
+// words rounded once); the inverse and adjoint directions as in post_store.
+__global__ void __launch_bounds__(FAST_THREADS) crt_ts_kernel(CrtArgs a)
+{
+    const int64_t chunks = (a.n + CRT_CHUNK - 1) / CRT_CHUNK;
+    const int64_t b = blockIdx.x / chunks;
+    const int64_t j0 = (blockIdx.x % chunks) * (int64_t)CRT_CHUNK;
+    const int64_t j1 = min(a.n, j0 + CRT_CHUNK);
+    const Sched* sc = a.sched + b * 4;
+    for (int64_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
+        ts3 acc[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            acc[c] = ts3{0.0f, 0.0f, 0.0f};
+            const Sched& S = sc[c];
+            const uint32_t* zp = a.Z + ((b * 4 + c) * a.G) * 2 * a.N + j;
+            for (int g = 0; g < S.ngroups; ++g) {
+                const uint32_t z0 = __ldg(zp + (int64_t)g * 2 * a.N), z1 = __ldg(zp + (int64_t)g * 2 * a.N + a.N);
+                acc[c] = ts_add(acc[c], ts_from_int_scaled(garner2(z0, z1), S.S[g]));
+            }
+        }
+        const ts3 yr = ts_sub(acc[0], acc[1]), yi = ts_add(acc[2], acc[3]);
+        const double2 wv = a.w[j];
+        const ts3 wc = ts_from_double(wv.x), wd = ts_from_double(wv.y);
+        const ts3 re = ts_sub(ts_mul(yr, wc), ts_mul(yi, wd));
+        const ts3 im = ts_add(ts_mul(yr, wd), ts_mul(yi, wc));
+        double x = ts_to_double(re), y = ts_to_double(im);
+        if (a.direction > 0) y = -y;
+        if (a.direction == 1 || a.direction == -2) {
+            x = __ddiv_rn(x, (double)a.n);
+            y = __ddiv_rn(y, (double)a.n);
+        }
+        a.out[b * a.n + j] = make_double2(x, y);
+    }
+}
+
+cudaError_t launch_crt_ts(const CrtArgs& a, cudaStream_t s)
+{
+    cudaError_t e = crt_init();
+    if (e != cudaSuccess) return e;
+    const int64_t chunks = (a.n + CRT_CHUNK - 1) / CRT_CHUNK;
+    crt_ts_kernel<<<(unsigned)(a.B * chunks), FAST_THREADS, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -93,5 +93,14 @@ struct CrtArgs {
 int crt_launches();        // kernels per launch_crt_post
 cudaError_t crt_init();    // uploads the Garner constants (once; call before any stream capture)
 cudaError_t launch_crt_post(const CrtArgs& a, cudaStream_t s);
+cudaError_t launch_crt_ts(const CrtArgs& a, cudaStream_t s);   // TS variant (two primes)
+
+// k_ts.cu: the TS variant's pre-multiply, w~* and split (TS vectors are three
+// binary32 word planes r[v][0..2][N])
+cudaError_t launch_ts_premul(const double2* x, const double2* w, int64_t n, int64_t N, int64_t B, int conj_in,
+                             float* r, uint64_t* mu, int K, int* status, cudaStream_t s);
+cudaError_t launch_ts_wstar(const double2* w, int64_t n, int64_t N, float* r, uint64_t* mu, int K, cudaStream_t s);
+cudaError_t launch_ts_split_level(int k, float* r, uint64_t* mu, int64_t N, int64_t nvec, int K, int alpha, int P,
+                                  uint32_t* X, int write_r, int* status, cudaStream_t s);
 
 }  // namespace oz

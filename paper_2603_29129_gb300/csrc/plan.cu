@@ -48,7 +48,7 @@ static int fail(int code, const std::string& msg)
 
 struct ozfft_plan_s {
     int64_t n = 0, N = 0, B = 0;
-    int direction = -1, K = 3, L = 1, P = 2, alpha = 0, G = 9, debug = 0, merge = 0;
+    int direction = -1, K = 3, L = 1, P = 2, alpha = 0, G = 9, debug = 0, merge = 0, ts = 0;
     int64_t chunk = 1;           // signals per inverse-stage chunk (Z holds one chunk)
     int device = 0;
     NttGeom geom_fwd{}, geom_inv{};
@@ -416,7 +416,8 @@ static int plan_build(ozfft_plan_s* p)
     if ((rc = dalloc(p, &p->Ym, (size_t)BW * 2 * K * P * N))) return rc;
     if ((rc = dalloc(p, &p->wk, (size_t)BW * 2))) return rc;
     if ((rc = dalloc(p, &p->wsexp, (size_t)BW * 2 * K))) return rc;
-    if ((rc = dalloc(p, &p->r, (size_t)B * 2 * N))) return rc;
+    // r: binary64 residuals [B][2][N], or (TS) three binary32 word planes per vector [B][2][3][N]
+    if ((rc = dalloc(p, &p->r, (size_t)B * (p->ts ? 3 : 2) * N))) return rc;
     if ((rc = dalloc(p, &p->mu, (size_t)B * 2 * (K + 1)))) return rc;
     if ((rc = dalloc(p, &p->X, (size_t)B * 2 * K * P * N))) return rc;
     if ((rc = dalloc(p, &p->kcnt, (size_t)B * 2))) return rc;
@@ -450,10 +451,17 @@ static int plan_build(ozfft_plan_s* p)
     }
     {
         CUDA_TRY(cudaMemset(p->mu, 0, sizeof(uint64_t) * BW * 2 * (K + 1)));
-        CUDA_TRY(launch_wstar(p->chirp, p->n, N, BW, p->sd, p->r, p->mu, K, p->status, s));
-        for (int k = 0; k < K; ++k)
-            CUDA_TRY(launch_split_level(k, p->r, p->mu, p->mu, N, BW * 2, K, p->alpha, p->sd, P, p->Ym, k + 1 < K,
-                                        p->status, s));
+        if (p->ts) {
+            CUDA_TRY(launch_ts_wstar(p->chirp, p->n, N, (float*)p->r, p->mu, K, s));
+            for (int k = 0; k < K; ++k)
+                CUDA_TRY(launch_ts_split_level(k, (float*)p->r, p->mu, N, 2, K, p->alpha, P, p->Ym, k + 1 < K,
+                                               p->status, s));
+        } else {
+            CUDA_TRY(launch_wstar(p->chirp, p->n, N, BW, p->sd, p->r, p->mu, K, p->status, s));
+            for (int k = 0; k < K; ++k)
+                CUDA_TRY(launch_split_level(k, p->r, p->mu, p->mu, N, BW * 2, K, p->alpha, p->sd, P, p->Ym,
+                                            k + 1 < K, p->status, s));
+        }
         std::vector<uint64_t> hmu((size_t)BW * 2 * (K + 1));
         CUDA_TRY(cudaMemcpy(hmu.data(), p->mu, sizeof(uint64_t) * hmu.size(), cudaMemcpyDeviceToHost));
         std::vector<int32_t> sexp((size_t)BW * 2 * K, 0), wk((size_t)BW * 2, 0);
@@ -466,7 +474,8 @@ static int plan_build(ozfft_plan_s* p)
                     double m;
                     std::memcpy(&m, &hmu[(b * 2 + v) * (K + 1) + k], sizeof m);
                     if (!(m > 0.0)) break;
-                    if (ceil_log2_h(m) + 53 - alpha > 1023) return fail(OZFFT_ERR_RANGE, "w* scale");
+                    if (p->ts ? ceil_log2_h(m) + 24 - alpha > 127 : ceil_log2_h(m) + 53 - alpha > 1023)
+                        return fail(OZFFT_ERR_RANGE, "w* scale");
                     sexp[(b * 2 + v) * K + k] = alpha - ceil_log2_h(m);
                 }
                 wk[b * 2 + v] = k;
@@ -504,7 +513,7 @@ static int plan_build(ozfft_plan_s* p)
     p->geom_inv.sched = p->sched;
     const int64_t nchunks = (B + p->chunk - 1) / p->chunk;
     p->launches = 1 /*premul*/ + K /*split*/ + 1 /*schedule*/ + ntt_launches(p->geom_fwd) +
-                  nchunks * (ntt_launches(p->geom_inv) + crt_launches());
+                  nchunks * (ntt_launches(p->geom_inv) + (p->ts ? 1 : crt_launches()));
     CUDA_TRY(crt_init());
     return OZFFT_OK;
 }
@@ -589,7 +598,8 @@ static int autotune_ntt(ozfft_plan_s* p)
     p->geom_inv.nvec = gi.nvec; p->geom_inv.P = gi.P; p->geom_inv.K = gi.K; p->geom_inv.G = gi.G;
     p->geom_inv.kcnt = gi.kcnt; p->geom_inv.sched = gi.sched;
     const int64_t nchunks = (B + p->chunk - 1) / p->chunk;
-    p->launches = 1 + K + 1 + ntt_launches(p->geom_fwd) + nchunks * (ntt_launches(p->geom_inv) + crt_launches());
+    p->launches = 1 + K + 1 + ntt_launches(p->geom_fwd) +
+                  nchunks * (ntt_launches(p->geom_inv) + (p->ts ? 1 : crt_launches()));
     return OZFFT_OK;
 }
 
@@ -610,13 +620,22 @@ static int run_plan(ozfft_plan_s* p, const void* in, void* out, cudaStream_t s)
             p->cur = &p->pending.back();
         }
     }
-    CUDA_TRY(launch_premul((const double2*)in, p->chirp, p->n, N, B, p->direction > 0, p->sd, p->io_ref, p->r, p->mu,
-                           K, p->status, s));
+    if (p->ts)
+        CUDA_TRY(launch_ts_premul((const double2*)in, p->chirp, p->n, N, B, p->direction > 0, (float*)p->r, p->mu, K,
+                                  p->status, s));
+    else
+        CUDA_TRY(launch_premul((const double2*)in, p->chirp, p->n, N, B, p->direction > 0, p->sd, p->io_ref, p->r,
+                               p->mu, K, p->status, s));
     mark(p, OZFFT_PROF_PREMUL, s);
-    if (p->debug) CUDA_TRY(cudaMemcpyAsync(p->dbg_r, p->r, sizeof(double) * B * 2 * N, cudaMemcpyDeviceToDevice, s));
+    if (p->debug && !p->ts)
+        CUDA_TRY(cudaMemcpyAsync(p->dbg_r, p->r, sizeof(double) * B * 2 * N, cudaMemcpyDeviceToDevice, s));
     for (int k = 0; k < K; ++k) {
-        CUDA_TRY(launch_split_level(k, p->r, p->mu, p->mu, N, B * 2, K, p->alpha, p->sd, p->P, p->X, k + 1 < K,
-                                    p->status, s));
+        if (p->ts)
+            CUDA_TRY(launch_ts_split_level(k, (float*)p->r, p->mu, N, B * 2, K, p->alpha, p->P, p->X, k + 1 < K,
+                                           p->status, s));
+        else
+            CUDA_TRY(launch_split_level(k, p->r, p->mu, p->mu, N, B * 2, K, p->alpha, p->sd, p->P, p->X, k + 1 < K,
+                                        p->status, s));
         mark(p, OZFFT_PROF_SPLIT, s);
     }
     if (p->debug)
@@ -647,7 +666,8 @@ static int run_plan(ozfft_plan_s* p, const void* in, void* out, cudaStream_t s)
         CrtArgs ca{p->Z, p->sched + b0 * 4, p->span + b0 * 3, p->chirp,
                    p->sd ? (double2*)out : (double2*)out + b0 * p->n, p->n, N, nb,
                    p->P, p->G, p->direction, p->status, p->sd ? p->sd + b0 : nullptr, p->io_ref, p->merge};
-        CUDA_TRY(launch_crt_post(ca, s));
+        if (p->ts) CUDA_TRY(launch_crt_ts(ca, s));
+        else CUDA_TRY(launch_crt_post(ca, s));
         if (b0 + p->chunk < B) mark(p, OZFFT_PROF_CRT, s);
     }
     mark(p, OZFFT_PROF_CRT, s);
@@ -708,7 +728,12 @@ ozfft_plan_t ozfft_plan_ex(int64_t n, int64_t batch, int direction, const ozfft_
         fail(OZFFT_ERR_LENGTH, "ozfft_plan: convolution length must be a power of two <= 2^24, equal to n or >= 2n-1");
         return nullptr;
     }
-    const int alpha = alpha_h(n, L, P);
+    if (o.ts && (P != 2 || o.merge)) {
+        fail(OZFFT_ERR_ARG, "ozfft_plan: the TS variant takes two primes and no merged schedules");
+        return nullptr;
+    }
+    int alpha = alpha_h(n, L, P);
+    if (o.ts && alpha > 23) alpha = 23;   // rho = 24 - alpha >= 1 in binary32
     if (alpha < 1) {
         fail(OZFFT_ERR_LENGTH, "ozfft_plan: no split width alpha >= 1 for this n, L and prime count");
         return nullptr;
@@ -725,6 +750,7 @@ ozfft_plan_t ozfft_plan_ex(int64_t n, int64_t batch, int direction, const ozfft_
     p->alpha = alpha;
     p->debug = o.debug;
     p->merge = o.merge != 0;
+    p->ts = o.ts != 0;
     {
         const int64_t zbytes = (int64_t)4 * p->G * P * N * 4;   // Z of one signal
         int64_t c = o.chunk > 0 ? o.chunk : std::max<int64_t>(1, (int64_t(16) << 30) / zbytes);
@@ -756,7 +782,8 @@ ozfft_plan_t ozfft_plan_many(const int64_t* lengths, int64_t count, int directio
     const int K = o.K ? o.K : 3, L = o.L ? o.L : 1, P = o.nprimes ? o.nprimes : 2;
     if (!lengths || count < 1 || (direction != OZFFT_FORWARD && direction != OZFFT_INVERSE &&
                                   direction != OZFFT_ADJOINT && direction != OZFFT_INVERSE_ADJOINT) ||
-        K < 1 || K > MAX_K || L < 1 || L > MAX_L || P < 2 || P > 3 || o.conv_len != 0 || o.debug != 0 || o.chunk < 0) {
+        K < 1 || K > MAX_K || L < 1 || L > MAX_L || P < 2 || P > 3 || o.conv_len != 0 || o.debug != 0 || o.chunk < 0 ||
+        o.ts != 0) {
         fail(OZFFT_ERR_ARG, "ozfft_plan_many: argument out of range");
         return nullptr;
     }
