@@ -609,37 +609,59 @@ def main():
 
     # ---- roofline of the dominant kernel (live CUDA events over the timed region)
     N = plan.N
+    lgN = N.bit_length() - 1
     runtime_fwd = stats["ntt_forward_runtime"]        # live forward vectors per execution
     inv_vecs = stats["ntt_inverse"]                   # live inverse vectors per execution
-    # algorithmic bytes per launch: every pass reads and writes each live vector once (4N + 4N);
+    m2f, m2i = stats["row_log_fwd"], stats["row_log_inv"]
+    # algorithmic bytes per execution: every pass reads and writes each live vector once (4N + 4N);
     # the fused multiply-accumulate reads X_s and Ym_t (4N each) per product instead of Z
     prods = sum(len(pairs) for b in range(B) for conv in plan.dump(ozfft.DUMP_SCHED, b)
                 for _, pairs in conv) * a.nprimes
     alg = {"ntt_fwd_col": 8 * N * runtime_fwd, "ntt_fwd_row": 8 * N * runtime_fwd,
            "ntt_inv_col": 8 * N * inv_vecs, "ntt_inv_row": 8 * N * prods + 4 * N * inv_vecs,
            "premul": B * (16 * n + 16 * n + 16 * N), "crt": 4 * n * inv_vecs + B * 32 * n}
+    # algorithmic modular multiplications per execution: one per radix-2 butterfly
+    # ((N/2) per stage and vector) and one per NTT-domain product and element
+    mm = {"ntt_fwd_col": runtime_fwd * (lgN - m2f) * N // 2, "ntt_fwd_row": runtime_fwd * m2f * N // 2,
+          "ntt_inv_col": inv_vecs * (lgN - m2i) * N // 2, "ntt_inv_row": inv_vecs * m2i * N // 2 + prods * N}
     slots = prof["slots"]
     dom = max(slots, key=lambda k: slots[k]["ms"])
     execs = max(1, prof["executions"])
     launches_per_exec = max(1, slots[dom]["launches"] // execs)
     dom_ms = slots[dom]["ms"] / max(1, slots[dom]["launches"])
     pk = peaks()
+    hbm_peak = pk["hbm_gbs"] if pk else 6800.0
     roof = None
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if os.path.exists(tfile):
+        t = json.load(open(tfile))
+        ent = t.get(dom)
+        if ent and ent.get("source_hash") == kernel_source_hash() and ent.get("config") == f"n={n},B={B},L={a.L}":
+            traffic = ent.get("bytes_per_launch")
+    hbm_view = None
     if alg.get(dom):
         alg_launch = alg[dom] / launches_per_exec          # the slot's bytes are per execution
-        achieved = alg_launch / (dom_ms / 1e3) / 1e9
-        peak = pk["hbm_gbs"] if pk else 6800.0
-        traffic = None
-        tfile = os.path.join(ROOT, "profiles", "ncu_traffic.json")
-        if os.path.exists(tfile):
-            t = json.load(open(tfile))
-            ent = t.get(dom)
-            if ent and ent.get("source_hash") == kernel_source_hash() and ent.get("config") == f"n={n},B={B},L={a.L}":
-                traffic = ent.get("bytes_per_launch")
-        roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic,
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if pk else "fallback 6.8 TB/s",
-                "algorithmic_bytes_per_launch": alg_launch, "launch_ms": dom_ms}
+        hbm_view = {"achieved": alg_launch / (dom_ms / 1e3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": alg_launch / (dom_ms / 1e3) / 1e9 / hbm_peak,
+                    "algorithmic_bytes_per_launch": alg_launch,
+                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if pk else "fallback 6.8 TB/s"}
+    if mm.get(dom):
+        # integer roofline: the NTT kernels are bound by integer issue (ncu: DRAM well below
+        # peak, issue slots busy); peak = 152 SMs x 4 schedulers x 32 lanes x 2.07 GHz lane
+        # instructions / 11 instructions per canonical Shoup butterfly
+        mm_launch = mm[dom] / launches_per_exec
+        peak_derived = 152 * 4 * 32 * 2.07e9 / 11 / 1e12
+        inv = dom.startswith("ntt_inv")
+        measured = ozfft.butterfly_rate(inverse=inv) / 1e12
+        achieved = mm_launch / (dom_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak_derived, "unit": "Tmodmul/s",
+                "frac": achieved / peak_derived, "traffic": traffic,
+                "peak_source": "derived: 152 SMs x 4 x 32 lanes x 2.07 GHz / 11 integer instructions per butterfly",
+                "peak_measured_registers": measured, "frac_of_measured": achieved / measured,
+                "modmuls_per_launch": mm_launch, "launch_ms": dom_ms, "hbm_view": hbm_view}
+    elif hbm_view:
+        roof = dict(hbm_view, bound="hbm", kernel=dom, traffic=traffic, launch_ms=dom_ms)
     total_ntt = runtime_fwd + inv_vecs
     ntt_ms = sum(slots[k]["ms"] for k in slots if k.startswith("ntt")) / execs
     breakdown = {k: round(v["ms"] / execs, 4) for k, v in slots.items()}

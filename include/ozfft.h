@@ -153,6 +153,8 @@ typedef struct {
     int64_t ntt_inverse;          /* inverse NTTs, summed over the batch */
     int64_t kernel_launches;      /* kernels enqueued by one ozfft_execute */
     int64_t workspace_bytes;      /* device memory held by the plan */
+    int32_t row_log_fwd;          /* forward NTT: stages in the row pass (the rest in the column pass) */
+    int32_t row_log_inv;          /* inverse NTT: stages in the row pass (uneven plans: of the largest N) */
 } ozfft_stats;
 int ozfft_get_stats(ozfft_plan_t plan, void* stream, ozfft_stats* out);
 
@@ -179,6 +181,17 @@ typedef struct {
 } ozfft_profile;
 int ozfft_set_profiling(ozfft_plan_t plan, int enable);
 int ozfft_get_profile(ozfft_plan_t plan, void* stream, ozfft_profile* out);
+
+/* The denominator of the integer roofline of the NTT kernels (the paper has no
+   counterpart: it measures on CPUs): radix-2 butterflies per second on the
+   current device with every operand in registers and no memory traffic, for
+   the forward (inverse = 0: Cooley-Tukey, (a, b) -> (a + bW, a - bW)) or the
+   inverse (inverse = 1: Gentleman-Sande, (a, b) -> (a + b, (a - b)W)) form the
+   NTT kernels use, canonical residues and Shoup products, i.e. the rate of
+   modular multiplications inside that instruction mix.  Runs a few milliseconds
+   of kernels on `stream` and synchronizes it; allocates and frees 1.2 MiB of
+   device memory.  *rate receives butterflies per second. */
+int ozfft_measure_butterfly_rate(int inverse, double* rate, void* stream);
 
 /* Transform without any allocation (the paper has no counterpart): for
    callers that cannot call cudaMalloc, such as code inside an application that

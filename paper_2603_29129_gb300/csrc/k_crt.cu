@@ -11,14 +11,22 @@
 // forward transform (+2) only conjugates, that of the inverse (-2) only divides.
 //
 // The exact sums use integer arithmetic only (binary64 throughput is low on
-// this part).  A thread keeps its element's sum as int64 limbs, each holding a
-// sum of 32-bit digits, in units of 2^-max(S).  A term z * 2^(max S - S_g) is
-// split into 32-bit digits and added to consecutive limbs without carries; one
-// carry pass and an integer round-to-nearest-even at the end produce the
-// binary64 bit pattern.  Two-prime signals whose scales span at most
-// REG_LIMBS - 5 limbs keep the limbs in registers (crt_reg_kernel, the common
-// case); the others go to crt_wide_kernel, which keeps a wider limb column per
-// thread in shared memory.
+// this part), in three kernels by signal:
+//   crt_fast_kernel  two primes, every convolution's group scales non-increasing
+//                    in schedule order (always, unless split levels have gaps)
+//                    and spanning <= FAST_SPAN bits: Horner's rule on a 192-bit
+//                    integer, groups taken from the smallest scale up, so a
+//                    change of scale is one left shift and every term a plain
+//                    add-with-carry;
+//   crt_reg_kernel   the other two-prime signals whose scales span at most
+//                    REG_LIMBS - 5 limbs: int64 limbs in registers, each holding
+//                    a sum of 32-bit digits in units of 2^-max(S); a term
+//                    z * 2^(max S - S_g) is split into digits and added to
+//                    consecutive limbs without carries;
+//   crt_wide_kernel  the rest (three primes, wide spans): the same limbs as a
+//                    column per thread in shared memory.
+// One carry pass and an integer round-to-nearest-even at the end produce the
+// binary64 bit pattern.
 #include "oz_common.cuh"
 #include "oz_kernels.h"
 #include "ts_arith.cuh"
@@ -285,6 +293,15 @@ __device__ __forceinline__ bool reg_path(const CrtArgs& a, int64_t b)
     return a.P == 2 && limbs_for(a.span[b * 3], a.span[b * 3 + 1]) <= REG_LIMBS;
 }
 
+// signals for crt_fast_kernel: two primes, scales non-increasing in group order
+// and spanning at most FAST_SPAN bits (every signal whose split levels have no
+// gaps); crt_reg_kernel takes the other register-path signals
+constexpr int FAST_SPAN = 120;
+__device__ __forceinline__ bool fast_path(const CrtArgs& a, int64_t b)
+{
+    return a.P == 2 && (a.span[b * 3 + 2] & 2) && a.span[b * 3 + 1] - a.span[b * 3] <= FAST_SPAN;
+}
+
 // a signal's length, chirp table and output row: the plan's (plain plans, the
 // kernel parameters themselves) or the signal's descriptor (uneven lengths)
 struct SigOut {
@@ -323,12 +340,12 @@ __global__ void __launch_bounds__(FAST_THREADS) crt_reg_kernel(CrtArgs a)
 {
     const int64_t chunks = (a.n + CRT_CHUNK - 1) / CRT_CHUNK;
     const int64_t b = blockIdx.x / chunks;
-    if (!reg_path(a, b)) return;
+    if (!reg_path(a, b) || fast_path(a, b)) return;
     const SigOut so = sig_out<SD>(a, b);
     const int64_t j0 = (blockIdx.x % chunks) * (int64_t)CRT_CHUNK;
     const int64_t j1 = min(so.n, j0 + CRT_CHUNK);
     const Sched* sc = a.sched + b * 4;
-    const int smax = a.span[b * 3 + 1], any = a.span[b * 3 + 2];
+    const int smax = a.span[b * 3 + 1], any = a.span[b * 3 + 2] & 1;
     for (int64_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
         double yp[2] = {0.0, 0.0};
         if (any) {
@@ -363,6 +380,114 @@ __global__ void __launch_bounds__(FAST_THREADS) crt_reg_kernel(CrtArgs a)
     }
 }
 
+// ------------------------------------------------------------ Horner path
+// A 192-bit two's complement integer in six 32-bit words (w[0] least
+// significant), with carry-chain arithmetic in inline PTX.
+struct Acc192 {
+    uint32_t w[6];
+};
+
+__device__ __forceinline__ void acc192_add64(Acc192& A, long long z)   // A += z, z sign-extended
+{
+    const uint32_t lo = (uint32_t)z, hi = (uint32_t)((unsigned long long)z >> 32), ext = (uint32_t)(z >> 63);
+    asm("add.cc.u32 %0, %0, %6;\n\t"
+        "addc.cc.u32 %1, %1, %7;\n\t"
+        "addc.cc.u32 %2, %2, %8;\n\t"
+        "addc.cc.u32 %3, %3, %8;\n\t"
+        "addc.cc.u32 %4, %4, %8;\n\t"
+        "addc.u32 %5, %5, %8;"
+        : "+r"(A.w[0]), "+r"(A.w[1]), "+r"(A.w[2]), "+r"(A.w[3]), "+r"(A.w[4]), "+r"(A.w[5])
+        : "r"(lo), "r"(hi), "r"(ext));
+}
+
+__device__ __forceinline__ void acc192_add(Acc192& A, const Acc192& B)   // A += B
+{
+    asm("add.cc.u32 %0, %0, %6;\n\t"
+        "addc.cc.u32 %1, %1, %7;\n\t"
+        "addc.cc.u32 %2, %2, %8;\n\t"
+        "addc.cc.u32 %3, %3, %9;\n\t"
+        "addc.cc.u32 %4, %4, %10;\n\t"
+        "addc.u32 %5, %5, %11;"
+        : "+r"(A.w[0]), "+r"(A.w[1]), "+r"(A.w[2]), "+r"(A.w[3]), "+r"(A.w[4]), "+r"(A.w[5])
+        : "r"(B.w[0]), "r"(B.w[1]), "r"(B.w[2]), "r"(B.w[3]), "r"(B.w[4]), "r"(B.w[5]));
+}
+
+// A <<= d for a shift d that is the same in every thread (0 <= d < 192)
+__device__ __forceinline__ void acc192_shl(Acc192& A, int d)
+{
+    for (; d >= 32; d -= 32) {   // whole words
+        A.w[5] = A.w[4]; A.w[4] = A.w[3]; A.w[3] = A.w[2]; A.w[2] = A.w[1]; A.w[1] = A.w[0]; A.w[0] = 0u;
+    }
+    if (d) {
+#pragma unroll
+        for (int i = 5; i >= 1; --i) A.w[i] = __funnelshift_l(A.w[i - 1], A.w[i], d);
+        A.w[0] <<= d;
+    }
+}
+
+// Exact accumulation by Horner's rule: a convolution's groups run from the
+// last (smallest scale S, largest terms) to the first, so every change of
+// scale multiplies the running sum by 2^(S_new - S_old) >= 1, a left shift;
+// terms are then added as plain integers.  The running sum of a convolution
+// ends in units of 2^-S of its first group and is shifted to the signal's
+// 2^-max S; at most 2^62 * 64 * 2^FAST_SPAN in magnitude, inside 192 bits.
+template <bool SD>
+__global__ void __launch_bounds__(FAST_THREADS) crt_fast_kernel(CrtArgs a)
+{
+    const int64_t chunks = (a.n + CRT_CHUNK - 1) / CRT_CHUNK;
+    const int64_t b = blockIdx.x / chunks;
+    if (!fast_path(a, b)) return;
+    const SigOut so = sig_out<SD>(a, b);
+    const int64_t j0 = (blockIdx.x % chunks) * (int64_t)CRT_CHUNK;
+    const int64_t j1 = min(so.n, j0 + CRT_CHUNK);
+    const Sched* sc = a.sched + b * 4;
+    const int smax = a.span[b * 3 + 1], any = a.span[b * 3 + 2] & 1;
+    for (int64_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
+        double yp[2] = {0.0, 0.0};
+        if (any) {
+#pragma unroll
+            for (int part = 0; part < 2; ++part) {
+                Acc192 A = {{0u, 0u, 0u, 0u, 0u, 0u}};
+#pragma unroll
+                for (int cc = 0; cc < 2; ++cc) {
+                    const int c = 2 * part + cc;
+                    const Sched& S = sc[c];
+                    const int ng = S.ngroups;
+                    if (ng == 0) continue;
+                    const uint32_t* zp = a.Z + ((b * 4 + c) * a.G) * 2 * a.N + j;
+                    Acc192 T = {{0u, 0u, 0u, 0u, 0u, 0u}};
+                    int scur = S.S[ng - 1];
+                    uint32_t z0 = __ldg(zp + (int64_t)(ng - 1) * 2 * a.N);
+                    uint32_t z1 = __ldg(zp + (int64_t)(ng - 1) * 2 * a.N + a.N);
+                    for (int g = ng - 1; g >= 0; --g) {
+                        const uint32_t c0 = z0, c1 = z1;
+                        if (g > 0) {   // prefetch the previous group
+                            z0 = __ldg(zp + (int64_t)(g - 1) * 2 * a.N);
+                            z1 = __ldg(zp + (int64_t)(g - 1) * 2 * a.N + a.N);
+                        }
+                        const int sg = S.S[g];
+                        if (sg != scur) {
+                            acc192_shl(T, sg - scur);
+                            scur = sg;
+                        }
+                        long long z = garner2(c0, c1);
+                        if (c == 1 && !a.merged) z = -z;   // II enters the real part with a minus sign
+                        acc192_add64(T, z);
+                    }
+                    acc192_shl(T, smax - scur);
+                    acc192_add(A, T);
+                }
+                long long limbs[6];
+#pragma unroll
+                for (int l = 0; l < 5; ++l) limbs[l] = (long long)A.w[l];
+                limbs[5] = (long long)(int32_t)A.w[5];
+                yp[part] = acc_to_double<6>(limbs, -smax);
+            }
+        }
+        post_store(a, so, j, yp[0], yp[1]);
+    }
+}
+
 // shared-memory path: any prime count and scale span, one limb column per thread
 template <bool SD>
 __global__ void __launch_bounds__(WIDE_THREADS) crt_wide_kernel(CrtArgs a)
@@ -380,7 +505,7 @@ __global__ void __launch_bounds__(WIDE_THREADS) crt_wide_kernel(CrtArgs a)
         const int64_t j0 = (item % chunks) * (int64_t)CRT_CHUNK;
         const int64_t j1 = min(so.n, j0 + CRT_CHUNK);
         const Sched* sc = a.sched + b * 4;
-        const int smin = a.span[b * 3 + 0], smax = a.span[b * 3 + 1], any = a.span[b * 3 + 2];
+        const int smin = a.span[b * 3 + 0], smax = a.span[b * 3 + 1], any = a.span[b * 3 + 2] & 1;
         const int nl = limbs_for(smin, smax);
         if (nl > WIDE_LIMBS) {   // cannot happen for finite inputs that passed the split's range check
             if (threadIdx.x == 0) atomicOr(a.status, ST_RANGE);
@@ -430,7 +555,7 @@ static uint64_t host_powmod(uint64_t b, uint64_t e, uint64_t m)
     return (uint64_t)r;
 }
 
-int crt_launches() { return 2; }
+int crt_launches() { return 3; }
 
 cudaError_t crt_init()
 {
@@ -455,6 +580,10 @@ cudaError_t launch_crt_post(const CrtArgs& a, cudaStream_t s)
     if (e != cudaSuccess) return e;
     const int64_t chunks = (a.n + CRT_CHUNK - 1) / CRT_CHUNK;
     const bool sd = a.sd != nullptr;
+    if (sd) crt_fast_kernel<true><<<(unsigned)(a.B * chunks), FAST_THREADS, 0, s>>>(a);
+    else crt_fast_kernel<false><<<(unsigned)(a.B * chunks), FAST_THREADS, 0, s>>>(a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
     if (sd) crt_reg_kernel<true><<<(unsigned)(a.B * chunks), FAST_THREADS, 0, s>>>(a);
     else crt_reg_kernel<false><<<(unsigned)(a.B * chunks), FAST_THREADS, 0, s>>>(a);
     e = cudaGetLastError();

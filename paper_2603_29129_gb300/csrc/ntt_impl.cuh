@@ -39,7 +39,7 @@
 
 namespace oz {
 
-constexpr int NTT_THREADS = 128;   // eight CTAs per SM overlap their load, compute and store phases
+constexpr int NTT_THREADS = 128;   // 8 (column pass) or 10 (row pass) CTAs per SM overlap load, compute, store
 constexpr int TILE_LOG = 12;   // CTA tile of 4096 residues: ~13 CTAs fit an SM by shared memory
 
 __device__ __forceinline__ int pad_idx(int i) { return i + (i >> 5); }
@@ -290,7 +290,15 @@ template <bool MERGED>
 __device__ __forceinline__ uint4 mac_sum4(const MacVec& m, const MacSrc& mac, int64_t j)
 {
     uint32_t a0 = 0u, a1 = 0u, a2 = 0u, a3 = 0u;
-    for (int k = 0; k < m.n; ++k) {
+    if (!MERGED && m.n > 0) {   // the first product sets the sums (no add of zero)
+        int64_t xo, yo;
+        mac_offsets<false>(m, 0, xo, yo);
+        const uint4 x = __ldg(reinterpret_cast<const uint4*>(mac.X + xo + j));
+        const uint4 y = __ldg(reinterpret_cast<const uint4*>(mac.Ym + yo + j));
+        a0 = mont_mul(x.x, y.x, m.p, m.pn); a1 = mont_mul(x.y, y.y, m.p, m.pn);
+        a2 = mont_mul(x.z, y.z, m.p, m.pn); a3 = mont_mul(x.w, y.w, m.p, m.pn);
+    }
+    for (int k = (!MERGED && m.n > 0) ? 1 : 0; k < m.n; ++k) {
         int64_t xo, yo;
         const bool neg = mac_offsets<MERGED>(m, k, xo, yo);
         const uint4 x = __ldg(reinterpret_cast<const uint4*>(mac.X + xo + j));
@@ -332,7 +340,7 @@ __device__ __forceinline__ uint32_t mac_load1(const MacVec& m, const MacSrc& mac
 }
 
 template <bool INV, bool MAC, int M2>
-__global__ void __launch_bounds__(NTT_THREADS, 8) ntt_row_kernel(NttGeom g, uint32_t* __restrict__ data,
+__global__ void __launch_bounds__(NTT_THREADS, 10) ntt_row_kernel(NttGeom g, uint32_t* __restrict__ data,
                                                                  const uint2* __restrict__ tw_all, MacSrc mac)
 {
     extern __shared__ uint32_t sm[];

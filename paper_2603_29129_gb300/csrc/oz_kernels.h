@@ -95,6 +95,10 @@ cudaError_t crt_init();    // uploads the Garner constants (once; call before an
 cudaError_t launch_crt_post(const CrtArgs& a, cudaStream_t s);
 cudaError_t launch_crt_ts(const CrtArgs& a, cudaStream_t s);   // TS variant (two primes)
 
+// k_peak.cu: butterflies per second with every operand in registers
+cudaError_t measure_butterfly_rate(int inverse, int blocks, int iters, uint32_t* scratch, double* rate,
+                                   cudaStream_t s);
+
 // k_ts.cu: the TS variant's pre-multiply, w~* and split (TS vectors are three
 // binary32 word planes r[v][0..2][N])
 cudaError_t launch_ts_premul(const double2* x, const double2* w, int64_t n, int64_t N, int64_t B, int conj_in,

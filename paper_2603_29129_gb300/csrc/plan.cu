@@ -181,8 +181,9 @@ static int ceil_log2_h(double mu)
 // split levels and scales come from mu, those of w~* from the plan (per
 // signal in a length class of a plan over uneven lengths, where sd gives each
 // signal's alpha).  One thread per signal; it also records the signal's scale
-// span over all groups (span[b] = {min S, max S, any group}) for the exact
-// accumulation.
+// span over all groups for the exact accumulation: span[b] = {min S, max S,
+// flags}, flags bit 0 = any group, bit 1 = the scales of every convolution are
+// non-increasing in group order (always, unless split levels have gaps).
 //
 // Merged schedules (merge != 0) extend Alg. 8's accumulation across the two
 // convolutions that feed one output part (RR and II into the real part, IR and
@@ -216,7 +217,7 @@ __global__ void schedule_kernel(const uint64_t* __restrict__ mu, int64_t B, int 
         kxv[v] = kx;
         kcnt[b * 2 + v] = kx;
     }
-    int smin = 0, smax = 0, any = 0;
+    int smin = 0, smax = 0, any = 0, mono = 1;   // mono: every convolution's scales non-increasing
     if (merge) {
         const int G = K * K;
         for (int part = 0; part < 2; ++part) {
@@ -262,7 +263,7 @@ __global__ void schedule_kernel(const uint64_t* __restrict__ mu, int64_t B, int 
         }
         span[b * 3 + 0] = smin;
         span[b * 3 + 1] = smax;
-        span[b * 3 + 2] = any;
+        span[b * 3 + 2] = any | 2;   // sorted by scale: non-increasing in group order
         return;
     }
     for (int c = 0; c < 4; ++c) {
@@ -279,6 +280,7 @@ __global__ void schedule_kernel(const uint64_t* __restrict__ mu, int64_t B, int 
                     const int t = k - s;
                     const int sc = sx[vx][s] + wsexp[vw * K + t];
                     if (l >= L || sc != cur) {   // flush: start a new group
+                        if (sc > cur) mono = 0;
                         ++g;
                         cur = sc;
                         l = 0;
@@ -298,7 +300,7 @@ __global__ void schedule_kernel(const uint64_t* __restrict__ mu, int64_t B, int 
     }
     span[b * 3 + 0] = smin;
     span[b * 3 + 1] = smax;
-    span[b * 3 + 2] = any;
+    span[b * 3 + 2] = any | (mono << 1);
 }
 
 // Y -> Y * N^-1 * 2^32 mod p, via Montgomery with the constant N^-1 2^64 mod p
@@ -945,6 +947,21 @@ int ozfft_get_profile(ozfft_plan_t p, void* stream, ozfft_profile* out)
     return OZFFT_OK;
 }
 
+int ozfft_measure_butterfly_rate(int inverse, double* rate, void* stream)
+{
+    if (!rate) return fail(OZFFT_ERR_ARG, "ozfft_measure_butterfly_rate: null argument");
+    int dev = 0, sms = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int blocks = sms * 8;                    // eight 256-thread CTAs per SM
+    uint32_t* scratch = nullptr;
+    CUDA_TRY(cudaMalloc((void**)&scratch, sizeof(uint32_t) * 256 * (size_t)blocks));
+    const cudaError_t e = measure_butterfly_rate(inverse, blocks, 4096, scratch, rate, (cudaStream_t)stream);
+    cudaFree(scratch);
+    if (e != cudaSuccess) return fail(OZFFT_ERR_CUDA, std::string("butterfly rate: ") + cudaGetErrorString(e));
+    return OZFFT_OK;
+}
+
 int ozfft_execute_host(ozfft_plan_t p, const void* in, void* out, void* stream)
 {
     if (!p || !in || !out) return fail(OZFFT_ERR_ARG, "ozfft_execute_host: null argument");
@@ -999,6 +1016,9 @@ int ozfft_get_stats(ozfft_plan_t p, void* stream, ozfft_stats* out)
     out->ntt_forward_plan = p->fwd_plan;
     out->kernel_launches = p->launches;
     out->workspace_bytes = p->bytes;
+    const ozfft_plan_s* g0 = p->classes.empty() ? p : p->classes.front();
+    out->row_log_fwd = g0->geom_fwd.m2;
+    out->row_log_inv = g0->geom_inv.m2;
     std::vector<ozfft_plan_s*> parts = p->classes;
     if (parts.empty()) parts.push_back(p);
     if (p->executed) CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));

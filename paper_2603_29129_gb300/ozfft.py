@@ -24,7 +24,8 @@ MAX_GROUPS, MAX_L = 64, 8
 # every symbol include/ozfft.h declares
 EXPORTS = ("ozfft_plan", "ozfft_plan_ex", "ozfft_execute", "ozfft_execute_host", "ozfft_get_status",
            "ozfft_get_stats", "ozfft_set_profiling", "ozfft_get_profile", "ozfft_destroy", "ozfft_error_string",
-           "ozfft_last_error", "ozfft_debug_dump", "ozfft_execute_noalloc", "ozfft_plan_many")
+           "ozfft_last_error", "ozfft_debug_dump", "ozfft_execute_noalloc", "ozfft_plan_many",
+           "ozfft_measure_butterfly_rate")
 PROF_SLOTS = ("premul", "split", "schedule", "ntt_fwd_col", "ntt_fwd_row", "ntt_inv_row", "ntt_inv_col", "crt")
 
 
@@ -39,7 +40,8 @@ class Stats(C.Structure):
                 ("K", C.c_int32), ("L", C.c_int32), ("nprimes", C.c_int32), ("alpha", C.c_int32),
                 ("direction", C.c_int32), ("wstar_levels", C.c_int32 * 2),
                 ("ntt_forward_runtime", C.c_int64), ("ntt_forward_plan", C.c_int64), ("ntt_inverse", C.c_int64),
-                ("kernel_launches", C.c_int64), ("workspace_bytes", C.c_int64)]
+                ("kernel_launches", C.c_int64), ("workspace_bytes", C.c_int64),
+                ("row_log_fwd", C.c_int32), ("row_log_inv", C.c_int32)]
 
 
 class Profile(C.Structure):
@@ -79,6 +81,8 @@ def load(path: str = LIB_PATH):
             L.ozfft_debug_dump.restype = i64; L.ozfft_debug_dump.argtypes = [P, C.c_int, i64, P, P]
             L.ozfft_execute_noalloc.restype = C.c_int
             L.ozfft_execute_noalloc.argtypes = [i64, C.c_int, P, P, P]
+            L.ozfft_measure_butterfly_rate.restype = C.c_int
+            L.ozfft_measure_butterfly_rate.argtypes = [C.c_int, C.POINTER(C.c_double), P]
             L.ozfft_plan_many.restype = P
             L.ozfft_plan_many.argtypes = [C.POINTER(i64), i64, C.c_int, C.POINTER(Options)]
             _lib = L
@@ -231,6 +235,14 @@ class PlanMany(Plan):
     def split(self, y):
         """The packed output as a list of per-signal views."""
         return [y[self.offsets[i]:self.offsets[i + 1]] for i in range(self.batch)]
+
+
+def butterfly_rate(inverse=False, stream=None):
+    """Radix-2 NTT butterflies per second with operands in registers (the
+    integer roofline's denominator, ozfft_measure_butterfly_rate)."""
+    r = C.c_double(0.0)
+    _check(load().ozfft_measure_butterfly_rate(int(bool(inverse)), C.byref(r), _stream_ptr(stream)))
+    return r.value
 
 
 def execute_noalloc(x, out, direction=FORWARD, stream=None):

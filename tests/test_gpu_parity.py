@@ -131,6 +131,22 @@ def test_wide_scale_spans(oz):
             assert np.array_equal(y[b].view(np.uint64), yo.view(np.uint64)), (P, b)
 
 
+@pytest.mark.parametrize("tiny", [1e-9, 1e-12, 1e-20, 1e-30])
+def test_split_gaps_moderate_spans(oz, tiny):
+    """A dominant sample over samples 1e-9 .. 1e-30 smaller: the split levels
+    have gaps, so flush-group scales are not monotone in schedule order, with
+    scale spans that still fit the register accumulator."""
+    n = 2048
+    xs = synth.complex_signal("uniform", n, 15, batch=2)
+    xs[:, 1:] *= tiny
+    xs[:, 0] = 1.0 - 0.5j
+    for L in (1, 3):
+        y, plan = run_gpu(oz, xs, L=L)
+        for b in range(2):
+            yo, _ = oracle_vs(xs[b], plan)
+            assert np.array_equal(y[b].view(np.uint64), yo.view(np.uint64)), (tiny, L, b)
+
+
 def test_batch_mixed_distributions(oz):
     n = 2048
     xs = np.concatenate([synth.complex_signal(k, n, 7, phi=4.0) for k in
