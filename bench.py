@@ -32,6 +32,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "FP64-accurate Ozaki-NTT FFTs/s at n=2^18 (batched); NTT GB/s; rel err"
+BUTTERFLY_INSTR = 7.17   # lane instructions per radix-2 butterfly of the NTT kernels (profiles/)
 UNIT = "FFT/s"
 
 
@@ -649,15 +650,17 @@ def main():
     if mm.get(dom):
         # integer roofline: the NTT kernels are bound by integer issue (ncu: DRAM well below
         # peak, issue slots busy); peak = 152 SMs x 4 schedulers x 32 lanes x 2.07 GHz lane
-        # instructions / 11 instructions per canonical Shoup butterfly
+        # instructions / the lane instructions of one butterfly as compiled (ncu
+        # smsp__inst_executed over the register-only kernel of the inverse butterfly: 7.17)
         mm_launch = mm[dom] / launches_per_exec
-        peak_derived = 152 * 4 * 32 * 2.07e9 / 11 / 1e12
+        peak_derived = 152 * 4 * 32 * 2.07e9 / BUTTERFLY_INSTR / 1e12
         inv = dom.startswith("ntt_inv")
         measured = ozfft.butterfly_rate(inverse=inv) / 1e12
         achieved = mm_launch / (dom_ms / 1e3) / 1e12
         roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak_derived, "unit": "Tmodmul/s",
                 "frac": achieved / peak_derived, "traffic": traffic,
-                "peak_source": "derived: 152 SMs x 4 x 32 lanes x 2.07 GHz / 11 integer instructions per butterfly",
+                "peak_source": f"derived: 152 SMs x 4 x 32 lanes x 2.07 GHz / {BUTTERFLY_INSTR} lane instructions "
+                               "per butterfly (ncu count of the register-only butterfly kernel)",
                 "peak_measured_registers": measured, "frac_of_measured": achieved / measured,
                 "modmuls_per_launch": mm_launch, "launch_ms": dom_ms, "hbm_view": hbm_view}
     elif hbm_view:
