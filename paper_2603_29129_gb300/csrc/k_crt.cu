@@ -457,6 +457,31 @@ __global__ void __launch_bounds__(FAST_THREADS) crt_fast_kernel(CrtArgs a)
                     const uint32_t* zp = a.Z + ((b * 4 + c) * a.G) * 2 * a.N + j;
                     Acc192 T = {{0u, 0u, 0u, 0u, 0u, 0u}};
                     int scur = S.S[ng - 1];
+                    constexpr int PF = 9;
+                    if (ng <= PF) {   // every group's residues in flight at once
+                        uint32_t r0[PF], r1[PF];
+#pragma unroll
+                        for (int q = 0; q < PF; ++q)
+                            if (q < ng) {
+                                r0[q] = __ldg(zp + (int64_t)q * 2 * a.N);
+                                r1[q] = __ldg(zp + (int64_t)q * 2 * a.N + a.N);
+                            }
+#pragma unroll
+                        for (int q = PF - 1; q >= 0; --q)
+                            if (q < ng) {
+                                const int sg = S.S[q];
+                                if (sg != scur) {
+                                    acc192_shl(T, sg - scur);
+                                    scur = sg;
+                                }
+                                long long z = garner2(r0[q], r1[q]);
+                                if (c == 1 && !a.merged) z = -z;
+                                acc192_add64(T, z);
+                            }
+                        acc192_shl(T, smax - scur);
+                        acc192_add(A, T);
+                        continue;
+                    }
                     uint32_t z0 = __ldg(zp + (int64_t)(ng - 1) * 2 * a.N);
                     uint32_t z1 = __ldg(zp + (int64_t)(ng - 1) * 2 * a.N + a.N);
                     for (int g = ng - 1; g >= 0; --g) {

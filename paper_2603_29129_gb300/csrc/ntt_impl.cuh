@@ -207,11 +207,23 @@ __global__ void __launch_bounds__(NTT_THREADS, 8) ntt_col_kernel(NttGeom g, uint
     const int pi = (int)(vec % (unsigned)g.P);
     uint32_t* v = data + (int64_t)vec * g.N + col0;
     constexpr int TILE4 = (T << M1) >> 2;
-    for (int q = threadIdx.x; q < TILE4; q += blockDim.x) {
-        const int row = q >> (LOG_T - 2), c = (q & ((T >> 2) - 1)) << 2;
-        const uint4 t = *reinterpret_cast<const uint4*>(v + ((int64_t)row << g.m2) + c);
-        uint32_t* s = sm + pad_idx((row << LOG_T) + c);
-        s[0] = t.x; s[1] = t.y; s[2] = t.z; s[3] = t.w;
+    static_assert(TILE4 % (8 * NTT_THREADS) == 0, "column tile");
+    // eight 16-byte loads in flight per thread before the shared-memory stores
+    for (int q0 = 0; q0 < TILE4; q0 += 8 * NTT_THREADS) {
+        uint4 t[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int q = q0 + k * NTT_THREADS + threadIdx.x;
+            const int row = q >> (LOG_T - 2), c = (q & ((T >> 2) - 1)) << 2;
+            t[k] = *reinterpret_cast<const uint4*>(v + ((int64_t)row << g.m2) + c);
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int q = q0 + k * NTT_THREADS + threadIdx.x;
+            const int row = q >> (LOG_T - 2), c = (q & ((T >> 2) - 1)) << 2;
+            uint32_t* s = sm + pad_idx((row << LOG_T) + c);
+            s[0] = t[k].x; s[1] = t[k].y; s[2] = t[k].z; s[3] = t[k].w;
+        }
     }
     __syncthreads();
     const PassArgs a{T, 1, 0, tw_all, g.N, pi, g.P, false};
@@ -361,10 +373,40 @@ __global__ void __launch_bounds__(NTT_THREADS, 10) ntt_row_kernel(NttGeom g, uin
         if (nel >= 4) {
             if (MAC) {
                 const MacVec mv = mac_decode(g, vec, mac.ym_stride);
+                if (!mv.merged && mv.n == 1 && (nel >> 2) % (2 * NTT_THREADS) == 0) {
+                    // one product (L = 1): two iterations' loads in flight per thread
+                    int64_t xo, yo;
+                    mac_offsets<false>(mv, 0, xo, yo);
+                    const uint4* xp = reinterpret_cast<const uint4*>(mac.X + xo + j0);
+                    const uint4* yp = reinterpret_cast<const uint4*>(mac.Ym + yo + j0);
+                    for (int q0 = threadIdx.x; q0 < (nel >> 2); q0 += 2 * NTT_THREADS) {
+                        const uint4 x0 = __ldg(xp + q0), y0 = __ldg(yp + q0);
+                        const uint4 x1 = __ldg(xp + q0 + NTT_THREADS), y1 = __ldg(yp + q0 + NTT_THREADS);
+                        uint32_t* s = sm + pad_idx(4 * q0);
+                        s[0] = mont_mul(x0.x, y0.x, mv.p, mv.pn); s[1] = mont_mul(x0.y, y0.y, mv.p, mv.pn);
+                        s[2] = mont_mul(x0.z, y0.z, mv.p, mv.pn); s[3] = mont_mul(x0.w, y0.w, mv.p, mv.pn);
+                        s = sm + pad_idx(4 * (q0 + NTT_THREADS));
+                        s[0] = mont_mul(x1.x, y1.x, mv.p, mv.pn); s[1] = mont_mul(x1.y, y1.y, mv.p, mv.pn);
+                        s[2] = mont_mul(x1.z, y1.z, mv.p, mv.pn); s[3] = mont_mul(x1.w, y1.w, mv.p, mv.pn);
+                    }
+                } else
                 for (int q = threadIdx.x; q < (nel >> 2); q += blockDim.x) {
                     const uint4 t = mac_load4(mv, mac, j0 + 4 * q);
                     uint32_t* s = sm + pad_idx(4 * q);
                     s[0] = t.x; s[1] = t.y; s[2] = t.z; s[3] = t.w;
+                }
+            } else if ((nel >> 2) % (8 * NTT_THREADS) == 0) {
+                // eight 16-byte loads in flight per thread before the shared-memory stores
+                for (int q0 = 0; q0 < (nel >> 2); q0 += 8 * NTT_THREADS) {
+                    uint4 t[8];
+#pragma unroll
+                    for (int k = 0; k < 8; ++k)
+                        t[k] = *reinterpret_cast<const uint4*>(data + gbase + 4 * (q0 + k * NTT_THREADS + threadIdx.x));
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        uint32_t* s = sm + pad_idx(4 * (q0 + k * NTT_THREADS + threadIdx.x));
+                        s[0] = t[k].x; s[1] = t[k].y; s[2] = t[k].z; s[3] = t[k].w;
+                    }
                 }
             } else {
                 for (int q = threadIdx.x; q < (nel >> 2); q += blockDim.x) {
