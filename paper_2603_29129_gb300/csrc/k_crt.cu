@@ -18,7 +18,8 @@
 //                    integer, groups taken from the smallest scale up, so a
 //                    change of scale is one left shift and every term a plain
 //                    add-with-carry;
-//   crt_reg_kernel   the other two-prime signals whose scales span at most
+//   crt_reg_body     (inside crt_fast_kernel's launch) the other two-prime
+//                    signals whose scales span at most
 //                    REG_LIMBS - 5 limbs: int64 limbs in registers, each holding
 //                    a sum of 32-bit digits in units of 2^-max(S); a term
 //                    z * 2^(max S - S_g) is split into digits and added to
@@ -295,7 +296,7 @@ __device__ __forceinline__ bool reg_path(const CrtArgs& a, int64_t b)
 
 // signals for crt_fast_kernel: two primes, scales non-increasing in group order
 // and spanning at most FAST_SPAN bits (every signal whose split levels have no
-// gaps); crt_reg_kernel takes the other register-path signals
+// gaps); crt_reg_body takes the other register-path signals
 constexpr int FAST_SPAN = 120;
 __device__ __forceinline__ bool fast_path(const CrtArgs& a, int64_t b)
 {
@@ -336,7 +337,7 @@ __device__ __forceinline__ void post_store(const CrtArgs& a, const SigOut& so, i
 
 // register path: one output element per thread, integer-only accumulation
 template <bool SD>
-__global__ void __launch_bounds__(FAST_THREADS) crt_reg_kernel(CrtArgs a)
+__device__ __forceinline__ void crt_reg_body(const CrtArgs& a)
 {
     const int64_t chunks = (a.n + CRT_CHUNK - 1) / CRT_CHUNK;
     const int64_t b = blockIdx.x / chunks;
@@ -436,7 +437,10 @@ __global__ void __launch_bounds__(FAST_THREADS) crt_fast_kernel(CrtArgs a)
 {
     const int64_t chunks = (a.n + CRT_CHUNK - 1) / CRT_CHUNK;
     const int64_t b = blockIdx.x / chunks;
-    if (!fast_path(a, b)) return;
+    if (!fast_path(a, b)) {   // the signal's CTAs take the limb path instead (one launch for both)
+        crt_reg_body<SD>(a);
+        return;
+    }
     const SigOut so = sig_out<SD>(a, b);
     const int64_t j0 = (blockIdx.x % chunks) * (int64_t)CRT_CHUNK;
     const int64_t j1 = min(so.n, j0 + CRT_CHUNK);
@@ -580,7 +584,7 @@ static uint64_t host_powmod(uint64_t b, uint64_t e, uint64_t m)
     return (uint64_t)r;
 }
 
-int crt_launches() { return 3; }
+int crt_launches() { return 2; }
 
 cudaError_t crt_init()
 {
@@ -609,10 +613,6 @@ cudaError_t launch_crt_post(const CrtArgs& a, cudaStream_t s)
     else crt_fast_kernel<false><<<(unsigned)(a.B * chunks), FAST_THREADS, 0, s>>>(a);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    if (sd) crt_reg_kernel<true><<<(unsigned)(a.B * chunks), FAST_THREADS, 0, s>>>(a);
-    else crt_reg_kernel<false><<<(unsigned)(a.B * chunks), FAST_THREADS, 0, s>>>(a);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
     // signals with three primes or a wide scale span: small blocks, limb columns in shared memory
     const size_t smem = sizeof(long long) * WIDE_LIMBS * WIDE_THREADS;
     static bool attr = false;
@@ -623,7 +623,7 @@ cudaError_t launch_crt_post(const CrtArgs& a, cudaStream_t s)
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    const int64_t grid = a.B * chunks < 1024 ? a.B * chunks : 1024;
+    const int64_t grid = a.B * chunks < 304 ? a.B * chunks : 304;
     if (sd) crt_wide_kernel<true><<<(unsigned)grid, WIDE_THREADS, smem, s>>>(a);
     else crt_wide_kernel<false><<<(unsigned)grid, WIDE_THREADS, smem, s>>>(a);
     return cudaGetLastError();
