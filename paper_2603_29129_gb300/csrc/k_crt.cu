@@ -24,8 +24,11 @@
 //                    a sum of 32-bit digits in units of 2^-max(S); a term
 //                    z * 2^(max S - S_g) is split into digits and added to
 //                    consecutive limbs without carries;
-//   crt_wide_kernel  the rest (three primes, wide spans): the same limbs as a
-//                    column per thread in shared memory.
+//   crt_fast3_kernel three primes, the same conditions (span <= FAST3_SPAN):
+//                    Horner's rule with 128-bit CRT integers;
+//   crt_wide_kernel  the rest (wide spans, scales out of order with three
+//                    primes): the same limbs as a column per thread in shared
+//                    memory.
 // One carry pass and an integer round-to-nearest-even at the end produce the
 // binary64 bit pattern.
 #include "oz_common.cuh"
@@ -302,6 +305,12 @@ __device__ __forceinline__ bool fast_path(const CrtArgs& a, int64_t b)
 {
     return a.P == 2 && (a.span[b * 3 + 2] & 2) && a.span[b * 3 + 1] - a.span[b * 3] <= FAST_SPAN;
 }
+// the same for three primes (|z'| < 2^92): crt_fast3_kernel
+constexpr int FAST3_SPAN = 90;
+__device__ __forceinline__ bool fast3_path(const CrtArgs& a, int64_t b)
+{
+    return a.P == 3 && (a.span[b * 3 + 2] & 2) && a.span[b * 3 + 1] - a.span[b * 3] <= FAST3_SPAN;
+}
 
 // a signal's length, chirp table and output row: the plan's (plain plans, the
 // kernel parameters themselves) or the signal's descriptor (uneven lengths)
@@ -413,6 +422,20 @@ __device__ __forceinline__ void acc192_add(Acc192& A, const Acc192& B)   // A +=
         : "r"(B.w[0]), "r"(B.w[1]), "r"(B.w[2]), "r"(B.w[3]), "r"(B.w[4]), "r"(B.w[5]));
 }
 
+__device__ __forceinline__ void acc192_add128(Acc192& A, i128p z)   // A += z, z sign-extended
+{
+    const unsigned long long lo = z.lo, hi = (unsigned long long)z.hi;
+    const uint32_t ext = (uint32_t)(z.hi >> 63);
+    asm("add.cc.u32 %0, %0, %6;\n\t"
+        "addc.cc.u32 %1, %1, %7;\n\t"
+        "addc.cc.u32 %2, %2, %8;\n\t"
+        "addc.cc.u32 %3, %3, %9;\n\t"
+        "addc.cc.u32 %4, %4, %10;\n\t"
+        "addc.u32 %5, %5, %10;"
+        : "+r"(A.w[0]), "+r"(A.w[1]), "+r"(A.w[2]), "+r"(A.w[3]), "+r"(A.w[4]), "+r"(A.w[5])
+        : "r"((uint32_t)lo), "r"((uint32_t)(lo >> 32)), "r"((uint32_t)hi), "r"((uint32_t)(hi >> 32)), "r"(ext));
+}
+
 // A <<= d for a shift d that is the same in every thread (0 <= d < 192)
 __device__ __forceinline__ void acc192_shl(Acc192& A, int d)
 {
@@ -517,6 +540,71 @@ __global__ void __launch_bounds__(FAST_THREADS) crt_fast_kernel(CrtArgs a)
     }
 }
 
+// Horner's rule for three primes: the same scheme with the 128-bit CRT
+// integers of the three-digit Garner form (|z'| < 2^92, so spans of at most
+// FAST3_SPAN bits stay inside 192 bits).
+template <bool SD>
+__global__ void __launch_bounds__(FAST_THREADS) crt_fast3_kernel(CrtArgs a)
+{
+    const int64_t chunks = (a.n + CRT_CHUNK - 1) / CRT_CHUNK;
+    const int64_t b = blockIdx.x / chunks;
+    if (!fast3_path(a, b)) return;
+    const SigOut so = sig_out<SD>(a, b);
+    const int64_t j0 = (blockIdx.x % chunks) * (int64_t)CRT_CHUNK;
+    const int64_t j1 = min(so.n, j0 + CRT_CHUNK);
+    const Sched* sc = a.sched + b * 4;
+    const int smax = a.span[b * 3 + 1], any = a.span[b * 3 + 2] & 1;
+    for (int64_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
+        double yp[2] = {0.0, 0.0};
+        if (any) {
+#pragma unroll
+            for (int part = 0; part < 2; ++part) {
+                Acc192 A = {{0u, 0u, 0u, 0u, 0u, 0u}};
+#pragma unroll
+                for (int cc = 0; cc < 2; ++cc) {
+                    const int c = 2 * part + cc;
+                    const Sched& S = sc[c];
+                    const int ng = S.ngroups;
+                    if (ng == 0) continue;
+                    const uint32_t* zp = a.Z + ((b * 4 + c) * a.G) * 3 * a.N + j;
+                    Acc192 T = {{0u, 0u, 0u, 0u, 0u, 0u}};
+                    int scur = S.S[ng - 1];
+                    uint32_t z[3] = {__ldg(zp + (int64_t)(ng - 1) * 3 * a.N), __ldg(zp + (int64_t)(ng - 1) * 3 * a.N + a.N),
+                                     __ldg(zp + (int64_t)(ng - 1) * 3 * a.N + 2 * a.N)};
+                    for (int g = ng - 1; g >= 0; --g) {
+                        const uint32_t cz[3] = {z[0], z[1], z[2]};
+                        if (g > 0) {   // prefetch the previous group
+                            const uint32_t* q = zp + (int64_t)(g - 1) * 3 * a.N;
+                            z[0] = __ldg(q);
+                            z[1] = __ldg(q + a.N);
+                            z[2] = __ldg(q + 2 * a.N);
+                        }
+                        const int sg = S.S[g];
+                        if (sg != scur) {
+                            acc192_shl(T, sg - scur);
+                            scur = sg;
+                        }
+                        i128p v = garner(cz, 3);
+                        if (c == 1 && !a.merged) {   // II enters the real part with a minus sign
+                            v.lo = ~v.lo + 1ull;
+                            v.hi = (long long)(~(unsigned long long)v.hi + (v.lo == 0 ? 1ull : 0ull));
+                        }
+                        acc192_add128(T, v);
+                    }
+                    acc192_shl(T, smax - scur);
+                    acc192_add(A, T);
+                }
+                long long limbs[6];
+#pragma unroll
+                for (int l = 0; l < 5; ++l) limbs[l] = (long long)A.w[l];
+                limbs[5] = (long long)(int32_t)A.w[5];
+                yp[part] = acc_to_double<6>(limbs, -smax);
+            }
+        }
+        post_store(a, so, j, yp[0], yp[1]);
+    }
+}
+
 // shared-memory path: any prime count and scale span, one limb column per thread
 template <bool SD>
 __global__ void __launch_bounds__(WIDE_THREADS) crt_wide_kernel(CrtArgs a)
@@ -526,7 +614,7 @@ __global__ void __launch_bounds__(WIDE_THREADS) crt_wide_kernel(CrtArgs a)
     const int64_t work = a.B * chunks;
     for (int64_t item = blockIdx.x; item < work; item += gridDim.x) {
         const int64_t b = item / chunks;
-        if (reg_path(a, b)) {   // skip the signal
+        if (reg_path(a, b) || fast3_path(a, b)) {   // skip the signal
             item += ((chunks - 1 - item % chunks) / gridDim.x) * gridDim.x;
             continue;
         }
@@ -609,8 +697,13 @@ cudaError_t launch_crt_post(const CrtArgs& a, cudaStream_t s)
     if (e != cudaSuccess) return e;
     const int64_t chunks = (a.n + CRT_CHUNK - 1) / CRT_CHUNK;
     const bool sd = a.sd != nullptr;
-    if (sd) crt_fast_kernel<true><<<(unsigned)(a.B * chunks), FAST_THREADS, 0, s>>>(a);
-    else crt_fast_kernel<false><<<(unsigned)(a.B * chunks), FAST_THREADS, 0, s>>>(a);
+    if (a.P == 3) {
+        if (sd) crt_fast3_kernel<true><<<(unsigned)(a.B * chunks), FAST_THREADS, 0, s>>>(a);
+        else crt_fast3_kernel<false><<<(unsigned)(a.B * chunks), FAST_THREADS, 0, s>>>(a);
+    } else {
+        if (sd) crt_fast_kernel<true><<<(unsigned)(a.B * chunks), FAST_THREADS, 0, s>>>(a);
+        else crt_fast_kernel<false><<<(unsigned)(a.B * chunks), FAST_THREADS, 0, s>>>(a);
+    }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     // signals with three primes or a wide scale span: small blocks, limb columns in shared memory

@@ -57,6 +57,8 @@ STAGE_CASES = [  # n, N (0 = default), K, L, nprimes
     (777, 0, 4, 2, 3),
     (64, 0, 1, 1, 2),
     (4096, 0, 2, 3, 2),
+    (4096, 0, 2, 1, 3),     # three primes, K = 2 (alpha 39 at this n): the three-prime Horner path
+    (1000, 0, 2, 2, 3),
 ]
 
 
