@@ -134,7 +134,10 @@ int ozfft_execute(ozfft_plan_t plan, const void* in, void* out, void* stream);
 
 /* Same transform with HOST buffers: copies `in` to the device, transforms,
    copies the result to `out`, and returns after the stream has synchronized.
-   Pinned (page-locked) host memory gives the fastest copies. */
+   Batches of 8 or more signals (plain plans) run as a pipeline of four parts:
+   the copies in and out of neighbouring parts, on two streams of the plan,
+   overlap the computation of a part on `stream`.  Pinned (page-locked) host
+   memory gives the fastest copies and the overlap. */
 int ozfft_execute_host(ozfft_plan_t plan, const void* in, void* out, void* stream);
 
 /* Synchronize `stream`, return the data-dependent status recorded by the

@@ -73,6 +73,10 @@ struct ozfft_plan_s {
     uint32_t* dbg_X = nullptr;   // [B][2][K][P][N] (debug plans)
     double2* stage_in = nullptr; // host-buffer execution staging [B][n]
     double2* stage_out = nullptr;
+    // host-buffer execution pipeline: copy streams and per-part events
+    static constexpr int HOST_PARTS = 4;
+    cudaStream_t cs_in = nullptr, cs_out = nullptr;
+    cudaEvent_t ev_go = nullptr, ev_in[HOST_PARTS] = {}, ev_done[HOST_PARTS] = {};
     bool executed = false;
     int64_t total = 0;           // complex elements per execution (B n, or the packed lengths)
     int64_t fwd_plan = 0;        // forward NTTs of the w~* slices
@@ -321,6 +325,13 @@ static void plan_free(ozfft_plan_s* p)
     for (void* q : ptrs)
         if (q) cudaFree(q);
     for (ozfft_plan_s* c : p->classes) plan_free(c);
+    if (p->cs_in) cudaStreamDestroy(p->cs_in);
+    if (p->cs_out) cudaStreamDestroy(p->cs_out);
+    if (p->ev_go) cudaEventDestroy(p->ev_go);
+    for (int i = 0; i < ozfft_plan_s::HOST_PARTS; ++i) {
+        if (p->ev_in[i]) cudaEventDestroy(p->ev_in[i]);
+        if (p->ev_done[i]) cudaEventDestroy(p->ev_done[i]);
+    }
     if (p->gexec) cudaGraphExecDestroy(p->gexec);
     if (p->graph) cudaGraphDestroy(p->graph);
     for (cudaStream_t st : p->streams) cudaStreamDestroy(st);
@@ -605,14 +616,24 @@ static int autotune_ntt(ozfft_plan_s* p)
     return OZFFT_OK;
 }
 
-// One execution of a plan (or of one length class of a plan over uneven
-// lengths, whose input and output pointers come from io_ref): every kernel is
-// enqueued on s.
-static int run_plan(ozfft_plan_s* p, const void* in, void* out, cudaStream_t s)
+// One execution of the signals [sb0, sb0 + B) of a plan (all of them, or one
+// length class of a plan over uneven lengths, whose input and output pointers
+// come from io_ref): every kernel is enqueued on s.
+static int run_plan_range(ozfft_plan_s* p, const void* in, void* out, cudaStream_t s, int64_t sb0, int64_t B)
 {
-    const int64_t N = p->N, B = p->B;
-    const int K = p->K;
-    CUDA_TRY(cudaMemsetAsync(p->mu, 0, sizeof(uint64_t) * B * 2 * (K + 1), s));
+    const int64_t N = p->N;
+    const int K = p->K, P = p->P;
+    // the signals [sb0, sb0 + B) of the plan's per-signal buffers; in and out point at signal sb0
+    uint64_t* mu = p->mu + sb0 * 2 * (K + 1);
+    double* r = p->r + sb0 * (p->ts ? 3 : 2) * N;
+    uint32_t* X = p->X + sb0 * 2 * K * P * N;
+    int32_t* kcnt = p->kcnt + sb0 * 2;
+    Sched* sched = p->sched + sb0 * 4;
+    int32_t* span = p->span + sb0 * 3;
+    const SigDesc* sd = p->sd ? p->sd + sb0 : nullptr;
+    const uint32_t* Ym = p->Ym + sb0 * p->ym_stride;
+    const bool whole = sb0 == 0 && B == p->B;
+    CUDA_TRY(cudaMemsetAsync(mu, 0, sizeof(uint64_t) * B * 2 * (K + 1), s));
     p->cur = nullptr;
     if (p->profiling) {
         cudaEvent_t e0 = take_event(p);
@@ -623,51 +644,54 @@ static int run_plan(ozfft_plan_s* p, const void* in, void* out, cudaStream_t s)
         }
     }
     if (p->ts)
-        CUDA_TRY(launch_ts_premul((const double2*)in, p->chirp, p->n, N, B, p->direction > 0, (float*)p->r, p->mu, K,
+        CUDA_TRY(launch_ts_premul((const double2*)in, p->chirp, p->n, N, B, p->direction > 0, (float*)r, mu, K,
                                   p->status, s));
     else
-        CUDA_TRY(launch_premul((const double2*)in, p->chirp, p->n, N, B, p->direction > 0, p->sd, p->io_ref, p->r,
-                               p->mu, K, p->status, s));
+        CUDA_TRY(launch_premul((const double2*)in, p->chirp, p->n, N, B, p->direction > 0, sd, p->io_ref, r, mu, K,
+                               p->status, s));
     mark(p, OZFFT_PROF_PREMUL, s);
-    if (p->debug && !p->ts)
+    if (p->debug && whole && !p->ts)
         CUDA_TRY(cudaMemcpyAsync(p->dbg_r, p->r, sizeof(double) * B * 2 * N, cudaMemcpyDeviceToDevice, s));
     for (int k = 0; k < K; ++k) {
         if (p->ts)
-            CUDA_TRY(launch_ts_split_level(k, (float*)p->r, p->mu, N, B * 2, K, p->alpha, p->P, p->X, k + 1 < K,
-                                           p->status, s));
+            CUDA_TRY(launch_ts_split_level(k, (float*)r, mu, N, B * 2, K, p->alpha, P, X, k + 1 < K, p->status, s));
         else
-            CUDA_TRY(launch_split_level(k, p->r, p->mu, p->mu, N, B * 2, K, p->alpha, p->sd, p->P, p->X, k + 1 < K,
-                                        p->status, s));
+            CUDA_TRY(launch_split_level(k, r, mu, mu, N, B * 2, K, p->alpha, sd, P, X, k + 1 < K, p->status, s));
         mark(p, OZFFT_PROF_SPLIT, s);
     }
-    if (p->debug)
-        CUDA_TRY(cudaMemcpyAsync(p->dbg_X, p->X, sizeof(uint32_t) * B * 2 * K * p->P * N, cudaMemcpyDeviceToDevice, s));
-    schedule_kernel<<<(unsigned)((B + 127) / 128), 128, 0, s>>>(p->mu, B, K, p->L, p->alpha, p->sd, p->wk, p->wsexp,
-                                                                 p->sched, p->kcnt, p->span, p->merge);
+    if (p->debug && whole)
+        CUDA_TRY(cudaMemcpyAsync(p->dbg_X, p->X, sizeof(uint32_t) * B * 2 * K * P * N, cudaMemcpyDeviceToDevice, s));
+    schedule_kernel<<<(unsigned)((B + 127) / 128), 128, 0, s>>>(mu, B, K, p->L, p->alpha, sd, p->wk, p->wsexp, sched,
+                                                                 kcnt, span, p->merge);
     CUDA_TRY(cudaGetLastError());
     mark(p, OZFFT_PROF_SCHEDULE, s);
-    if (p->geom_fwd.m1 > 0) {
-        CUDA_TRY(launch_ntt_fwd_col(p->geom_fwd, p->X, p->tw, s));
+    NttGeom gf = p->geom_fwd;
+    gf.nvec = B * 2 * K * P;
+    gf.kcnt = kcnt;
+    gf.sched = sched;
+    if (gf.m1 > 0) {
+        CUDA_TRY(launch_ntt_fwd_col(gf, X, p->tw, s));
         mark(p, OZFFT_PROF_NTT_FWD_COL, s);
     }
-    CUDA_TRY(launch_ntt_fwd_row(p->geom_fwd, p->X, p->tw, s));
+    CUDA_TRY(launch_ntt_fwd_row(gf, X, p->tw, s));
     mark(p, OZFFT_PROF_NTT_FWD_ROW, s);
     // inverse stages chunk by chunk: Z of one chunk stays in L2 between the passes
     for (int64_t b0 = 0; b0 < B; b0 += p->chunk) {
         const int64_t nb = std::min<int64_t>(p->chunk, B - b0);
         NttGeom gi = p->geom_inv;
-        gi.nvec = nb * 4 * p->G * p->P;
-        gi.sched = p->sched + b0 * 4;
-        const MacSrc mac{p->X + b0 * 2 * K * p->P * N, p->Ym + b0 * p->ym_stride, p->ym_stride};
+        gi.nvec = nb * 4 * p->G * P;
+        gi.kcnt = kcnt;
+        gi.sched = sched + b0 * 4;
+        const MacSrc mac{X + b0 * 2 * K * P * N, Ym + b0 * p->ym_stride, p->ym_stride};
         CUDA_TRY(launch_ntt_inv_row(gi, p->Z, p->twinv, mac, s));
         mark(p, OZFFT_PROF_NTT_INV_ROW, s);
         if (gi.m1 > 0) {
             CUDA_TRY(launch_ntt_inv_col(gi, p->Z, p->twinv, s));
             mark(p, OZFFT_PROF_NTT_INV_COL, s);
         }
-        CrtArgs ca{p->Z, p->sched + b0 * 4, p->span + b0 * 3, p->chirp,
-                   p->sd ? (double2*)out : (double2*)out + b0 * p->n, p->n, N, nb,
-                   p->P, p->G, p->direction, p->status, p->sd ? p->sd + b0 : nullptr, p->io_ref, p->merge};
+        CrtArgs ca{p->Z, sched + b0 * 4, span + b0 * 3, p->chirp,
+                   sd ? (double2*)out : (double2*)out + b0 * p->n, p->n, N, nb,
+                   P, p->G, p->direction, p->status, sd ? sd + b0 : nullptr, p->io_ref, p->merge};
         if (p->ts) CUDA_TRY(launch_crt_ts(ca, s));
         else CUDA_TRY(launch_crt_post(ca, s));
         if (b0 + p->chunk < B) mark(p, OZFFT_PROF_CRT, s);
@@ -676,6 +700,14 @@ static int run_plan(ozfft_plan_s* p, const void* in, void* out, cudaStream_t s)
     p->cur = nullptr;
     p->executed = true;
     return OZFFT_OK;
+}
+
+// One execution of a plan (or of one length class of a plan over uneven
+// lengths, whose input and output pointers come from io_ref): every kernel is
+// enqueued on s.
+static int run_plan(ozfft_plan_s* p, const void* in, void* out, cudaStream_t s)
+{
+    return run_plan_range(p, in, out, s, 0, p->B);
 }
 
 // The length classes of a plan over uneven lengths, forked from s onto their
@@ -972,10 +1004,45 @@ int ozfft_execute_host(ozfft_plan_t p, const void* in, void* out, void* stream)
         if ((rc = dalloc(p, &p->stage_in, p->total))) return rc;
         if ((rc = dalloc(p, &p->stage_out, p->total))) return rc;
     }
-    CUDA_TRY(cudaMemcpyAsync(p->stage_in, in, bytes, cudaMemcpyHostToDevice, s));
-    int rc = ozfft_execute(p, p->stage_in, p->stage_out, stream);
-    if (rc) return rc;
-    CUDA_TRY(cudaMemcpyAsync(out, p->stage_out, bytes, cudaMemcpyDeviceToHost, s));
+    const int parts = (p->classes.empty() && !p->debug && p->B >= 8) ? ozfft_plan_s::HOST_PARTS : 1;
+    if (parts == 1) {
+        CUDA_TRY(cudaMemcpyAsync(p->stage_in, in, bytes, cudaMemcpyHostToDevice, s));
+        int rc = ozfft_execute(p, p->stage_in, p->stage_out, stream);
+        if (rc) return rc;
+        CUDA_TRY(cudaMemcpyAsync(out, p->stage_out, bytes, cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(cudaStreamSynchronize(s));
+        return OZFFT_OK;
+    }
+    // a pipeline over parts of the batch: the copy in of part i + 1 and the copy
+    // out of part i - 1 run on their own streams while part i computes on s
+    if (!p->cs_in) {
+        CUDA_TRY(cudaStreamCreateWithFlags(&p->cs_in, cudaStreamNonBlocking));
+        CUDA_TRY(cudaStreamCreateWithFlags(&p->cs_out, cudaStreamNonBlocking));
+        CUDA_TRY(cudaEventCreateWithFlags(&p->ev_go, cudaEventDisableTiming));
+        for (int i = 0; i < parts; ++i) {
+            CUDA_TRY(cudaEventCreateWithFlags(&p->ev_in[i], cudaEventDisableTiming));
+            CUDA_TRY(cudaEventCreateWithFlags(&p->ev_done[i], cudaEventDisableTiming));
+        }
+    }
+    CUDA_TRY(cudaEventRecord(p->ev_go, s));             // earlier work on s may still use the staging
+    CUDA_TRY(cudaStreamWaitEvent(p->cs_in, p->ev_go, 0));
+    const int64_t per = (p->B + parts - 1) / parts;
+    for (int i = 0; i < parts; ++i) {
+        const int64_t b0 = i * per, nb = std::min<int64_t>(per, p->B - b0);
+        if (nb <= 0) break;
+        const size_t off = (size_t)(b0 * p->n), cnt = (size_t)(nb * p->n);
+        CUDA_TRY(cudaMemcpyAsync(p->stage_in + off, (const double2*)in + off, sizeof(double2) * cnt,
+                                 cudaMemcpyHostToDevice, p->cs_in));
+        CUDA_TRY(cudaEventRecord(p->ev_in[i], p->cs_in));
+        CUDA_TRY(cudaStreamWaitEvent(s, p->ev_in[i], 0));
+        const int rc = run_plan_range(p, p->stage_in + off, p->stage_out + off, s, b0, nb);
+        if (rc) return rc;
+        CUDA_TRY(cudaEventRecord(p->ev_done[i], s));
+        CUDA_TRY(cudaStreamWaitEvent(p->cs_out, p->ev_done[i], 0));
+        CUDA_TRY(cudaMemcpyAsync((double2*)out + off, p->stage_out + off, sizeof(double2) * cnt,
+                                 cudaMemcpyDeviceToHost, p->cs_out));
+    }
+    CUDA_TRY(cudaStreamSynchronize(p->cs_out));
     CUDA_TRY(cudaStreamSynchronize(s));
     return OZFFT_OK;
 }

@@ -242,3 +242,19 @@ def test_in_place_and_host_buffers(oz):
     out = np.empty_like(x)
     plan.execute_host(np.ascontiguousarray(x), out)
     assert np.array_equal(out.view(np.uint64), ref.view(np.uint64))
+
+
+@pytest.mark.parametrize("B", [8, 13])
+def test_host_buffer_pipeline(oz, B):
+    """Batches of 8 or more signals run the host-buffer path as a pipeline of parts
+    (copies overlapping computation): same bits as the device-buffer execution."""
+    n = 3000
+    x = synth.complex_signal("phi", n, 16, batch=B, phi=1.0)
+    ref, plan = run_gpu(oz, x)
+    for pinned in (True, False):
+        hin = torch.from_numpy(x).pin_memory() if pinned else np.ascontiguousarray(x)
+        hout = torch.empty_like(hin).pin_memory() if pinned else np.empty_like(x)
+        for _ in range(2):
+            plan.execute_host(hin, hout)
+            got = hout.numpy() if pinned else hout
+            assert np.array_equal(got.view(np.uint64), ref.view(np.uint64)), (B, pinned)
