@@ -1,6 +1,7 @@
 // k_ntt_col.cu -- column-pass instantiations (one kernel per column length
 // 2^m1, m1 = 1..10) for both directions; the kernels are described in
-// ntt_impl.cuh.
+// ntt_impl.cuh.  Plans with a tensor map take the TMA kernels of
+// k_ntt_col_tma.cu for m1 >= 4.
 #include "ntt_impl.cuh"
 
 namespace oz {
@@ -8,6 +9,8 @@ namespace oz {
 cudaError_t launch_ntt_fwd_col(const NttGeom& g, uint32_t* data, const uint2* tw, cudaStream_t s)
 {
     if (g.nvec == 0 || g.m1 == 0) return cudaSuccess;
+    cudaError_t e;
+    if (launch_col_tma(false, g, tw, s, &e)) return e;
     switch (g.m1) {
     case 1: return launch_col_m<false, 1>(g, data, tw, s);
     case 2: return launch_col_m<false, 2>(g, data, tw, s);
@@ -26,6 +29,8 @@ cudaError_t launch_ntt_fwd_col(const NttGeom& g, uint32_t* data, const uint2* tw
 cudaError_t launch_ntt_inv_col(const NttGeom& g, uint32_t* data, const uint2* tw, cudaStream_t s)
 {
     if (g.nvec == 0 || g.m1 == 0) return cudaSuccess;
+    cudaError_t e;
+    if (launch_col_tma(true, g, tw, s, &e)) return e;
     switch (g.m1) {
     case 1: return launch_col_m<true, 1>(g, data, tw, s);
     case 2: return launch_col_m<true, 2>(g, data, tw, s);

@@ -89,16 +89,18 @@ __device__ __forceinline__ void radix_group(uint32_t (&v)[1 << RL], const uint2*
 }
 
 // load, transform and store one group whose elements are S words apart
-template <bool INV, int RL, int S>
+// (PAD = false: a dense tile without the pad words, as the tensor-memory-access
+// column pass keeps it)
+template <bool INV, int RL, int S, bool PAD = true>
 __device__ __forceinline__ void group_bfly(uint32_t* smp, const uint2* __restrict__ tw, int B0, uint32_t p)
 {
     constexpr int R = 1 << RL;
     uint32_t v[R];
 #pragma unroll
-    for (int u = 0; u < R; ++u) v[u] = smp[u * S + (u * S) / 32];
+    for (int u = 0; u < R; ++u) v[u] = smp[PAD ? u * S + (u * S) / 32 : u * S];
     radix_group<INV, RL>(v, tw, B0, p);
 #pragma unroll
-    for (int u = 0; u < R; ++u) smp[u * S + (u * S) / 32] = v[u];
+    for (int u = 0; u < R; ++u) smp[PAD ? u * S + (u * S) / 32 : u * S] = v[u];
 }
 
 // round partition of an M = 2^ML point pass: ceil(ML/4) rounds, sizes equal
@@ -147,7 +149,7 @@ __device__ __forceinline__ void row_round(uint32_t* sm, const PassArgs& a)
 }
 
 // column pass round: element l of column c at sm[pad((l << LOG_T) + c)]
-template <bool INV, int ML, int S0, int RL, int LOG_T>
+template <bool INV, int ML, int S0, int RL, int LOG_T, bool PAD = true>
 __device__ __forceinline__ void col_round(uint32_t* sm, const PassArgs& a)
 {
     constexpr int LOG_H = ML - S0 - RL, H = 1 << LOG_H, LOG_GPC = ML - RL;
@@ -159,20 +161,21 @@ __device__ __forceinline__ void col_round(uint32_t* sm, const PassArgs& a)
         const int l0 = (blk << (ML - S0)) + (grp & (H - 1));
         uint32_t p;
         const uint2* tw = table_of(a, 0, p);
-        group_bfly<INV, RL, H * T>(sm + pad_idx((l0 << LOG_T) + c), tw, (1 << S0) + blk, p);
+        const int at = (l0 << LOG_T) + c;
+        group_bfly<INV, RL, H * T, PAD>(sm + (PAD ? pad_idx(at) : at), tw, (1 << S0) + blk, p);
     }
 }
 
-template <bool INV, bool COL, int ML, int LOG_T, int I>
+template <bool INV, bool COL, int ML, int LOG_T, int I, bool PAD = true>
 __device__ __forceinline__ void run_rounds(uint32_t* sm, const PassArgs& a)
 {
     if constexpr (I < Part<ML>::NR) {
         constexpr int R_ = INV ? Part<ML>::NR - 1 - I : I;
         constexpr int S0 = Part<ML>::start(R_), RL = Part<ML>::size(R_);
-        if constexpr (COL) col_round<INV, ML, S0, RL, LOG_T>(sm, a);
+        if constexpr (COL) col_round<INV, ML, S0, RL, LOG_T, PAD>(sm, a);
         else row_round<INV, ML, S0, RL>(sm, a);
         __syncthreads();
-        run_rounds<INV, COL, ML, LOG_T, I + 1>(sm, a);
+        run_rounds<INV, COL, ML, LOG_T, I + 1, PAD>(sm, a);
     }
 }
 

@@ -20,6 +20,7 @@ constexpr int MAX_L = 8;                      // products per flush group
 // data-dependent status bits (ozfft_get_status)
 constexpr int ST_NONFINITE = 1;
 constexpr int ST_RANGE = 2;
+constexpr int ST_TIMEOUT = 4;   // a bounded device-side wait gave up
 
 struct PrimeInfo {
     uint32_t p;

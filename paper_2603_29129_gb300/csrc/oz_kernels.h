@@ -2,6 +2,7 @@
 // kernel translation units of libozfft.  Internal; not part of the C ABI.
 #pragma once
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "oz_common.cuh"
@@ -39,7 +40,18 @@ struct NttGeom {
     const int32_t* kcnt;   // [B][2] live split levels of x~' (forward skip test)
     const Sched* sched;    // [B][4] flush schedules (inverse skip test and MAC)
     int merged;            // schedules merge the two convolutions of each output part
+    const CUtensorMap* tmap;   // column pass by tensor memory access: [vectors][2^m1][2^m2] map of the
+                               // buffer (null: per-thread loads); host memory, passed by value
+    int64_t vec0;          // index of the launch's first vector in that map
+    int* status;           // status word for bounded waits that give up
 };
+
+// tensor map of a buffer of nvec vectors of 2^m1 x 2^m2 residues, box = one
+// column tile of the column pass (false when the geometry has no TMA kernel)
+bool ntt_make_tmap(CUtensorMap* map, const NttGeom& g, uint32_t* base, int64_t nvec);
+// k_ntt_col_tma.cu: the column pass by tensor memory access when g.tmap is set
+// and m1 >= 4; returns false (nothing launched) otherwise
+bool launch_col_tma(bool inv, const NttGeom& g, const uint2* tw, cudaStream_t s, cudaError_t* err);
 
 // Inputs of the multiply-accumulate fused into the inverse NTT's load.
 struct MacSrc {

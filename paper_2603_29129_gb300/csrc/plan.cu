@@ -52,6 +52,7 @@ struct ozfft_plan_s {
     int64_t chunk = 1;           // signals per inverse-stage chunk (Z holds one chunk)
     int device = 0;
     NttGeom geom_fwd{}, geom_inv{};
+    CUtensorMap tmap_x{}, tmap_z{};   // column-pass tensor maps of X and Z (when the geometry has them)
     int64_t launches = 0, bytes = 0;
     int32_t wk_host[2] = {0, 0};
     // device
@@ -361,6 +362,8 @@ static int dalloc(ozfft_plan_s* p, T** ptr, size_t count)
     return OZFFT_OK;
 }
 
+static void attach_tmaps(ozfft_plan_s* p);
+
 // twiddle tables, one per prime and direction: w_N = g^((p-1)/N) (inverse:
 // w_N^-1); entry 2^s + i = w^((N/2^(s+1)) bitrev_s(i)) with its Shoup
 // quotient, for the block-i butterflies of stage s (k_ntt.cu)
@@ -527,8 +530,19 @@ static int plan_build(ozfft_plan_s* p)
     const int64_t nchunks = (B + p->chunk - 1) / p->chunk;
     p->launches = 1 /*premul*/ + K /*split*/ + 1 /*schedule*/ + ntt_launches(p->geom_fwd) +
                   nchunks * (ntt_launches(p->geom_inv) + (p->ts ? 1 : crt_launches()));
+    attach_tmaps(p);
     CUDA_TRY(crt_init());
     return OZFFT_OK;
+}
+
+// the column-pass tensor maps of X (forward) and Z (inverse) for the plan's
+// current geometry; without them the column pass uses per-thread loads
+static void attach_tmaps(ozfft_plan_s* p)
+{
+    p->geom_fwd.status = p->geom_inv.status = p->status;
+    p->geom_fwd.vec0 = p->geom_inv.vec0 = 0;
+    p->geom_fwd.tmap = ntt_make_tmap(&p->tmap_x, p->geom_fwd, p->X, p->B * 2 * p->K * p->P) ? &p->tmap_x : nullptr;
+    p->geom_inv.tmap = ntt_make_tmap(&p->tmap_z, p->geom_inv, p->Z, p->chunk * 4 * p->G * p->P) ? &p->tmap_z : nullptr;
 }
 
 // Autotuning (ozfft_options.autotune): time every supported split of the
@@ -576,6 +590,9 @@ static int autotune_ntt(ozfft_plan_s* p)
         ntt_configure_split(gi, p->N, m2);
         gf.nvec = p->geom_fwd.nvec; gf.P = p->P; gf.K = p->K; gf.G = p->G; gf.kcnt = p->kcnt; gf.sched = p->sched;
         gi.nvec = p->geom_inv.nvec; gi.P = p->P; gi.K = p->K; gi.G = p->G; gi.kcnt = p->kcnt; gi.sched = p->sched;
+        CUtensorMap tx{}, tz{};   // this split's tensor maps, so the candidates run the kernels they would use
+        gf.tmap = ntt_make_tmap(&tx, gf, p->X, gf.nvec) ? &tx : nullptr;
+        gi.tmap = ntt_make_tmap(&tz, gi, p->Z, gi.nvec) ? &tz : nullptr;
         const MacSrc mac{p->X, p->Ym, p->ym_stride};
         float tf = 1e30f, ti = 1e30f;
         for (int rep = 0; rep < 3 && err == cudaSuccess; ++rep) {
@@ -613,6 +630,7 @@ static int autotune_ntt(ozfft_plan_s* p)
     const int64_t nchunks = (B + p->chunk - 1) / p->chunk;
     p->launches = 1 + K + 1 + ntt_launches(p->geom_fwd) +
                   nchunks * (ntt_launches(p->geom_inv) + (p->ts ? 1 : crt_launches()));
+    attach_tmaps(p);
     return OZFFT_OK;
 }
 
@@ -669,6 +687,7 @@ static int run_plan_range(ozfft_plan_s* p, const void* in, void* out, cudaStream
     gf.nvec = B * 2 * K * P;
     gf.kcnt = kcnt;
     gf.sched = sched;
+    gf.vec0 = sb0 * 2 * K * P;   // the launch's first vector in the tensor map of X
     if (gf.m1 > 0) {
         CUDA_TRY(launch_ntt_fwd_col(gf, X, p->tw, s));
         mark(p, OZFFT_PROF_NTT_FWD_COL, s);
@@ -1063,6 +1082,7 @@ int ozfft_get_status(ozfft_plan_t p, void* stream)
     }
     if (st & ST_NONFINITE) return OZFFT_ERR_NONFINITE;
     if (st & ST_RANGE) return OZFFT_ERR_RANGE;
+    if (st & ST_TIMEOUT) return OZFFT_ERR_TIMEOUT;
     return OZFFT_OK;
 }
 
