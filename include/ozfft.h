@@ -196,6 +196,17 @@ int ozfft_get_profile(ozfft_plan_t plan, void* stream, ozfft_profile* out);
    device memory.  *rate receives butterflies per second. */
 int ozfft_measure_butterfly_rate(int inverse, double* rate, void* stream);
 
+/* Self-test of failure detection (the paper has no counterpart): the device
+   waits of libozfft are bounded (the column pass polls its tile's mbarrier at
+   most 2^20 times, then records OZFFT_ERR_TIMEOUT in the plan's status word and
+   skips the tile).  This call runs one column-pass tile whose barrier expects
+   4 KiB more than its copy delivers, so the wait must give up; no address is
+   invalid and nothing spins without a limit.  It allocates and frees about
+   0.8 MiB, synchronizes `stream`, and returns OZFFT_ERR_TIMEOUT when the
+   timeout path reported the stall (the expected result), OZFFT_OK if the wait
+   completed, or an error code. */
+int ozfft_selftest_wait_timeout(void* stream);
+
 /* Transform without any allocation (the paper has no counterpart): for
    callers that cannot call cudaMalloc, such as code inside an application that
    owns the whole device memory pool (a stray cudaMalloc fails or fragments it)

@@ -63,7 +63,8 @@ __global__ void __launch_bounds__(NTT_THREADS, 8) ntt_col_tma_kernel(const __gri
     if (threadIdx.x == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bara) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bara), "r"(BYTES) : "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bara), "r"(BYTES + g.extra_tx)
+                     : "memory");
 #pragma unroll
         for (int b = 0; b < NBOX; ++b)
             asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
@@ -120,6 +121,46 @@ bool launch_col_tma(bool inv, const NttGeom& g, const uint2* tw, cudaStream_t s,
     default: *err = inv ? launch_col_tma_m<true, 10>(g, tw, s) : launch_col_tma_m<false, 10>(g, tw, s); break;
     }
     return true;
+}
+
+cudaError_t col_tma_timeout_selftest(int* status_host, cudaStream_t s)
+{
+    // one live vector of N = 2^16 (m1 = 4: 16 tiles of 256 columns x 16 rows) in fresh memory
+    NttGeom g{};
+    ntt_configure(g, int64_t(1) << 16);
+    g.nvec = 1;
+    g.P = 1;
+    g.K = 1;
+    g.G = 1;
+    g.extra_tx = 4096;                                 // never delivered: the bounded wait must give up
+    uint32_t* data = nullptr;
+    uint2* tw = nullptr;
+    int32_t* kcnt = nullptr;
+    int* status = nullptr;
+    CUtensorMap map;
+    cudaError_t e = cudaMalloc((void**)&data, sizeof(uint32_t) << 16);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&tw, sizeof(uint2) << 16);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&kcnt, 2 * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&status, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(data, 0, sizeof(uint32_t) << 16);
+    if (e == cudaSuccess) e = cudaMemset(tw, 0, sizeof(uint2) << 16);
+    const int32_t live[2] = {1, 1};
+    if (e == cudaSuccess) e = cudaMemcpy(kcnt, live, sizeof live, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(status, 0, sizeof(int));
+    if (e == cudaSuccess && !ntt_make_tmap(&map, g, data, 1)) e = cudaErrorNotSupported;
+    if (e == cudaSuccess) {
+        g.kcnt = kcnt;
+        g.tmap = &map;
+        g.status = status;
+        if (!launch_col_tma(false, g, tw, s, &e)) e = cudaErrorNotSupported;
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaMemcpy(status_host, status, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(data);
+    cudaFree(tw);
+    cudaFree(kcnt);
+    cudaFree(status);
+    return e;
 }
 
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no link to libcuda)

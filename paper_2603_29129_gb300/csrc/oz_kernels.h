@@ -44,6 +44,7 @@ struct NttGeom {
                                // buffer (null: per-thread loads); host memory, passed by value
     int64_t vec0;          // index of the launch's first vector in that map
     int* status;           // status word for bounded waits that give up
+    uint32_t extra_tx;     // self-test only: bytes the barrier expects beyond the tile (0)
 };
 
 // tensor map of a buffer of nvec vectors of 2^m1 x 2^m2 residues, box = one
@@ -52,6 +53,9 @@ bool ntt_make_tmap(CUtensorMap* map, const NttGeom& g, uint32_t* base, int64_t n
 // k_ntt_col_tma.cu: the column pass by tensor memory access when g.tmap is set
 // and m1 >= 4; returns false (nothing launched) otherwise
 bool launch_col_tma(bool inv, const NttGeom& g, const uint2* tw, cudaStream_t s, cudaError_t* err);
+// self-test of the bounded wait: one forward column-pass tile (N = 2^16) whose
+// barrier expects more bytes than its copy brings; *status receives the status bits
+cudaError_t col_tma_timeout_selftest(int* status_host, cudaStream_t s);
 
 // Inputs of the multiply-accumulate fused into the inverse NTT's load.
 struct MacSrc {

@@ -1013,6 +1013,14 @@ int ozfft_measure_butterfly_rate(int inverse, double* rate, void* stream)
     return OZFFT_OK;
 }
 
+int ozfft_selftest_wait_timeout(void* stream)
+{
+    int st = 0;
+    const cudaError_t e = col_tma_timeout_selftest(&st, (cudaStream_t)stream);
+    if (e != cudaSuccess) return fail(OZFFT_ERR_CUDA, std::string("wait self-test: ") + cudaGetErrorString(e));
+    return (st & ST_TIMEOUT) ? OZFFT_ERR_TIMEOUT : OZFFT_OK;
+}
+
 int ozfft_execute_host(ozfft_plan_t p, const void* in, void* out, void* stream)
 {
     if (!p || !in || !out) return fail(OZFFT_ERR_ARG, "ozfft_execute_host: null argument");

@@ -25,7 +25,7 @@ MAX_GROUPS, MAX_L = 64, 8
 EXPORTS = ("ozfft_plan", "ozfft_plan_ex", "ozfft_execute", "ozfft_execute_host", "ozfft_get_status",
            "ozfft_get_stats", "ozfft_set_profiling", "ozfft_get_profile", "ozfft_destroy", "ozfft_error_string",
            "ozfft_last_error", "ozfft_debug_dump", "ozfft_execute_noalloc", "ozfft_plan_many",
-           "ozfft_measure_butterfly_rate")
+           "ozfft_measure_butterfly_rate", "ozfft_selftest_wait_timeout")
 PROF_SLOTS = ("premul", "split", "schedule", "ntt_fwd_col", "ntt_fwd_row", "ntt_inv_row", "ntt_inv_col", "crt")
 
 
@@ -83,6 +83,8 @@ def load(path: str = LIB_PATH):
             L.ozfft_execute_noalloc.argtypes = [i64, C.c_int, P, P, P]
             L.ozfft_measure_butterfly_rate.restype = C.c_int
             L.ozfft_measure_butterfly_rate.argtypes = [C.c_int, C.POINTER(C.c_double), P]
+            L.ozfft_selftest_wait_timeout.restype = C.c_int
+            L.ozfft_selftest_wait_timeout.argtypes = [P]
             L.ozfft_plan_many.restype = P
             L.ozfft_plan_many.argtypes = [C.POINTER(i64), i64, C.c_int, C.POINTER(Options)]
             _lib = L
@@ -243,6 +245,12 @@ def butterfly_rate(inverse=False, stream=None):
     r = C.c_double(0.0)
     _check(load().ozfft_measure_butterfly_rate(int(bool(inverse)), C.byref(r), _stream_ptr(stream)))
     return r.value
+
+
+def selftest_wait_timeout(stream=None):
+    """Status code of ozfft_selftest_wait_timeout (ERR_TIMEOUT when the bounded
+    device wait gave up as it must)."""
+    return load().ozfft_selftest_wait_timeout(_stream_ptr(stream))
 
 
 def execute_noalloc(x, out, direction=FORWARD, stream=None):
