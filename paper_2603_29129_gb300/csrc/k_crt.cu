@@ -456,7 +456,7 @@ __device__ __forceinline__ void acc192_shl(Acc192& A, int d)
 // ends in units of 2^-S of its first group and is shifted to the signal's
 // 2^-max S; at most 2^62 * 64 * 2^FAST_SPAN in magnitude, inside 192 bits.
 template <bool SD>
-__global__ void __launch_bounds__(FAST_THREADS) crt_fast_kernel(CrtArgs a)
+__global__ void __launch_bounds__(FAST_THREADS, 10) crt_fast_kernel(CrtArgs a)
 {
     const int64_t chunks = (a.n + CRT_CHUNK - 1) / CRT_CHUNK;
     const int64_t b = blockIdx.x / chunks;
@@ -469,6 +469,11 @@ __global__ void __launch_bounds__(FAST_THREADS) crt_fast_kernel(CrtArgs a)
     const int64_t j1 = min(so.n, j0 + CRT_CHUNK);
     const Sched* sc = a.sched + b * 4;
     const int smax = a.span[b * 3 + 1], any = a.span[b * 3 + 2] & 1;
+    __shared__ int s_S[4][MAX_GROUPS], s_ng[4];   // the signal's group scales, read once per CTA
+    for (int i = threadIdx.x; i < 4 * MAX_GROUPS; i += blockDim.x)
+        s_S[i / MAX_GROUPS][i % MAX_GROUPS] = sc[i / MAX_GROUPS].S[i % MAX_GROUPS];
+    if (threadIdx.x < 4) s_ng[threadIdx.x] = sc[threadIdx.x].ngroups;
+    __syncthreads();
     for (int64_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
         double yp[2] = {0.0, 0.0};
         if (any) {
@@ -478,12 +483,12 @@ __global__ void __launch_bounds__(FAST_THREADS) crt_fast_kernel(CrtArgs a)
 #pragma unroll
                 for (int cc = 0; cc < 2; ++cc) {
                     const int c = 2 * part + cc;
-                    const Sched& S = sc[c];
-                    const int ng = S.ngroups;
+                    const int ng = s_ng[c];
+                    const int* SS = s_S[c];
                     if (ng == 0) continue;
                     const uint32_t* zp = a.Z + ((b * 4 + c) * a.G) * 2 * a.N + j;
                     Acc192 T = {{0u, 0u, 0u, 0u, 0u, 0u}};
-                    int scur = S.S[ng - 1];
+                    int scur = SS[ng - 1];
                     constexpr int PF = 9;
                     if (ng <= PF) {   // every group's residues in flight at once
                         uint32_t r0[PF], r1[PF];
@@ -496,7 +501,7 @@ __global__ void __launch_bounds__(FAST_THREADS) crt_fast_kernel(CrtArgs a)
 #pragma unroll
                         for (int q = PF - 1; q >= 0; --q)
                             if (q < ng) {
-                                const int sg = S.S[q];
+                                const int sg = SS[q];
                                 if (sg != scur) {
                                     acc192_shl(T, sg - scur);
                                     scur = sg;
@@ -517,7 +522,7 @@ __global__ void __launch_bounds__(FAST_THREADS) crt_fast_kernel(CrtArgs a)
                             z0 = __ldg(zp + (int64_t)(g - 1) * 2 * a.N);
                             z1 = __ldg(zp + (int64_t)(g - 1) * 2 * a.N + a.N);
                         }
-                        const int sg = S.S[g];
+                        const int sg = SS[g];
                         if (sg != scur) {
                             acc192_shl(T, sg - scur);
                             scur = sg;
