@@ -53,8 +53,11 @@ def parse():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--cpu-signals", type=int, default=0,
                     help="oracle transforms timed for cpu_baseline (default: one per host core)")
-    ap.add_argument("--autotune", action="store_true", help="autotune the NTT column/row split at plan time")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="keep the default NTT column/row split instead of timing the candidates at plan time")
     ap.add_argument("--merge", action="store_true", help="merged schedules across the convolutions of a part")
+    ap.add_argument("--row-log", type=int, default=0,
+                    help="force the NTT row pass to 2^row_log residues (profiling runs without plan-time tuning)")
     ap.add_argument("--ts", action="store_true", help="the TS (triple-single) variant of the method")
     ap.add_argument("--uneven-count", type=int, default=4096, help="signals of the uneven workload")
     ap.add_argument("--plain-sample", type=int, default=256,
@@ -79,7 +82,7 @@ def workload(a):
     return {"workload": f"complex128 n=2^{a.n.bit_length() - 1} x {a.batch} signals, uniform[-1,1) parts, "
                         f"forward, K={a.K}, L={a.L}, {a.nprimes} primes",
             "n": a.n, "batch_per_gpu": a.batch, "K": a.K, "L": a.L, "nprimes": a.nprimes, "seed": a.seed,
-            "autotune": a.autotune, "merge": a.merge, "ts": a.ts,
+            "autotune": a.autotune, "merge": a.merge, "ts": a.ts, "row_log": a.row_log,
             "l2": "inputs (batch x n x 16 B) exceed L2 each step; no flush"}
 
 
@@ -582,7 +585,7 @@ def main():
     y = torch.empty_like(x)
     stream = torch.cuda.current_stream(dev)
     plan = ozfft.Plan(n, B, ozfft.FORWARD, K=a.K, L=a.L, nprimes=a.nprimes, autotune=a.autotune, merge=a.merge,
-                      ts=a.ts)
+                      ts=a.ts, row_log=a.row_log)
 
     # ---- batched, device-resident (the headline value), with per-kernel events
     for _ in range(a.warmup):
@@ -614,7 +617,7 @@ def main():
     plain = None
     if not a.skip_plain:
         p1 = ozfft.Plan(n, 1, ozfft.FORWARD, K=a.K, L=a.L, nprimes=a.nprimes, autotune=a.autotune, merge=a.merge,
-                        ts=a.ts)
+                        ts=a.ts, row_log=a.row_log)
         xs = [x[i:i + 1] for i in range(B)]
         ys = [y[i:i + 1] for i in range(B)]
         for _ in range(a.warmup):
@@ -746,6 +749,7 @@ def main():
         "plain": plain, "e2e": e2e, "roofline": roof, "cpu_baseline": cpu, "clocks": clk,
         "gpu_launches": int(stats["kernel_launches"] * a.steps),
         "ntt": {"per_transform_runtime": total_ntt / B, "per_transform_total": (total_ntt + stats["ntt_forward_plan"] * B) / B,
+                "row_pass_stages": {"forward": m2f, "inverse": m2i},
                 "GBps_algorithmic": total_ntt * 8 * N / (ntt_ms / 1e3) / 1e9},
         "kernel_ms_per_step": breakdown, "accuracy": acc,
     }

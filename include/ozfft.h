@@ -91,6 +91,9 @@ typedef struct {
                          per transform and prime pair without gaps); the result is bit-identical
                          to merge = 0 with the same L, since y' is the exactly rounded sum of the
                          same products either way */
+    int32_t row_log;  /* nonzero: stages of the NTT row pass (10..14, the rest in the column pass) for
+                         both directions, instead of the default split or the autotuner's choice;
+                         OZFFT_ERR_ARG if no kernel covers that split of N */
     int32_t ts;       /* nonzero: the TS (triple-single) variant of §4.1 (Alg. 4, Alg. 6, Alg. 8):
                          chirp products and the split in TS arithmetic (three binary32 words,
                          rho = 24 - alpha, alpha capped at 23), the rescaled CRT integers

@@ -194,7 +194,9 @@ __device__ __forceinline__ bool inv_live(const NttGeom& g, unsigned vec)
     return grp < g.sched[bc].ngroups;
 }
 
-constexpr int col_log_t(int m1) { return (TILE_LOG - m1) > 5 ? (TILE_LOG - m1) : 5; }
+// columns per column-pass tile: 2^(12 - m1) up to m1 = 6 (4096-residue tiles), then 64
+// columns (256-byte row segments) up to m1 = 8, then 32
+constexpr int col_log_t(int m1) { return m1 <= 6 ? ((TILE_LOG - m1) > 5 ? (TILE_LOG - m1) : 5) : (m1 <= 8 ? 6 : 5); }
 
 // ---------------------------------------------------------------- column pass
 template <bool INV, int M1>

@@ -545,6 +545,21 @@ static void attach_tmaps(ozfft_plan_s* p)
     p->geom_inv.tmap = ntt_make_tmap(&p->tmap_z, p->geom_inv, p->Z, p->chunk * 4 * p->G * p->P) ? &p->tmap_z : nullptr;
 }
 
+// ozfft_options.row_log: the row pass of both directions forced to 2^m2 residues
+static int force_split(ozfft_plan_s* p, int m2)
+{
+    NttGeom gf = p->geom_fwd, gi = p->geom_inv;
+    if (!ntt_configure_split(p->geom_fwd, p->N, m2) || !ntt_configure_split(p->geom_inv, p->N, m2))
+        return fail(OZFFT_ERR_ARG, "ozfft_plan: no kernel for a row pass of 2^" + std::to_string(m2) + " residues");
+    p->geom_fwd.nvec = gf.nvec; p->geom_fwd.kcnt = gf.kcnt; p->geom_fwd.sched = gf.sched;
+    p->geom_inv.nvec = gi.nvec; p->geom_inv.kcnt = gi.kcnt; p->geom_inv.sched = gi.sched;
+    const int64_t nchunks = (p->B + p->chunk - 1) / p->chunk;
+    p->launches = 1 + p->K + 1 + ntt_launches(p->geom_fwd) +
+                  nchunks * (ntt_launches(p->geom_inv) + (p->ts ? 1 : crt_launches()));
+    attach_tmaps(p);
+    return OZFFT_OK;
+}
+
 // Autotuning (ozfft_options.autotune): time every supported split of the
 // plan's NTT length into column and row passes, forward and inverse, on the
 // plan's own buffers with every vector live, and keep the fastest of each.
@@ -811,7 +826,8 @@ ozfft_plan_t ozfft_plan_ex(int64_t n, int64_t batch, int direction, const ozfft_
         p->chunk = std::min<int64_t>(c, batch);
     }
     p->total = n * batch;
-    if (plan_build(p) != OZFFT_OK || (o.autotune && autotune_ntt(p) != OZFFT_OK)) {
+    if (plan_build(p) != OZFFT_OK || (o.autotune && !o.row_log && autotune_ntt(p) != OZFFT_OK) ||
+        (o.row_log && force_split(p, o.row_log) != OZFFT_OK)) {
         plan_free(p);
         return nullptr;
     }

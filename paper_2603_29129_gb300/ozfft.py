@@ -32,7 +32,7 @@ PROF_SLOTS = ("premul", "split", "schedule", "ntt_fwd_col", "ntt_fwd_row", "ntt_
 class Options(C.Structure):
     _fields_ = [("K", C.c_int32), ("L", C.c_int32), ("nprimes", C.c_int32), ("conv_len", C.c_int64),
                 ("debug", C.c_int32), ("chunk", C.c_int32), ("autotune", C.c_int32), ("no_graph", C.c_int32),
-                ("merge", C.c_int32), ("ts", C.c_int32)]
+                ("merge", C.c_int32), ("row_log", C.c_int32), ("ts", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -108,12 +108,12 @@ class Plan:
     """A plan for `batch` transforms of length n (see ozfft_plan_ex)."""
 
     def __init__(self, n, batch=1, direction=FORWARD, K=3, L=1, nprimes=2, conv_len=0, debug=False, chunk=0,
-                 autotune=False, merge=False, ts=False):
+                 autotune=False, merge=False, ts=False, row_log=0):
         lib = load()
         self.n, self.batch, self.direction = int(n), int(batch), int(direction)
         self.K, self.L, self.nprimes, self.merge, self.ts = int(K), int(L), int(nprimes), bool(merge), bool(ts)
         opt = Options(self.K, self.L, self.nprimes, int(conv_len), int(bool(debug)), int(chunk), int(bool(autotune)), 0,
-                      int(self.merge), int(self.ts))
+                      int(self.merge), int(row_log), int(self.ts))
         self._h = lib.ozfft_plan_ex(self.n, self.batch, self.direction, C.byref(opt))
         if not self._h:
             raise OzfftError(-1, lib.ozfft_last_error().decode())
@@ -225,7 +225,7 @@ class PlanMany(Plan):
         self.direction, self.K, self.L, self.nprimes = int(direction), int(K), int(L), int(nprimes)
         self.merge = bool(merge)
         opt = Options(self.K, self.L, self.nprimes, 0, 0, int(chunk), int(bool(autotune)), int(not graph),
-                      int(self.merge))
+                      int(self.merge), 0, 0)
         self._h = lib.ozfft_plan_many(lens.ctypes.data_as(C.POINTER(C.c_int64)), lens.size, self.direction,
                                       C.byref(opt))
         if not self._h:

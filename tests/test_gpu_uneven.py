@@ -77,12 +77,20 @@ def test_graph_chunking_autotune_agree(oz):
         assert np.array_equal(xi.cpu().numpy().view(np.uint64), r2.view(np.uint64)), kw
 
 
-def test_autotuned_uniform_plan(oz):
+def test_autotuned_and_forced_splits(oz):
+    """The autotuner's choice and every forced row/column split give the same bits."""
     n, B = 1 << 16, 4
     x = torch.from_numpy(synth.complex_signal("uniform", n, 65, batch=B)).cuda()
     a = oz.Plan(n, B).execute(x).cpu().numpy()
     b = oz.Plan(n, B, autotune=True).execute(x).cpu().numpy()
     assert np.array_equal(a.view(np.uint64), b.view(np.uint64))
+    for m2 in (10, 11, 13, 14):       # column passes of 2^6 (TMA) down to 2^2 (per-thread loads) rows
+        p = oz.Plan(n, B, row_log=m2)
+        assert p.stats()["row_log_inv"] == m2
+        c = p.execute(x).cpu().numpy()
+        assert np.array_equal(a.view(np.uint64), c.view(np.uint64)), m2
+    with pytest.raises(oz.OzfftError):
+        oz.Plan(n, B, row_log=3)
 
 
 def test_status_stats_and_errors(oz):

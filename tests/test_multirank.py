@@ -36,6 +36,7 @@ def _rank_main(rank, world, port, out):
     class A:   # a bounded reference-arm run: only rank 0 times and prints
         n, K, L, nprimes, seed, steps, warmup, batch = 64, 3, 1, 2, 2, 1, 0, 64
         autotune = merge = ts = False
+        row_log = 0
     buf = io.StringIO()
     with redirect_stdout(buf):
         bench.run_reference(A, rank, world)
