@@ -177,19 +177,31 @@ __global__ void __launch_bounds__(SPLIT_THREADS) premul_kernel(const double2* __
     bool bad = false;
     double* rr = r + (2 * b) * N;
     double* ri = rr + N;
-    for (int64_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
-        double re = 0.0, im = 0.0;
-        if (j < nb) {
-            const double2 xv = x[j];
-            const double2 wv = w[j];
-            const double xi = conj_in ? -xv.y : xv.y;
-            if (!isfinite(xv.x) || !isfinite(xv.y)) bad = true;
-            cmul(xv.x, xi, wv.x, wv.y, re, im);
+    for (int64_t jb = j0 + threadIdx.x; jb < j1; jb += 4 * (int64_t)blockDim.x) {
+        double2 xv[4], wv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {   // four elements' loads in flight before the arithmetic
+            const int64_t j = jb + u * (int64_t)blockDim.x;
+            if (j < j1 && j < nb) {
+                xv[u] = __ldg(x + j);
+                wv[u] = __ldg(w + j);
+            }
         }
-        rr[j] = re;
-        ri[j] = im;
-        mr = umax64(mr, (uint64_t)__double_as_longlong(re) & 0x7fffffffffffffffull);
-        mi = umax64(mi, (uint64_t)__double_as_longlong(im) & 0x7fffffffffffffffull);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t j = jb + u * (int64_t)blockDim.x;
+            if (j >= j1) break;
+            double re = 0.0, im = 0.0;
+            if (j < nb) {
+                const double xi = conj_in ? -xv[u].y : xv[u].y;
+                if (!isfinite(xv[u].x) || !isfinite(xv[u].y)) bad = true;
+                cmul(xv[u].x, xi, wv[u].x, wv[u].y, re, im);
+            }
+            rr[j] = re;
+            ri[j] = im;
+            mr = umax64(mr, (uint64_t)__double_as_longlong(re) & 0x7fffffffffffffffull);
+            mi = umax64(mi, (uint64_t)__double_as_longlong(im) & 0x7fffffffffffffffull);
+        }
     }
     if (bad) atomicOr(status, ST_NONFINITE);
     block_umax_to(&mu[(2 * b) * (K + 1)], mr);
