@@ -173,6 +173,26 @@ __device__ __forceinline__ long long garner2(uint32_t z0, uint32_t z1)
     return (long long)v0 + (long long)ds * (long long)P0;
 }
 
+// The same without centering z0, valid when every convolution value obeys
+// |z| < p0 p1 / 2 - p0 (the host checks L n 4^alpha against that bound).  With
+// u = z0 + e p0 in [0, p0 p1) (e = ((z1 - z0) p0^-1) mod p1): z >= 0 gives
+// u = z, so e p0 <= z < p0 p1 / 2 - p0 and e < (p1 - 1) / 2; z < 0 gives
+// u = z + p0 p1 > p0 p1 / 2 + p0, so e p0 > p0 p1 / 2 and e > (p1 - 1) / 2.
+// Taking e symmetric therefore yields z0 + e p0 = z in both cases.
+__device__ __forceinline__ long long garner2u(uint32_t z0, uint32_t z1)
+{
+    const uint32_t t = min(z0, z0 - P1);   // z0 mod p1 (z0 < p0 < 2 p1)
+    const uint32_t e = shoup(mod_sub(z1, t, P1), c_garner.inv01, c_garner.inv01q, P1);
+    const int32_t es = (int32_t)(e > (P1 - 1) / 2 ? e - P1 : e);
+    return (long long)es * (long long)P0 + (long long)z0;
+}
+
+template <bool UC>
+__device__ __forceinline__ long long garner2x(uint32_t z0, uint32_t z1)
+{
+    return UC ? garner2u(z0, z1) : garner2(z0, z1);
+}
+
 // acc[q..q+2] += digits of z * 2^b for a signed z with |z 2^b| < 2^95: two
 // unsigned low digits and a signed top digit; q is uniform across the warp, so
 // the switch selects fixed registers without divergence.
@@ -345,7 +365,7 @@ __device__ __forceinline__ void post_store(const CrtArgs& a, const SigOut& so, i
 }
 
 // register path: one output element per thread, integer-only accumulation
-template <bool SD>
+template <bool SD, bool UC>
 __device__ __forceinline__ void crt_reg_body(const CrtArgs& a)
 {
     const int64_t chunks = (a.n + CRT_CHUNK - 1) / CRT_CHUNK;
@@ -378,7 +398,7 @@ __device__ __forceinline__ void crt_reg_body(const CrtArgs& a)
                             z0 = __ldg(zp + (int64_t)(g + 1) * 2 * a.N);
                             z1 = __ldg(zp + (int64_t)(g + 1) * 2 * a.N + a.N);
                         }
-                        long long z = garner2(c0, c1);
+                        long long z = garner2x<UC>(c0, c1);
                         if (c == 1 && !a.merged) z = -z;   // II enters the real part with a minus sign
                         acc_add3(acc, z, smax - S.S[g]);
                     }
@@ -449,19 +469,74 @@ __device__ __forceinline__ void acc192_shl(Acc192& A, int d)
     }
 }
 
+// Round the 192-bit two's complement integer A (in units of 2^unit) to the
+// nearest binary64, ties to even: magnitude, leading 64-bit word, a 64-bit
+// window with the leading one at bit 63 and a sticky flag for the rest.  Not
+// inlined: inside the Horner kernels' register budget it would spill.
+__device__ __noinline__ double acc192_to_double(Acc192 A, int unit)
+{
+    const bool neg = (int32_t)A.w[5] < 0;
+    if (neg) {
+        const uint32_t zero = 0u;
+        asm("sub.cc.u32 %0, %6, %0;\n\t"
+            "subc.cc.u32 %1, %6, %1;\n\t"
+            "subc.cc.u32 %2, %6, %2;\n\t"
+            "subc.cc.u32 %3, %6, %3;\n\t"
+            "subc.cc.u32 %4, %6, %4;\n\t"
+            "subc.u32 %5, %6, %5;"
+            : "+r"(A.w[0]), "+r"(A.w[1]), "+r"(A.w[2]), "+r"(A.w[3]), "+r"(A.w[4]), "+r"(A.w[5])
+            : "r"(zero));
+    }
+    const unsigned long long h = ((unsigned long long)A.w[5] << 32) | A.w[4];
+    const unsigned long long m = ((unsigned long long)A.w[3] << 32) | A.w[2];
+    const unsigned long long l = ((unsigned long long)A.w[1] << 32) | A.w[0];
+    unsigned long long hi, mid;
+    bool low;
+    int top;
+    if (h) { top = 2; hi = h; mid = m; low = l != 0ull; }
+    else if (m) { top = 1; hi = m; mid = l; low = false; }
+    else if (l) { top = 0; hi = l; mid = 0ull; low = false; }
+    else return 0.0;
+    const int lz = __clzll((long long)hi);
+    const unsigned long long w = lz ? (hi << lz) | (mid >> (64 - lz)) : hi;
+    bool sticky = low || (mid << lz) != 0ull;
+    const int lead = unit + 64 * top + 63 - lz;            // exponent of the leading one
+    const int eulp = max(lead - 52, -1074);
+    if (eulp > 971) return neg ? -__longlong_as_double(0x7ff0000000000000ll) : __longlong_as_double(0x7ff0000000000000ll);
+    const int kb = lead - eulp + 1;                         // kept bits (<= 53)
+    unsigned long long qv;
+    bool rb;
+    if (kb >= 1) {
+        qv = w >> (64 - kb);
+        rb = (w >> (63 - kb)) & 1ull;
+        sticky = sticky || (w << (kb + 1)) != 0ull;
+    } else if (kb == 0) {
+        qv = 0;
+        rb = true;                                          // the leading one is the round bit
+        sticky = sticky || (w << 1) != 0ull;
+    } else {
+        qv = 0;
+        rb = false;
+        sticky = true;
+    }
+    if (rb && (sticky || (qv & 1ull))) qv += 1;
+    const double r = __longlong_as_double((long long)(((unsigned long long)(eulp + 1074) << 52) + qv));
+    return neg ? -r : r;
+}
+
 // Exact accumulation by Horner's rule: a convolution's groups run from the
 // last (smallest scale S, largest terms) to the first, so every change of
 // scale multiplies the running sum by 2^(S_new - S_old) >= 1, a left shift;
 // terms are then added as plain integers.  The running sum of a convolution
 // ends in units of 2^-S of its first group and is shifted to the signal's
 // 2^-max S; at most 2^62 * 64 * 2^FAST_SPAN in magnitude, inside 192 bits.
-template <bool SD>
+template <bool SD, bool UC>
 __global__ void __launch_bounds__(FAST_THREADS, 10) crt_fast_kernel(CrtArgs a)
 {
     const int64_t chunks = (a.n + CRT_CHUNK - 1) / CRT_CHUNK;
     const int64_t b = blockIdx.x / chunks;
     if (!fast_path(a, b)) {   // the signal's CTAs take the limb path instead (one launch for both)
-        crt_reg_body<SD>(a);
+        crt_reg_body<SD, UC>(a);
         return;
     }
     const SigOut so = sig_out<SD>(a, b);
@@ -506,7 +581,7 @@ __global__ void __launch_bounds__(FAST_THREADS, 10) crt_fast_kernel(CrtArgs a)
                                     acc192_shl(T, sg - scur);
                                     scur = sg;
                                 }
-                                long long z = garner2(r0[q], r1[q]);
+                                long long z = garner2x<UC>(r0[q], r1[q]);
                                 if (c == 1 && !a.merged) z = -z;
                                 acc192_add64(T, z);
                             }
@@ -527,18 +602,14 @@ __global__ void __launch_bounds__(FAST_THREADS, 10) crt_fast_kernel(CrtArgs a)
                             acc192_shl(T, sg - scur);
                             scur = sg;
                         }
-                        long long z = garner2(c0, c1);
+                        long long z = garner2x<UC>(c0, c1);
                         if (c == 1 && !a.merged) z = -z;   // II enters the real part with a minus sign
                         acc192_add64(T, z);
                     }
                     acc192_shl(T, smax - scur);
                     acc192_add(A, T);
                 }
-                long long limbs[6];
-#pragma unroll
-                for (int l = 0; l < 5; ++l) limbs[l] = (long long)A.w[l];
-                limbs[5] = (long long)(int32_t)A.w[5];
-                yp[part] = acc_to_double<6>(limbs, -smax);
+                yp[part] = acc192_to_double(A, -smax);
             }
         }
         post_store(a, so, j, yp[0], yp[1]);
@@ -599,11 +670,7 @@ __global__ void __launch_bounds__(FAST_THREADS) crt_fast3_kernel(CrtArgs a)
                     acc192_shl(T, smax - scur);
                     acc192_add(A, T);
                 }
-                long long limbs[6];
-#pragma unroll
-                for (int l = 0; l < 5; ++l) limbs[l] = (long long)A.w[l];
-                limbs[5] = (long long)(int32_t)A.w[5];
-                yp[part] = acc_to_double<6>(limbs, -smax);
+                yp[part] = acc192_to_double(A, -smax);
             }
         }
         post_store(a, so, j, yp[0], yp[1]);
@@ -706,8 +773,14 @@ cudaError_t launch_crt_post(const CrtArgs& a, cudaStream_t s)
         if (sd) crt_fast3_kernel<true><<<(unsigned)(a.B * chunks), FAST_THREADS, 0, s>>>(a);
         else crt_fast3_kernel<false><<<(unsigned)(a.B * chunks), FAST_THREADS, 0, s>>>(a);
     } else {
-        if (sd) crt_fast_kernel<true><<<(unsigned)(a.B * chunks), FAST_THREADS, 0, s>>>(a);
-        else crt_fast_kernel<false><<<(unsigned)(a.B * chunks), FAST_THREADS, 0, s>>>(a);
+        const unsigned grid = (unsigned)(a.B * chunks);
+        if (a.garner_u) {
+            if (sd) crt_fast_kernel<true, true><<<grid, FAST_THREADS, 0, s>>>(a);
+            else crt_fast_kernel<false, true><<<grid, FAST_THREADS, 0, s>>>(a);
+        } else {
+            if (sd) crt_fast_kernel<true, false><<<grid, FAST_THREADS, 0, s>>>(a);
+            else crt_fast_kernel<false, false><<<grid, FAST_THREADS, 0, s>>>(a);
+        }
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;

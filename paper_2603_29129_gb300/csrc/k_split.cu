@@ -307,6 +307,127 @@ __global__ void __launch_bounds__(SPLIT_THREADS) split_kernel(int k, double* __r
     if (k + 1 <= K) block_umax_to(&mu[v * (K + 1) + k + 1], m);
 }
 
+// All K levels of Alg. 3 in one pass over the vectors, the exponent of level
+// k >= 1 taken as e_k = e_0 - k alpha.  Level k rounds to a grid of 2^(e_k + 1
+// - alpha) (2^(e_k - alpha) for negative r), so its residual stays within
+// 2^(e_k - alpha) and e_(k+1) = ceil_log2 mu^(k+1) can only be that or smaller;
+// it is smaller only when no residual of the whole vector reaches half the
+// bound.  The maxima of the residuals actually produced are reduced into
+// mu[v][1..K] as the level-by-level kernel does; split_fix_kernel then redoes
+// every vector whose maxima contradict the guess, so the slices are those of
+// Alg. 3 either way.  Residuals are not written back (r keeps r^(0)).  KM
+// bounds K at compile time (the per-level maxima stay in registers).
+template <bool SD, int KM>
+__global__ void __launch_bounds__(SPLIT_THREADS) split_spec_kernel(const double* __restrict__ r,
+                                                                   uint64_t* __restrict__ mu, int64_t N, int K,
+                                                                   int alpha, const SigDesc* __restrict__ sd, int P,
+                                                                   uint32_t* __restrict__ X, int* status)
+{
+    const int64_t chunks = (N + CHUNK - 1) / CHUNK;
+    const int64_t v = blockIdx.x / chunks;
+    if (SD) alpha = sd[v >> 1].alpha;
+    const int64_t j0 = (blockIdx.x % chunks) * CHUNK;
+    const int64_t j1 = min(N, j0 + CHUNK);
+    const uint64_t mub = mu[v * (K + 1)];
+    if (mub == 0) return;                                 // every level empty
+    const int e0 = ceil_log2_pos(__longlong_as_double((long long)mub));
+    if (e0 + 53 - alpha > 1023) {
+        if (threadIdx.x == 0) atomicOr(status, ST_RANGE);
+        return;
+    }
+    const uint64_t* rv = reinterpret_cast<const uint64_t*>(r + v * N);
+    uint32_t* xv = X + (v * K) * P * N;
+    uint64_t m[KM];
+#pragma unroll
+    for (int k = 0; k < KM; ++k) m[k] = 0;
+    for (int64_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
+        uint64_t rb = rv[j];
+#pragma unroll
+        for (int k = 0; k < KM; ++k) {
+            if (k >= K) break;
+            long long q;
+            uint64_t rn;
+            split_level_int(rb, e0 - k * alpha, alpha, q, rn);
+#pragma unroll
+            for (int pi = 0; pi < MAX_PRIMES; ++pi) {
+                if (pi >= P) break;
+                const long long p = (long long)prime_of(pi);
+                long long a = alpha <= 30 ? q : q % p;   // |q| <= 2^alpha < p when alpha <= 30
+                if (a < 0) a += p;
+                xv[(k * P + pi) * N + j] = (uint32_t)a;
+            }
+            m[k] = umax64(m[k], rn & 0x7fffffffffffffffull);
+            rb = rn;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < KM; ++k) {
+        if (k >= K) break;
+        block_umax_to(&mu[v * (K + 1) + k + 1], m[k]);
+        __syncthreads();
+    }
+}
+
+// One CTA per vector: keep the speculative split when every nonzero mu[v][k]
+// (k = 1 .. K-1) has ceil_log2 = e_0 - k alpha; otherwise run Alg. 3 level by
+// level from r^(0), residuals in place, and rewrite mu[v][1..K].
+constexpr int FIX_THREADS = 512;
+template <bool SD>
+__global__ void __launch_bounds__(FIX_THREADS) split_fix_kernel(double* __restrict__ r, uint64_t* __restrict__ mu,
+                                                                int64_t N, int K, int alpha,
+                                                                const SigDesc* __restrict__ sd, int P,
+                                                                uint32_t* __restrict__ X)
+{
+    const int64_t v = blockIdx.x;
+    if (SD) alpha = sd[v >> 1].alpha;
+    uint64_t* mv = mu + v * (K + 1);
+    if (mv[0] == 0) return;
+    const int e0 = ceil_log2_pos(__longlong_as_double((long long)mv[0]));
+    if (e0 + 53 - alpha > 1023) return;                   // flagged by the speculative pass
+    bool ok = true;
+    for (int k = 1; k < K && ok; ++k) {
+        if (mv[k] == 0) break;                            // r^(k) = 0: the rest is zero under any exponent
+        ok = ceil_log2_pos(__longlong_as_double((long long)mv[k])) == e0 - k * alpha;
+    }
+    if (ok) return;
+    __syncthreads();                                      // every thread has read mu before it changes
+    __shared__ uint64_t redu[32];
+    uint64_t* rv = reinterpret_cast<uint64_t*>(r + v * N);
+    for (int k = 0; k < K; ++k) {
+        const uint64_t mk = mv[k];
+        if (mk == 0) {                                    // level k empty: so are the rest
+            if (threadIdx.x == 0)
+                for (int l = k + 1; l <= K; ++l) mv[l] = 0;
+            return;
+        }
+        const int e = ceil_log2_pos(__longlong_as_double((long long)mk));
+        uint32_t* xk = X + ((v * K + k) * P) * N;
+        uint64_t m = 0;
+        for (int64_t j = threadIdx.x; j < N; j += blockDim.x) {
+            long long q;
+            uint64_t rn;
+            split_level_int(rv[j], e, alpha, q, rn);
+            for (int pi = 0; pi < P; ++pi) {
+                const long long p = (long long)prime_of(pi);
+                long long a = alpha <= 30 ? q : q % p;
+                if (a < 0) a += p;
+                xk[pi * N + j] = (uint32_t)a;
+            }
+            if (k + 1 < K) rv[j] = rn;
+            m = umax64(m, rn & 0x7fffffffffffffffull);
+        }
+        for (int o = 16; o > 0; o >>= 1) m = umax64(m, (uint64_t)__shfl_xor_sync(0xffffffffu, (unsigned long long)m, o));
+        if ((threadIdx.x & 31) == 0) redu[threadIdx.x >> 5] = m;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint64_t t = 0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = umax64(t, redu[w]);
+            mv[k + 1] = t;
+        }
+        __syncthreads();                                  // mu[v][k + 1] and r^(k + 1) before the next level
+    }
+}
+
 // ------------------------------------------------------------------ launchers
 static unsigned grid_for(int64_t nvec, int64_t N) { return (unsigned)(nvec * ((N + CHUNK - 1) / CHUNK)); }
 
@@ -339,6 +460,22 @@ cudaError_t launch_split_level(int k, double* r, const uint64_t*, uint64_t* mu, 
 {
     if (sd) split_kernel<true><<<grid_for(nvec, N), SPLIT_THREADS, 0, s>>>(k, r, mu, N, K, alpha, sd, P, X, write_r, status);
     else split_kernel<false><<<grid_for(nvec, N), SPLIT_THREADS, 0, s>>>(k, r, mu, N, K, alpha, sd, P, X, write_r, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_split_spec(double* r, uint64_t* mu, int64_t N, int64_t nvec, int K, int alpha, const SigDesc* sd,
+                              int P, uint32_t* X, int* status, cudaStream_t s)
+{
+    const unsigned grid = grid_for(nvec, N);
+    if (sd) {
+        if (K <= 4) split_spec_kernel<true, 4><<<grid, SPLIT_THREADS, 0, s>>>(r, mu, N, K, alpha, sd, P, X, status);
+        else split_spec_kernel<true, MAX_K><<<grid, SPLIT_THREADS, 0, s>>>(r, mu, N, K, alpha, sd, P, X, status);
+        split_fix_kernel<true><<<(unsigned)nvec, FIX_THREADS, 0, s>>>(r, mu, N, K, alpha, sd, P, X);
+    } else {
+        if (K <= 4) split_spec_kernel<false, 4><<<grid, SPLIT_THREADS, 0, s>>>(r, mu, N, K, alpha, sd, P, X, status);
+        else split_spec_kernel<false, MAX_K><<<grid, SPLIT_THREADS, 0, s>>>(r, mu, N, K, alpha, sd, P, X, status);
+        split_fix_kernel<false><<<(unsigned)nvec, FIX_THREADS, 0, s>>>(r, mu, N, K, alpha, sd, P, X);
+    }
     return cudaGetLastError();
 }
 

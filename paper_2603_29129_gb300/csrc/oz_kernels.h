@@ -90,6 +90,11 @@ cudaError_t launch_premul(const double2* x, const double2* w, int64_t n, int64_t
 cudaError_t launch_split_level(int k, double* r, const uint64_t* mu_in, uint64_t* mu_out, int64_t N,
                                int64_t nvec, int K, int alpha, const SigDesc* sd, int P, uint32_t* X, int write_r,
                                int* status, cudaStream_t s);
+// every level at once with guessed exponents, then a per-vector check that
+// redoes the vectors whose residual maxima contradict the guess (2 kernels)
+cudaError_t launch_split_spec(double* r, uint64_t* mu, int64_t N, int64_t nvec, int K, int alpha, const SigDesc* sd,
+                              int P, uint32_t* X, int* status, cudaStream_t s);
+constexpr int SPLIT_SPEC_LAUNCHES = 2;
 cudaError_t launch_set_io(IoPtrs* io, const void* in, void* out, cudaStream_t s);
 
 // k_crt.cu
@@ -105,6 +110,7 @@ struct CrtArgs {
     const SigDesc* sd;     // [B] per-signal lengths and offsets, or null
     const IoPtrs* io;      // device-held output pointer, or null
     int merged;            // merged schedules: the MAC already applied the sign of II
+    int garner_u;          // |z| < p0 p1 / 2 - p0 for every value: two-prime CRT without centering z0
 };
 int crt_launches();        // kernels per launch_crt_post
 cudaError_t crt_init();    // uploads the Garner constants (once; call before any stream capture)

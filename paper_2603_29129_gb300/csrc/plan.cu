@@ -49,6 +49,7 @@ static int fail(int code, const std::string& msg)
 struct ozfft_plan_s {
     int64_t n = 0, N = 0, B = 0;
     int direction = -1, K = 3, L = 1, P = 2, alpha = 0, G = 9, debug = 0, merge = 0, ts = 0;
+    int garner_u = 0;            // every convolution value |z| < p0 p1 / 2 - p0 (CRT without centering z0)
     int64_t chunk = 1;           // signals per inverse-stage chunk (Z holds one chunk)
     int device = 0;
     NttGeom geom_fwd{}, geom_inv{};
@@ -172,6 +173,17 @@ static int alpha_h(int64_t n, int L, int P)
         if ((base << (2 * t)) < prod) a = t; else break;
     }
     return a;
+}
+
+// |z| <= L n 4^alpha for every convolution value of a signal (|q| <= 2^alpha
+// for every slice); the two-prime CRT may skip centering z0 when that stays
+// below p0 p1 / 2 - p0
+static bool garner_u_ok(int64_t n, int L, int alpha)
+{
+    if (alpha < 0 || alpha > 40) return false;
+    const unsigned __int128 P01 = (unsigned __int128)prime_of(0) * prime_of(1);
+    const unsigned __int128 zmax = (unsigned __int128)((uint64_t)L * (uint64_t)n) << (2 * alpha);
+    return 2 * (zmax + prime_of(0)) < P01;
 }
 
 static int ceil_log2_h(double mu)
@@ -410,6 +422,9 @@ static int build_twiddles(ozfft_plan_s* p)
 // signal; a plain plan has one of each for the batch.
 static int plan_build(ozfft_plan_s* p)
 {
+    p->garner_u = p->P == 2;
+    if (p->sd_host.empty()) p->garner_u = p->garner_u && garner_u_ok(p->n, p->L, p->alpha);
+    for (const SigDesc& d : p->sd_host) p->garner_u = p->garner_u && garner_u_ok(d.n, p->L, d.alpha);
     const int64_t N = p->N, B = p->B;
     const int K = p->K, P = p->P;
     const bool uneven = !p->sd_host.empty();
@@ -528,7 +543,7 @@ static int plan_build(ozfft_plan_s* p)
     p->geom_inv.kcnt = p->kcnt;
     p->geom_inv.sched = p->sched;
     const int64_t nchunks = (B + p->chunk - 1) / p->chunk;
-    p->launches = 1 /*premul*/ + K /*split*/ + 1 /*schedule*/ + ntt_launches(p->geom_fwd) +
+    p->launches = 1 /*premul*/ + (p->ts ? K : SPLIT_SPEC_LAUNCHES) /*split*/ + 1 /*schedule*/ + ntt_launches(p->geom_fwd) +
                   nchunks * (ntt_launches(p->geom_inv) + (p->ts ? 1 : crt_launches()));
     attach_tmaps(p);
     CUDA_TRY(crt_init());
@@ -554,7 +569,7 @@ static int force_split(ozfft_plan_s* p, int m2)
     p->geom_fwd.nvec = gf.nvec; p->geom_fwd.kcnt = gf.kcnt; p->geom_fwd.sched = gf.sched;
     p->geom_inv.nvec = gi.nvec; p->geom_inv.kcnt = gi.kcnt; p->geom_inv.sched = gi.sched;
     const int64_t nchunks = (p->B + p->chunk - 1) / p->chunk;
-    p->launches = 1 + p->K + 1 + ntt_launches(p->geom_fwd) +
+    p->launches = 1 + (p->ts ? p->K : SPLIT_SPEC_LAUNCHES) + 1 + ntt_launches(p->geom_fwd) +
                   nchunks * (ntt_launches(p->geom_inv) + (p->ts ? 1 : crt_launches()));
     attach_tmaps(p);
     return OZFFT_OK;
@@ -643,7 +658,7 @@ static int autotune_ntt(ozfft_plan_s* p)
     p->geom_inv.nvec = gi.nvec; p->geom_inv.P = gi.P; p->geom_inv.K = gi.K; p->geom_inv.G = gi.G;
     p->geom_inv.kcnt = gi.kcnt; p->geom_inv.sched = gi.sched;
     const int64_t nchunks = (B + p->chunk - 1) / p->chunk;
-    p->launches = 1 + K + 1 + ntt_launches(p->geom_fwd) +
+    p->launches = 1 + (p->ts ? K : SPLIT_SPEC_LAUNCHES) + 1 + ntt_launches(p->geom_fwd) +
                   nchunks * (ntt_launches(p->geom_inv) + (p->ts ? 1 : crt_launches()));
     attach_tmaps(p);
     return OZFFT_OK;
@@ -685,11 +700,13 @@ static int run_plan_range(ozfft_plan_s* p, const void* in, void* out, cudaStream
     mark(p, OZFFT_PROF_PREMUL, s);
     if (p->debug && whole && !p->ts)
         CUDA_TRY(cudaMemcpyAsync(p->dbg_r, p->r, sizeof(double) * B * 2 * N, cudaMemcpyDeviceToDevice, s));
-    for (int k = 0; k < K; ++k) {
-        if (p->ts)
+    if (p->ts) {
+        for (int k = 0; k < K; ++k) {
             CUDA_TRY(launch_ts_split_level(k, (float*)r, mu, N, B * 2, K, p->alpha, P, X, k + 1 < K, p->status, s));
-        else
-            CUDA_TRY(launch_split_level(k, r, mu, mu, N, B * 2, K, p->alpha, sd, P, X, k + 1 < K, p->status, s));
+            mark(p, OZFFT_PROF_SPLIT, s);
+        }
+    } else {
+        CUDA_TRY(launch_split_spec(r, mu, N, B * 2, K, p->alpha, sd, P, X, p->status, s));
         mark(p, OZFFT_PROF_SPLIT, s);
     }
     if (p->debug && whole)
@@ -725,7 +742,8 @@ static int run_plan_range(ozfft_plan_s* p, const void* in, void* out, cudaStream
         }
         CrtArgs ca{p->Z, sched + b0 * 4, span + b0 * 3, p->chirp,
                    sd ? (double2*)out : (double2*)out + b0 * p->n, p->n, N, nb,
-                   P, p->G, p->direction, p->status, sd ? sd + b0 : nullptr, p->io_ref, p->merge};
+                   P, p->G, p->direction, p->status, sd ? sd + b0 : nullptr, p->io_ref, p->merge,
+                   p->garner_u};
         if (p->ts) CUDA_TRY(launch_crt_ts(ca, s));
         else CUDA_TRY(launch_crt_post(ca, s));
         if (b0 + p->chunk < B) mark(p, OZFFT_PROF_CRT, s);
@@ -1313,6 +1331,7 @@ static int noalloc_setup(NoallocState& st, int dev, int64_t n, int64_t N, int al
     ozfft_plan_s& p = st.plan;
     const int K = 3, P = 2, NM = (int)NOALLOC_MAX_N;
     p.n = n; p.N = N; p.B = 1; p.K = K; p.L = 1; p.P = P; p.G = K * K; p.alpha = alpha; p.debug = 0; p.chunk = 1;
+    p.garner_u = garner_u_ok(n, 1, alpha);
     p.device = dev; p.profiling = false; p.bytes = 0;
     unsigned char* cur = st.base;
     p.chirp = (double2*)noalloc_take(cur, sizeof(double2) * NM);

@@ -149,6 +149,37 @@ def test_split_gaps_moderate_spans(oz, tiny):
             assert np.array_equal(y[b].view(np.uint64), yo.view(np.uint64)), (tiny, L, b)
 
 
+def test_split_exponent_guess_redone(oz):
+    """The one-pass split guesses e_k = e_0 - k alpha for the later levels and
+    redoes, level by level, every vector whose residual maxima say otherwise.
+    Impulses whose value has a short second slice (1 + 2^-40: the level-1
+    residual is far below its bound) or none at all (1.0) sit in one batch with
+    vectors where the guess holds; every level's residues and the output must
+    match the oracle."""
+    n = 10000                         # N = 2^15: several CTAs per vector in the one-pass kernel
+    xs = synth.complex_signal("uniform", n, 16, batch=5)
+    xs[1] = 0.0
+    xs[1, 0] = (1.0 + 2.0 ** -40) + (3.0 - 2.0 ** -45) * 1j
+    xs[2] = 0.0
+    xs[2, 0] = 1.0 - 0.5j
+    xs[3, 1:] *= 2.0 ** -30            # level 1 of a dominant first sample over small ones
+    xs[3, 0] = 1.0 + 2.0 ** -20
+    xs[4] = synth.complex_signal("spikes", n, 17)[0]
+    y, plan = run_gpu(oz, xs, debug=True)
+    assert plan.status() == oz.OK
+    for b in range(xs.shape[0]):
+        yo, info = oracle_vs(xs[b], plan, trace={"q"})
+        res = plan.dump(oz.DUMP_XRES, b)
+        mu = plan.dump(oz.DUMP_MU, b)
+        for v in range(2):
+            assert np.count_nonzero(mu[v][:plan.K]) == info["kcount"][v], (b, v)
+            for k in range(info["kcount"][v]):
+                for i in range(plan.nprimes):
+                    p = oracle.prime(i)
+                    assert np.array_equal(res[v, k, i], (info["q"][v, k] % p).astype(np.uint32)), (b, v, k, i)
+        assert np.array_equal(y[b].view(np.uint64), yo.view(np.uint64)), b
+
+
 def test_batch_mixed_distributions(oz):
     n = 2048
     xs = np.concatenate([synth.complex_signal(k, n, 7, phi=4.0) for k in
