@@ -241,7 +241,10 @@ const char* ozfft_last_error(void);
    `stream`.  `index` selects the signal b (or is ignored).  Stages:
      OZFFT_DUMP_CHIRP     n complex128                 chirp table w
      OZFFT_DUMP_XPRIME    [2][N] binary64              Re/Im of x~' of signal b
-     OZFFT_DUMP_MU        [2][K+1] binary64            per-level maxima of signal b
+     OZFFT_DUMP_MU        [2][K+1] binary64            per-level maxima of signal b: entry 0 is
+                                                       max |x~'|; entry k >= 1 is 2^ceil(log2 max
+                                                       |r^(k)|) (Alg. 3 uses mu only through
+                                                       ceil(log2 mu)), 0 for an empty level
      OZFFT_DUMP_XRES      [2][K][P][N] uint32          slice residues of signal b before the NTT
                                                        (plans made with options.debug only)
      OZFFT_DUMP_XSPEC     [2][K][P][N] uint32          forward spectra of signal b, natural order

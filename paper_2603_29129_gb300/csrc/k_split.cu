@@ -192,9 +192,11 @@ __global__ void __launch_bounds__(SPLIT_THREADS) premul_kernel(const double2* __
             const int64_t j = jb + u * (int64_t)blockDim.x;
             if (j >= j1) break;
             double re = 0.0, im = 0.0;
-            if (j < nb) {
-                const double xi = conj_in ? -xv[u].y : xv[u].y;
-                if (!isfinite(xv[u].x) || !isfinite(xv[u].y)) bad = true;
+            if (j < nb) {   // integer sign flip and finiteness test: the binary64 pipe is kept for the product
+                const uint64_t bx = (uint64_t)__double_as_longlong(xv[u].x);
+                const uint64_t by = (uint64_t)__double_as_longlong(xv[u].y);
+                if ((~bx & 0x7ff0000000000000ull) == 0 || (~by & 0x7ff0000000000000ull) == 0) bad = true;
+                const double xi = __longlong_as_double((long long)(by ^ ((uint64_t)(conj_in != 0) << 63)));
                 cmul(xv[u].x, xi, wv[u].x, wv[u].y, re, im);
             }
             rr[j] = re;
@@ -307,16 +309,63 @@ __global__ void __launch_bounds__(SPLIT_THREADS) split_kernel(int k, double* __r
     if (k + 1 <= K) block_umax_to(&mu[v * (K + 1) + k + 1], m);
 }
 
+// One level of Alg. 3 on an element held as sign, integer magnitude and the
+// fixed exponent of its binary64 input: r = (-1)^neg a 2^E with a < 2^53 and
+// E the weight of the input's last mantissa bit.  The level's grid is 2^g
+// (g as in split_level_int); with sh = g - E the level keeps
+// kq = round_half_even(a / 2^sh) grid units and leaves the exact residual
+// (a - kq 2^sh) 2^E, which stays in the same units, so nothing is renormalised
+// between levels.  q = +-kq 2^(g - (e - alpha)).
+__device__ __forceinline__ long long split_level_fixed(uint64_t& a, bool& neg, int E, int e, int alpha)
+{
+    if (a == 0) return 0;
+    const int g = max(neg ? e - alpha : e + 1 - alpha, -1074);
+    const int sh = g - E;
+    uint64_t kq;
+    long long d;
+    if (sh <= 0) {                       // the grid is at least as fine as the input: all of it is kept
+        kq = a << (-sh);
+        d = 0;
+    } else if (sh >= 64) {               // a < 2^53 <= 2^(sh - 1): rounds to zero
+        kq = 0;
+        d = (long long)a;
+    } else {
+        kq = a >> sh;
+        const uint64_t rem = a & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+        if (rem > half || (rem == half && (kq & 1))) ++kq;
+        d = (long long)a - (long long)(kq << sh);
+    }
+    long long q = (long long)(kq << (g - (e - alpha)));
+    if (neg) q = -q;
+    neg = neg != (d < 0);
+    a = (uint64_t)(d < 0 ? -d : d);
+    return q;
+}
+
+// ceil(log2(a 2^E)) for a > 0
+__device__ __forceinline__ int ceil_log2_fixed(uint64_t a, int E)
+{
+    return E + (a == 1 ? 0 : 64 - __clzll((long long)(a - 1)));
+}
+
+// binary64 bit pattern of 2^c (-1074 <= c <= 1023)
+__device__ __forceinline__ uint64_t pow2_bits(int c)
+{
+    return c >= -1022 ? (uint64_t)(c + 1023) << 52 : 1ull << (c + 1074);
+}
+
 // All K levels of Alg. 3 in one pass over the vectors, the exponent of level
 // k >= 1 taken as e_k = e_0 - k alpha.  Level k rounds to a grid of 2^(e_k + 1
 // - alpha) (2^(e_k - alpha) for negative r), so its residual stays within
 // 2^(e_k - alpha) and e_(k+1) = ceil_log2 mu^(k+1) can only be that or smaller;
 // it is smaller only when no residual of the whole vector reaches half the
-// bound.  The maxima of the residuals actually produced are reduced into
-// mu[v][1..K] as the level-by-level kernel does; split_fix_kernel then redoes
-// every vector whose maxima contradict the guess, so the slices are those of
-// Alg. 3 either way.  Residuals are not written back (r keeps r^(0)).  KM
-// bounds K at compile time (the per-level maxima stay in registers).
+// bound.  Alg. 3 uses mu^(k) only through ceil_log2 mu^(k), and ceil_log2 of a
+// maximum is the maximum of the ceil_log2, so mu[v][k] (k >= 1) receives
+// 2^ceil_log2 of the largest residual (0 when all are zero);
+// split_fix_kernel then redoes every vector whose exponents contradict the
+// guess, so the slices are those of Alg. 3 either way.  Residuals are not
+// written back (r keeps r^(0)).  KM bounds K at compile time (the per-level
+// maxima stay in registers).
 template <bool SD, int KM>
 __global__ void __launch_bounds__(SPLIT_THREADS) split_spec_kernel(const double* __restrict__ r,
                                                                    uint64_t* __restrict__ mu, int64_t N, int K,
@@ -337,40 +386,50 @@ __global__ void __launch_bounds__(SPLIT_THREADS) split_spec_kernel(const double*
     }
     const uint64_t* rv = reinterpret_cast<const uint64_t*>(r + v * N);
     uint32_t* xv = X + (v * K) * P * N;
-    uint64_t m[KM];
+    int cmax[KM];
 #pragma unroll
-    for (int k = 0; k < KM; ++k) m[k] = 0;
+    for (int k = 0; k < KM; ++k) cmax[k] = -2000;
     for (int64_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
-        uint64_t rb = rv[j];
+        const uint64_t rb = rv[j];
+        bool neg = (rb >> 63) != 0;
+        const int Eb = (int)((rb >> 52) & 0x7ff);
+        uint64_t a = rb & ((1ull << 52) - 1);
+        int E = -1074;
+        if (Eb) { a |= 1ull << 52; E = Eb - 1075; }
 #pragma unroll
         for (int k = 0; k < KM; ++k) {
             if (k >= K) break;
-            long long q;
-            uint64_t rn;
-            split_level_int(rb, e0 - k * alpha, alpha, q, rn);
+            const long long q = split_level_fixed(a, neg, E, e0 - k * alpha, alpha);
 #pragma unroll
             for (int pi = 0; pi < MAX_PRIMES; ++pi) {
                 if (pi >= P) break;
-                const long long p = (long long)prime_of(pi);
-                long long a = alpha <= 30 ? q : q % p;   // |q| <= 2^alpha < p when alpha <= 30
-                if (a < 0) a += p;
-                xv[(k * P + pi) * N + j] = (uint32_t)a;
+                const uint32_t p = prime_of(pi);
+                uint32_t res;
+                if (alpha <= 30) {               // |q| <= 2^alpha < p
+                    const int32_t q32 = (int32_t)q;
+                    res = q32 < 0 ? (uint32_t)(q32 + (int32_t)p) : (uint32_t)q32;
+                } else {
+                    long long t = q % (long long)p;
+                    if (t < 0) t += p;
+                    res = (uint32_t)t;
+                }
+                xv[(k * P + pi) * N + j] = res;
             }
-            m[k] = umax64(m[k], rn & 0x7fffffffffffffffull);
-            rb = rn;
+            if (a) cmax[k] = max(cmax[k], ceil_log2_fixed(a, E));
         }
     }
 #pragma unroll
     for (int k = 0; k < KM; ++k) {
         if (k >= K) break;
-        block_umax_to(&mu[v * (K + 1) + k + 1], m[k]);
+        block_umax_to(&mu[v * (K + 1) + k + 1], cmax[k] > -2000 ? pow2_bits(cmax[k]) : 0ull);
         __syncthreads();
     }
 }
 
 // One CTA per vector: keep the speculative split when every nonzero mu[v][k]
 // (k = 1 .. K-1) has ceil_log2 = e_0 - k alpha; otherwise run Alg. 3 level by
-// level from r^(0), residuals in place, and rewrite mu[v][1..K].
+// level from r^(0), residuals in place, and rewrite mu[v][1..K] (as powers of
+// two, like the one-pass kernel).
 constexpr int FIX_THREADS = 512;
 template <bool SD>
 __global__ void __launch_bounds__(FIX_THREADS) split_fix_kernel(double* __restrict__ r, uint64_t* __restrict__ mu,
@@ -422,7 +481,7 @@ __global__ void __launch_bounds__(FIX_THREADS) split_fix_kernel(double* __restri
         if (threadIdx.x == 0) {
             uint64_t t = 0;
             for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = umax64(t, redu[w]);
-            mv[k + 1] = t;
+            mv[k + 1] = t ? pow2_bits(ceil_log2_pos(__longlong_as_double((long long)t))) : 0ull;
         }
         __syncthreads();                                  // mu[v][k + 1] and r^(k + 1) before the next level
     }
