@@ -171,13 +171,15 @@ int ozfft_get_stats(ozfft_plan_t plan, void* stream, ozfft_stats* out);
    previous call, and restarts the sums.  Slots: */
 enum {
     OZFFT_PROF_PREMUL = 0,      /* x~' = x (.) w and level-0 maxima */
-    OZFFT_PROF_SPLIT = 1,       /* the K split levels (K launches) */
+    OZFFT_PROF_SPLIT = 1,       /* the K split levels (two launches; K for the TS variant) */
     OZFFT_PROF_SCHEDULE = 2,    /* Alg. 8 flush schedule */
     OZFFT_PROF_NTT_FWD_COL = 3, /* forward NTT, column pass (two-pass lengths only) */
     OZFFT_PROF_NTT_FWD_ROW = 4, /* forward NTT, row pass */
     OZFFT_PROF_NTT_INV_ROW = 5, /* NTT-domain multiply-accumulate + inverse NTT row pass */
-    OZFFT_PROF_NTT_INV_COL = 6, /* inverse NTT, column pass (two-pass lengths only) */
-    OZFFT_PROF_CRT = 7,         /* Garner, rescale, accumulation, post-multiply */
+    OZFFT_PROF_NTT_INV_COL = 6, /* inverse NTT, column pass (two-pass lengths whose column pass
+                                   is not fused with the CRT) */
+    OZFFT_PROF_CRT = 7,         /* Garner, rescale, accumulation, post-multiply; with two primes
+                                   and m1 = 4..7 column stages also the inverse column pass, fused */
     OZFFT_PROF_SLOTS = 8
 };
 typedef struct {

@@ -31,8 +31,7 @@
 //                    memory.
 // One carry pass and an integer round-to-nearest-even at the end produce the
 // binary64 bit pattern.
-#include "oz_common.cuh"
-#include "oz_kernels.h"
+#include "ntt_impl.cuh"
 #include "ts_arith.cuh"
 
 namespace oz {
@@ -539,6 +538,7 @@ __global__ void __launch_bounds__(FAST_THREADS, 10) crt_fast_kernel(CrtArgs a)
         crt_reg_body<SD, UC>(a);
         return;
     }
+    if (a.fused) return;      // done by the fused column pass (colcrt_kernel)
     const SigOut so = sig_out<SD>(a, b);
     const int64_t j0 = (blockIdx.x % chunks) * (int64_t)CRT_CHUNK;
     const int64_t j1 = min(so.n, j0 + CRT_CHUNK);
@@ -761,6 +761,251 @@ cudaError_t crt_init()
         s_garner_ready = true;
     }
     return cudaSuccess;
+}
+
+// ------------------------------------- inverse column pass fused with the CRT
+// For the signals of crt_fast_kernel (two primes, monotone group scales, span
+// <= FAST_SPAN) the inverse NTT's column stages and the exact accumulation run
+// in one kernel, so the inverse-NTT residues never return to HBM.  A CTA owns
+// T adjacent columns x all 2^m1 rows (1024 positions j = row 2^m2 + col) of
+// one signal and walks the flush groups of both output parts, two per step:
+// it copies their four column tiles (two groups x two primes) into shared
+// memory with cp.async (the next step's copies in flight during this step's
+// arithmetic), runs the column rounds of the Gentleman-Sande inverse on all
+// four between the same barriers, and every thread adds the Garner integers
+// of its four positions to a 192-bit Horner sum.  The groups of a part's two convolutions (RR and II, or
+// IR and RI) are taken in one merged order of increasing scale, so one
+// accumulator per position serves the whole part (II with a minus sign); the
+// real part is rounded before the imaginary part starts.  Signals off that
+// path get the column pass only, stored back for the other CRT kernels.
+//
+// Shared-memory tiles are [row][T] with T pad words after every 16 rows
+// (T < 32): the column rounds then touch 32 distinct banks per warp.
+constexpr int FC_THREADS = 256;
+constexpr int FC_TILE = 1024;                         // positions per tile (per prime)
+constexpr int FC_E = FC_TILE / FC_THREADS;            // positions per thread
+constexpr int FC_STAGES = 2;
+
+template <int LOG_T>
+__host__ __device__ constexpr int fc_words() { return FC_TILE + (LOG_T < 5 ? (FC_TILE >> (LOG_T + 4)) << LOG_T : 0); }
+template <int LOG_T>
+__device__ __forceinline__ int fc_pad(int i) { return LOG_T < 5 ? i + ((i >> (LOG_T + 4)) << LOG_T) : i; }
+
+// one column round over NT tiles (PW words apart; even tiles prime 0, odd
+// tiles prime 1): 2^RL-point groups of stride H rows; element u of a group
+// sits at the group's base plus the compile-time offset u H T + T floor(u H /
+// 16) (a group never straddles a 16-row bucket except at multiples of H)
+template <int ML, int S0, int RL, int LOG_T, int NT>
+__device__ __forceinline__ void fc_round(uint32_t* st, const uint2* __restrict__ tw0, const uint2* __restrict__ tw1)
+{
+    constexpr int LOG_H = ML - S0 - RL, H = 1 << LOG_H, LOG_GPC = ML - RL, T = 1 << LOG_T, R = 1 << RL;
+    constexpr int GPT = T << LOG_GPC, PW = fc_words<LOG_T>();
+    for (int gid = threadIdx.x; gid < NT * GPT; gid += FC_THREADS) {
+        const int tile = gid / GPT, pr = tile & 1;
+        const int gg = gid - tile * GPT;
+        const int c = gg & (T - 1), grp = gg >> LOG_T;
+        const int blk = grp >> LOG_H;
+        const int l0 = (blk << (ML - S0)) + (grp & (H - 1));
+        uint32_t* base = st + tile * PW + (l0 << LOG_T) + c + (LOG_T < 5 ? ((l0 >> 4) << LOG_T) : 0);
+        uint32_t v[R];
+#pragma unroll
+        for (int u = 0; u < R; ++u) v[u] = base[u * H * T + (LOG_T < 5 ? ((u * H) >> 4) << LOG_T : 0)];
+        radix_group<true, RL>(v, pr ? tw1 : tw0, (1 << S0) + blk, pr ? P1 : P0);
+#pragma unroll
+        for (int u = 0; u < R; ++u) base[u * H * T + (LOG_T < 5 ? ((u * H) >> 4) << LOG_T : 0)] = v[u];
+    }
+}
+
+template <int ML, int LOG_T, int NT, int I>
+__device__ __forceinline__ void fc_rounds(uint32_t* st, const uint2* tw0, const uint2* tw1)
+{
+    if constexpr (I < Part<ML>::NR) {
+        constexpr int R_ = Part<ML>::NR - 1 - I;   // the inverse takes the rounds last to first
+        fc_round<ML, Part<ML>::start(R_), Part<ML>::size(R_), LOG_T, NT>(st, tw0, tw1);
+        __syncthreads();
+        fc_rounds<ML, LOG_T, NT, I + 1>(st, tw0, tw1);
+    }
+}
+
+struct FcTerm {
+    int64_t off;     // Z offset of the group's prime-0 vector
+    int16_t sh;      // left shift of the running sum before the term
+    int16_t neg;     // II: subtract
+};
+
+// TB flush groups per step (their 2 TB tiles transformed between the same
+// barriers)
+template <bool SD, int M1, int TB>
+__global__ void __launch_bounds__(FC_THREADS, 4) colcrt_kernel(CrtArgs a, int m2, const uint2* __restrict__ tw_all)
+{
+    constexpr int LOG_T = 10 - M1, T = 1 << LOG_T;
+    constexpr int PW = fc_words<LOG_T>(), SW = 2 * TB * PW;
+    static_assert((1 << M1) * T == FC_TILE && T >= 4, "column tile");
+    extern __shared__ __align__(16) uint32_t fc_sm[];
+    __shared__ FcTerm terms[4 * MAX_GROUPS];
+    __shared__ int s_pstart[3], s_fsh[2];
+    const int tiles = (1 << m2) >> LOG_T;
+    const int64_t b = blockIdx.x / tiles;
+    const int c0 = (int)(blockIdx.x % tiles) << LOG_T;
+    const bool fast = fast_path(a, b);
+    const Sched* sc = a.sched + b * 4;
+    const int smax = a.span[b * 3 + 1];
+    if (threadIdx.x == 0) {   // both parts' groups, each part merged in increasing scale
+        int n = 0;
+        for (int part = 0; part < 2; ++part) {
+            s_pstart[part] = n;
+            const Sched& A = sc[2 * part];
+            const Sched& B = sc[2 * part + 1];
+            int ia = A.ngroups - 1, ib = B.ngroups - 1, scur = 0;
+            bool first = true;
+            while (ia >= 0 || ib >= 0) {
+                const bool takeA = ib < 0 || (ia >= 0 && A.S[ia] <= B.S[ib]);
+                const int c = takeA ? 2 * part : 2 * part + 1, g = takeA ? ia-- : ib--;
+                const int S = takeA ? A.S[g] : B.S[g];
+                FcTerm t;
+                t.off = ((b * 4 + c) * a.G + g) * 2 * a.N;
+                t.sh = (int16_t)(first ? 0 : S - scur);
+                t.neg = (int16_t)(c == 1 && !a.merged);
+                terms[n++] = t;
+                scur = S;
+                first = false;
+            }
+            s_fsh[part] = first ? 0 : smax - scur;
+        }
+        s_pstart[2] = n;
+    }
+    __syncthreads();
+    const int nterms = s_pstart[2], nsteps = (nterms + TB - 1) / TB;
+    const uint2* tw0 = tw_all;
+    const uint2* tw1 = tw_all + a.N;
+    // chunk q of a tile pair: prime q / 256, row and 16-byte column group
+    auto issue = [&](int i) {
+#pragma unroll
+        for (int tb = 0; tb < TB; ++tb) {
+            const int ti = i * TB + tb;
+            if (ti < nterms) {
+                uint32_t* st = fc_sm + (i % FC_STAGES) * SW + tb * 2 * PW;
+                const uint32_t* zb = a.Z + terms[ti].off + c0;
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    const int q = threadIdx.x + k * FC_THREADS;
+                    const int pr = q >> 8, w = q & 255;
+                    const int row = w >> (LOG_T - 2), cw = (w & ((T >> 2) - 1)) << 2;
+                    const uint32_t* src = zb + pr * a.N + ((int64_t)row << m2) + cw;
+                    const uint32_t dst =
+                        (uint32_t)__cvta_generic_to_shared(st + pr * PW + fc_pad<LOG_T>((row << LOG_T) + cw));
+                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+                }
+            }
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+#pragma unroll
+    for (int i = 0; i < FC_STAGES - 1; ++i) issue(i);
+    Acc192 acc[FC_E];
+    double yr[FC_E];
+#pragma unroll
+    for (int e = 0; e < FC_E; ++e) {
+        acc[e] = Acc192{{0u, 0u, 0u, 0u, 0u, 0u}};
+        yr[e] = 0.0;
+    }
+    for (int i = 0; i < nsteps; ++i) {
+        issue(i + FC_STAGES - 1);
+        asm volatile("cp.async.wait_group %0;" ::"n"(FC_STAGES - 1) : "memory");
+        __syncthreads();                                  // step i's tiles are in shared memory
+        uint32_t* st = fc_sm + (i % FC_STAGES) * SW;
+        fc_rounds<M1, LOG_T, 2 * TB, 0>(st, tw0, tw1);    // ends with a barrier
+#pragma unroll
+        for (int tb = 0; tb < TB; ++tb) {
+            const int ti = i * TB + tb;
+            if (ti >= nterms) break;
+            const FcTerm t = terms[ti];
+            const uint32_t* sp = st + tb * 2 * PW;
+            if (fast) {
+#pragma unroll
+                for (int e = 0; e < FC_E; ++e) {
+                    const int p = fc_pad<LOG_T>(threadIdx.x + e * FC_THREADS);
+                    long long z = a.garner_u ? garner2u(sp[p], sp[PW + p]) : garner2(sp[p], sp[PW + p]);
+                    if (t.neg) z = -z;
+                    if (t.sh) acc192_shl(acc[e], t.sh);
+                    acc192_add64(acc[e], z);
+                }
+                if (ti + 1 == s_pstart[1]) {              // the real part is complete
+#pragma unroll
+                    for (int e = 0; e < FC_E; ++e) {
+                        acc192_shl(acc[e], s_fsh[0]);
+                        yr[e] = acc192_to_double(acc[e], -smax);
+                        acc[e] = Acc192{{0u, 0u, 0u, 0u, 0u, 0u}};
+                    }
+                }
+            } else {                                      // column pass only: back to Z for the other kernels
+                uint32_t* zb = const_cast<uint32_t*>(a.Z) + t.off + c0;   // the plan's Z buffer
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    const int q = threadIdx.x + k * FC_THREADS;
+                    const int pr = q >> 8, w = q & 255;
+                    const int row = w >> (LOG_T - 2), cw = (w & ((T >> 2) - 1)) << 2;
+                    const uint32_t* s4 = sp + pr * PW + fc_pad<LOG_T>((row << LOG_T) + cw);
+                    *reinterpret_cast<uint4*>(zb + pr * a.N + ((int64_t)row << m2) + cw) =
+                        make_uint4(s4[0], s4[1], s4[2], s4[3]);
+                }
+            }
+        }
+        __syncthreads();                                  // the stage is read before it is refilled
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    if (!fast) return;
+    double yi[FC_E];
+#pragma unroll
+    for (int e = 0; e < FC_E; ++e) {
+        if (nterms > s_pstart[1]) {
+            acc192_shl(acc[e], s_fsh[1]);
+            yi[e] = acc192_to_double(acc[e], -smax);
+        } else {
+            yi[e] = 0.0;
+        }
+    }
+    const SigOut so = sig_out<SD>(a, b);
+#pragma unroll
+    for (int e = 0; e < FC_E; ++e) {
+        const int idx = threadIdx.x + e * FC_THREADS;
+        const int64_t j = ((int64_t)(idx >> LOG_T) << m2) + c0 + (idx & (T - 1));
+        if (j < so.n) post_store(a, so, j, yr[e], yi[e]);
+    }
+}
+
+constexpr int FC_TB = 2;
+
+template <bool SD, int M1>
+static cudaError_t launch_colcrt_m(const CrtArgs& a, int m2, const uint2* tw, cudaStream_t s)
+{
+    constexpr int LOG_T = 10 - M1;
+    const size_t smem = (size_t)FC_STAGES * 2 * FC_TB * fc_words<LOG_T>() * sizeof(uint32_t);
+    cudaError_t e = cudaFuncSetAttribute(colcrt_kernel<SD, M1, FC_TB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    const int64_t grid = a.B * ((int64_t(1) << m2) >> LOG_T);
+    colcrt_kernel<SD, M1, FC_TB><<<(unsigned)grid, FC_THREADS, smem, s>>>(a, m2, tw);
+    return cudaGetLastError();
+}
+
+bool colcrt_supported(int P, int m1, int m2, bool merged)
+{
+    return P == 2 && !merged && m1 >= 4 && m1 <= 7 && m2 >= 10 - m1;
+}
+
+cudaError_t launch_colcrt(const CrtArgs& a, int m1, int m2, const uint2* tw, cudaStream_t s)
+{
+    cudaError_t e = crt_init();
+    if (e != cudaSuccess) return e;
+    const bool sd = a.sd != nullptr;
+    switch (m1) {
+    case 4: return sd ? launch_colcrt_m<true, 4>(a, m2, tw, s) : launch_colcrt_m<false, 4>(a, m2, tw, s);
+    case 5: return sd ? launch_colcrt_m<true, 5>(a, m2, tw, s) : launch_colcrt_m<false, 5>(a, m2, tw, s);
+    case 6: return sd ? launch_colcrt_m<true, 6>(a, m2, tw, s) : launch_colcrt_m<false, 6>(a, m2, tw, s);
+    case 7: return sd ? launch_colcrt_m<true, 7>(a, m2, tw, s) : launch_colcrt_m<false, 7>(a, m2, tw, s);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_crt_post(const CrtArgs& a, cudaStream_t s)

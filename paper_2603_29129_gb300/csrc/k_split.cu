@@ -389,8 +389,10 @@ __global__ void __launch_bounds__(SPLIT_THREADS) split_spec_kernel(const double*
     int cmax[KM];
 #pragma unroll
     for (int k = 0; k < KM; ++k) cmax[k] = -2000;
+    uint64_t rb_next = j0 + threadIdx.x < j1 ? rv[j0 + threadIdx.x] : 0ull;
     for (int64_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
-        const uint64_t rb = rv[j];
+        const uint64_t rb = rb_next;   // the next element's load in flight during this one's levels
+        if (j + blockDim.x < j1) rb_next = rv[j + blockDim.x];
         bool neg = (rb >> 63) != 0;
         const int Eb = (int)((rb >> 52) & 0x7ff);
         uint64_t a = rb & ((1ull << 52) - 1);

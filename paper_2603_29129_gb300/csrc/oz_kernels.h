@@ -111,11 +111,16 @@ struct CrtArgs {
     const IoPtrs* io;      // device-held output pointer, or null
     int merged;            // merged schedules: the MAC already applied the sign of II
     int garner_u;          // |z| < p0 p1 / 2 - p0 for every value: two-prime CRT without centering z0
+    int fused;             // colcrt_kernel already produced the Horner-path signals' outputs
 };
 int crt_launches();        // kernels per launch_crt_post
 cudaError_t crt_init();    // uploads the Garner constants (once; call before any stream capture)
 cudaError_t launch_crt_post(const CrtArgs& a, cudaStream_t s);
 cudaError_t launch_crt_ts(const CrtArgs& a, cudaStream_t s);   // TS variant (two primes)
+// the inverse NTT's column pass (stages 0..m1-1 of Z, table tw) fused with the
+// CRT for the Horner-path signals; the others get the column pass only
+bool colcrt_supported(int P, int m1, int m2, bool merged);
+cudaError_t launch_colcrt(const CrtArgs& a, int m1, int m2, const uint2* tw, cudaStream_t s);
 
 // k_peak.cu: butterflies per second with every operand in registers
 cudaError_t measure_butterfly_rate(int inverse, int blocks, int iters, uint32_t* scratch, double* rate,

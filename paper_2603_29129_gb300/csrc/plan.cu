@@ -736,14 +736,20 @@ static int run_plan_range(ozfft_plan_s* p, const void* in, void* out, cudaStream
         const MacSrc mac{X + b0 * 2 * K * P * N, Ym + b0 * p->ym_stride, p->ym_stride};
         CUDA_TRY(launch_ntt_inv_row(gi, p->Z, p->twinv, mac, s));
         mark(p, OZFFT_PROF_NTT_INV_ROW, s);
-        if (gi.m1 > 0) {
-            CUDA_TRY(launch_ntt_inv_col(gi, p->Z, p->twinv, s));
-            mark(p, OZFFT_PROF_NTT_INV_COL, s);
-        }
         CrtArgs ca{p->Z, sched + b0 * 4, span + b0 * 3, p->chirp,
                    sd ? (double2*)out : (double2*)out + b0 * p->n, p->n, N, nb,
                    P, p->G, p->direction, p->status, sd ? sd + b0 : nullptr, p->io_ref, p->merge,
-                   p->garner_u};
+                   p->garner_u, 0};
+        // the column pass fused with the CRT (Z stays on chip), unless the
+        // stage dumps need Z or the schedule is one the fused kernel does not take
+        const bool fuse = !p->ts && !p->debug && gi.m1 > 0 && colcrt_supported(P, gi.m1, gi.m2, p->merge);
+        if (fuse) {
+            CUDA_TRY(launch_colcrt(ca, gi.m1, gi.m2, p->twinv, s));
+            ca.fused = 1;
+        } else if (gi.m1 > 0) {
+            CUDA_TRY(launch_ntt_inv_col(gi, p->Z, p->twinv, s));
+            mark(p, OZFFT_PROF_NTT_INV_COL, s);
+        }
         if (p->ts) CUDA_TRY(launch_crt_ts(ca, s));
         else CUDA_TRY(launch_crt_post(ca, s));
         if (b0 + p->chunk < B) mark(p, OZFFT_PROF_CRT, s);
