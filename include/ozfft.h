@@ -179,7 +179,7 @@ enum {
     OZFFT_PROF_NTT_INV_COL = 6, /* inverse NTT, column pass (two-pass lengths whose column pass
                                    is not fused with the CRT) */
     OZFFT_PROF_CRT = 7,         /* Garner, rescale, accumulation, post-multiply; with two primes
-                                   and m1 = 4..7 column stages also the inverse column pass, fused */
+                                   and m1 = 4..8 column stages also the inverse column pass, fused */
     OZFFT_PROF_SLOTS = 8
 };
 typedef struct {

@@ -777,7 +777,9 @@ cudaError_t crt_init()
 // IR and RI) are taken in one merged order of increasing scale, so one
 // accumulator per position serves the whole part (II with a minus sign); the
 // real part is rounded before the imaginary part starts.  Signals off that
-// path get the column pass only, stored back for the other CRT kernels.
+// path get the column pass only, stored back for the other CRT kernels.  In
+// a merged schedule a part's groups fill the slots of its two convolutions,
+// each slot in scale order, with II's sign already applied by the MAC.
 //
 // Shared-memory tiles are [row][T] with T pad words after every 16 rows
 // (T < 32): the column rounds then touch 32 distinct banks per warp.
@@ -989,9 +991,9 @@ static cudaError_t launch_colcrt_m(const CrtArgs& a, int m2, const uint2* tw, cu
     return cudaGetLastError();
 }
 
-bool colcrt_supported(int P, int m1, int m2, bool merged)
+bool colcrt_supported(int P, int m1, int m2, bool)
 {
-    return P == 2 && !merged && m1 >= 4 && m1 <= 7 && m2 >= 10 - m1;
+    return P == 2 && m1 >= 4 && m1 <= 8 && m2 >= 10 - m1;
 }
 
 cudaError_t launch_colcrt(const CrtArgs& a, int m1, int m2, const uint2* tw, cudaStream_t s)
@@ -1004,6 +1006,7 @@ cudaError_t launch_colcrt(const CrtArgs& a, int m1, int m2, const uint2* tw, cud
     case 5: return sd ? launch_colcrt_m<true, 5>(a, m2, tw, s) : launch_colcrt_m<false, 5>(a, m2, tw, s);
     case 6: return sd ? launch_colcrt_m<true, 6>(a, m2, tw, s) : launch_colcrt_m<false, 6>(a, m2, tw, s);
     case 7: return sd ? launch_colcrt_m<true, 7>(a, m2, tw, s) : launch_colcrt_m<false, 7>(a, m2, tw, s);
+    case 8: return sd ? launch_colcrt_m<true, 8>(a, m2, tw, s) : launch_colcrt_m<false, 8>(a, m2, tw, s);
     default: return cudaErrorInvalidValue;
     }
 }

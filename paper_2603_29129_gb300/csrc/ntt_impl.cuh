@@ -356,8 +356,77 @@ __device__ __forceinline__ uint32_t mac_load1(const MacVec& m, const MacSrc& mac
     return m.merged ? mac_sum1<true>(m, mac, j) : mac_sum1<false>(m, mac, j);
 }
 
+// middle rounds I = 1 .. NR - 2 of the inverse row pass
+template <int ML, int I>
+__device__ __forceinline__ void inv_middle_rounds(uint32_t* sm, const PassArgs& a)
+{
+    if constexpr (I < Part<ML>::NR - 1) {
+        constexpr int R_ = Part<ML>::NR - 1 - I;
+        row_round<true, ML, Part<ML>::start(R_), Part<ML>::size(R_)>(sm, a);
+        __syncthreads();
+        inv_middle_rounds<ML, I + 1>(sm, a);
+    }
+}
+
+// The inverse row pass of a full tile of ROWS rows of one vector with the MAC
+// in registers: the first round's groups are 2^RL contiguous residues, so each
+// thread forms their Alg. 8 sums straight from X and Ym; the last round (the
+// stages of stride H = 2^(ML - RL)) stores straight to global memory, with
+// consecutive lanes on consecutive addresses.  Two shared-memory passes and two
+// barriers fewer than loading, transforming and storing separately.
+template <int ML, int ROWS>
+__device__ __forceinline__ void row_inv_mac(uint32_t* sm, uint32_t* __restrict__ out, const uint2* __restrict__ tw_all,
+                                            int pi, int64_t tw_stride, int rbase, const MacVec& mv, const MacSrc& mac,
+                                            int64_t j0)
+{
+    using PT = Part<ML>;
+    const uint2* tw = tw_all + (int64_t)pi * tw_stride;
+    const uint32_t p = prime_of(pi);
+    {
+        constexpr int R_ = PT::NR - 1, S0 = PT::start(R_), RL = PT::size(R_), R = 1 << RL, LOG_GPC = ML - RL;
+        static_assert(S0 + RL == ML && RL >= 2 && RL <= 4, "first inverse round: contiguous groups");
+        constexpr int NG = ROWS << LOG_GPC;
+#pragma unroll 1
+        for (int gid = threadIdx.x; gid < NG; gid += NTT_THREADS) {
+            const int grp = gid & ((1 << LOG_GPC) - 1), c = gid >> LOG_GPC;
+            const int base = (c << ML) + (grp << RL);
+            uint32_t v[R];
+#pragma unroll
+            for (int q = 0; q < R; q += 4) {
+                const uint4 t = mac_load4(mv, mac, j0 + base + q);
+                v[q] = t.x; v[q + 1] = t.y; v[q + 2] = t.z; v[q + 3] = t.w;
+            }
+            radix_group<true, RL>(v, tw, ((rbase + c) << S0) + grp, p);
+            uint32_t* smp = sm + pad_idx(base);
+#pragma unroll
+            for (int u = 0; u < R; ++u) smp[u] = v[u];
+        }
+    }
+    __syncthreads();
+    const PassArgs a{ROWS, rbase, 1, tw_all, tw_stride, pi, 1, false};
+    inv_middle_rounds<ML, 1>(sm, a);
+    {
+        constexpr int RL = PT::size(0), R = 1 << RL, LOG_H = ML - RL, H = 1 << LOG_H;
+        constexpr int NG = ROWS << LOG_H;
+#pragma unroll 1
+        for (int gid = threadIdx.x; gid < NG; gid += NTT_THREADS) {
+            const int l0 = gid & (H - 1), c = gid >> LOG_H;
+            const int base = (c << ML) + l0;
+            uint32_t v[R];
+            const uint32_t* smp = sm + pad_idx(base);
+#pragma unroll
+            for (int u = 0; u < R; ++u) v[u] = smp[u * H + (u * H) / 32];
+            radix_group<true, RL>(v, tw, rbase + c, p);
+#pragma unroll
+            for (int u = 0; u < R; ++u) out[base + u * H] = v[u];
+        }
+    }
+}
+
+// 10 CTAs per SM (48 registers); the inverse pass with the MAC in registers
+// needs 56 (9 CTAs) to stay free of spills
 template <bool INV, bool MAC, int M2>
-__global__ void __launch_bounds__(NTT_THREADS, 10) ntt_row_kernel(NttGeom g, uint32_t* __restrict__ data,
+__global__ void __launch_bounds__(NTT_THREADS, (INV && MAC) ? 9 : 10) ntt_row_kernel(NttGeom g, uint32_t* __restrict__ data,
                                                                  const uint2* __restrict__ tw_all, MacSrc mac)
 {
     extern __shared__ uint32_t sm[];
@@ -375,6 +444,14 @@ __global__ void __launch_bounds__(NTT_THREADS, 10) ntt_row_kernel(NttGeom g, uin
         if (INV ? !inv_live(g, vec) : !fwd_live(g, vec)) return;
         const int pi = (int)(vec % (unsigned)g.P);
         const int64_t j0 = gbase - ((int64_t)vec << g.lgN);   // offset inside the vector
+        if constexpr (INV && MAC && Part<M2>::NR >= 2 && M2 <= TILE_LOG) {
+            if (rows == RPC) {
+                const MacVec mv = mac_decode(g, vec, mac.ym_stride);
+                const int rin0 = (int)(row0 & ((int64_t(1) << lg_rpv) - 1));
+                row_inv_mac<M2, RPC>(sm, data + gbase, tw_all, pi, g.N, (1 << g.m1) + rin0, mv, mac, j0);
+                return;
+            }
+        }
         if (nel >= 4) {
             if (MAC) {
                 const MacVec mv = mac_decode(g, vec, mac.ym_stride);
