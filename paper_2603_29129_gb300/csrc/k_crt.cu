@@ -773,7 +773,10 @@ cudaError_t crt_init()
 // memory with cp.async (the next step's copies in flight during this step's
 // arithmetic), runs the column rounds of the Gentleman-Sande inverse on all
 // four between the same barriers, and every thread adds the Garner integers
-// of its four positions to a 192-bit Horner sum.  The groups of a part's two convolutions (RR and II, or
+// of its four positions to a 192-bit Horner sum.  With up to six column
+// stages the last two run in registers: each thread transforms the four
+// positions it accumulates (one column group, both primes) and feeds them to
+// Garner directly, one shared-memory pass and one barrier fewer per step.  The groups of a part's two convolutions (RR and II, or
 // IR and RI) are taken in one merged order of increasing scale, so one
 // accumulator per position serves the whole part (II with a minus sign); the
 // real part is rounded before the imaginary part starts.  Signals off that
@@ -829,6 +832,16 @@ __device__ __forceinline__ void fc_rounds(uint32_t* st, const uint2* tw0, const 
     }
 }
 
+// the column rounds for stages 2 .. ML-1 in one round (ML <= 6); stages 0 and
+// 1 then run in registers in colcrt_kernel
+template <int ML, int LOG_T, int NT>
+__device__ __forceinline__ void fc_rounds_hi(uint32_t* st, const uint2* tw0, const uint2* tw1)
+{
+    static_assert(ML - 2 >= 1 && ML - 2 <= 4, "one shared-memory round");
+    fc_round<ML, 2, ML - 2, LOG_T, NT>(st, tw0, tw1);
+    __syncthreads();
+}
+
 struct FcTerm {
     int64_t off;     // Z offset of the group's prime-0 vector
     int16_t sh;      // left shift of the running sum before the term
@@ -878,6 +891,14 @@ __global__ void __launch_bounds__(FC_THREADS, 4) colcrt_kernel(CrtArgs a, int m2
     }
     __syncthreads();
     const int nterms = s_pstart[2], nsteps = (nterms + TB - 1) / TB;
+    // up to 6 column stages: stages 2.. in shared memory, then each thread runs
+    // stages 1 and 0 of one column group (four positions, rows fl0 + u HB of
+    // column fcl) for both primes in registers and accumulates those positions;
+    // otherwise all rounds in shared memory, positions threadIdx.x + e FC_THREADS
+    constexpr bool REG01 = M1 <= 6;
+    constexpr int HB = 1 << (M1 - 2);                     // stride of stages 0 and 1 in rows
+    static_assert(!REG01 || (T * HB == FC_THREADS && FC_E == 4), "one column group of four positions per thread");
+    const int fcl = threadIdx.x & (T - 1), fl0 = threadIdx.x >> LOG_T;
     const uint2* tw0 = tw_all;
     const uint2* tw1 = tw_all + a.N;
     // chunk q of a tile pair: prime q / 256, row and 16-byte column group
@@ -905,29 +926,48 @@ __global__ void __launch_bounds__(FC_THREADS, 4) colcrt_kernel(CrtArgs a, int m2
 #pragma unroll
     for (int i = 0; i < FC_STAGES - 1; ++i) issue(i);
     Acc192 acc[FC_E];
-    double yr[FC_E];
+    __shared__ double s_yr[FC_E][FC_THREADS];           // the real parts, kept out of the registers
 #pragma unroll
     for (int e = 0; e < FC_E; ++e) {
         acc[e] = Acc192{{0u, 0u, 0u, 0u, 0u, 0u}};
-        yr[e] = 0.0;
+        s_yr[e][threadIdx.x] = 0.0;
     }
     for (int i = 0; i < nsteps; ++i) {
         issue(i + FC_STAGES - 1);
         asm volatile("cp.async.wait_group %0;" ::"n"(FC_STAGES - 1) : "memory");
         __syncthreads();                                  // step i's tiles are in shared memory
         uint32_t* st = fc_sm + (i % FC_STAGES) * SW;
-        fc_rounds<M1, LOG_T, 2 * TB, 0>(st, tw0, tw1);    // ends with a barrier
+        if constexpr (REG01) fc_rounds_hi<M1, LOG_T, 2 * TB>(st, tw0, tw1);   // ends with a barrier
+        else fc_rounds<M1, LOG_T, 2 * TB, 0>(st, tw0, tw1);
 #pragma unroll
         for (int tb = 0; tb < TB; ++tb) {
             const int ti = i * TB + tb;
             if (ti >= nterms) break;
             const FcTerm t = terms[ti];
             const uint32_t* sp = st + tb * 2 * PW;
-            if (fast) {
+            uint32_t v0[FC_E], v1[FC_E];                  // the thread's positions, prime 0 and prime 1
+            if constexpr (REG01) {
+                const uint32_t* gp = sp + (fl0 << LOG_T) + fcl + (LOG_T < 5 ? ((fl0 >> 4) << LOG_T) : 0);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int o = u * HB * T + (LOG_T < 5 ? ((u * HB) >> 4) << LOG_T : 0);
+                    v0[u] = gp[o];
+                    v1[u] = gp[PW + o];
+                }
+                radix_group<true, 2>(v0, tw0, 1, P0);     // stages 1 and 0 (table entries 1..3)
+                radix_group<true, 2>(v1, tw1, 1, P1);
+            } else {
 #pragma unroll
                 for (int e = 0; e < FC_E; ++e) {
                     const int p = fc_pad<LOG_T>(threadIdx.x + e * FC_THREADS);
-                    long long z = a.garner_u ? garner2u(sp[p], sp[PW + p]) : garner2(sp[p], sp[PW + p]);
+                    v0[e] = sp[p];
+                    v1[e] = sp[PW + p];
+                }
+            }
+            if (fast) {
+#pragma unroll
+                for (int e = 0; e < FC_E; ++e) {
+                    long long z = a.garner_u ? garner2u(v0[e], v1[e]) : garner2(v0[e], v1[e]);
                     if (t.neg) z = -z;
                     if (t.sh) acc192_shl(acc[e], t.sh);
                     acc192_add64(acc[e], z);
@@ -936,20 +976,19 @@ __global__ void __launch_bounds__(FC_THREADS, 4) colcrt_kernel(CrtArgs a, int m2
 #pragma unroll
                     for (int e = 0; e < FC_E; ++e) {
                         acc192_shl(acc[e], s_fsh[0]);
-                        yr[e] = acc192_to_double(acc[e], -smax);
+                        s_yr[e][threadIdx.x] = acc192_to_double(acc[e], -smax);
                         acc[e] = Acc192{{0u, 0u, 0u, 0u, 0u, 0u}};
                     }
                 }
             } else {                                      // column pass only: back to Z for the other kernels
                 uint32_t* zb = const_cast<uint32_t*>(a.Z) + t.off + c0;   // the plan's Z buffer
 #pragma unroll
-                for (int k = 0; k < 2; ++k) {
-                    const int q = threadIdx.x + k * FC_THREADS;
-                    const int pr = q >> 8, w = q & 255;
-                    const int row = w >> (LOG_T - 2), cw = (w & ((T >> 2) - 1)) << 2;
-                    const uint32_t* s4 = sp + pr * PW + fc_pad<LOG_T>((row << LOG_T) + cw);
-                    *reinterpret_cast<uint4*>(zb + pr * a.N + ((int64_t)row << m2) + cw) =
-                        make_uint4(s4[0], s4[1], s4[2], s4[3]);
+                for (int e = 0; e < FC_E; ++e) {
+                    const int64_t o = REG01 ? ((int64_t)(fl0 + e * HB) << m2) + fcl
+                                            : ((int64_t)((threadIdx.x + e * FC_THREADS) >> LOG_T) << m2) +
+                                                  ((threadIdx.x + e * FC_THREADS) & (T - 1));
+                    zb[o] = v0[e];
+                    zb[a.N + o] = v1[e];
                 }
             }
         }
@@ -971,8 +1010,9 @@ __global__ void __launch_bounds__(FC_THREADS, 4) colcrt_kernel(CrtArgs a, int m2
 #pragma unroll
     for (int e = 0; e < FC_E; ++e) {
         const int idx = threadIdx.x + e * FC_THREADS;
-        const int64_t j = ((int64_t)(idx >> LOG_T) << m2) + c0 + (idx & (T - 1));
-        if (j < so.n) post_store(a, so, j, yr[e], yi[e]);
+        const int64_t j = REG01 ? ((int64_t)(fl0 + e * HB) << m2) + c0 + fcl
+                                : ((int64_t)(idx >> LOG_T) << m2) + c0 + (idx & (T - 1));
+        if (j < so.n) post_store(a, so, j, s_yr[e][threadIdx.x], yi[e]);
     }
 }
 
