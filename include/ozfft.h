@@ -139,8 +139,10 @@ int ozfft_execute(ozfft_plan_t plan, const void* in, void* out, void* stream);
    copies the result to `out`, and returns after the stream has synchronized.
    Batches of 8 or more signals (plain plans) run as a pipeline of four parts:
    the copies in and out of neighbouring parts, on two streams of the plan,
-   overlap the computation of a part on `stream`.  Pinned (page-locked) host
-   memory gives the fastest copies and the overlap. */
+   overlap the computation of a part on `stream`; from 28 signals on, the
+   first and last parts are small (1/14 of the batch each), since only their
+   copies are not hidden.  Pinned (page-locked) host memory gives the fastest
+   copies and the overlap. */
 int ozfft_execute_host(ozfft_plan_t plan, const void* in, void* out, void* stream);
 
 /* Synchronize `stream`, return the data-dependent status recorded by the

@@ -1093,10 +1093,19 @@ int ozfft_execute_host(ozfft_plan_t p, const void* in, void* out, void* stream)
     }
     CUDA_TRY(cudaEventRecord(p->ev_go, s));             // earlier work on s may still use the staging
     CUDA_TRY(cudaStreamWaitEvent(p->cs_in, p->ev_go, 0));
-    const int64_t per = (p->B + parts - 1) / parts;
+    // only the first part's copy in and the last part's copy out are not hidden
+    // behind computation, so those parts are small (weights 1, 6, 6, 1 of the
+    // batch; equal parts for small batches)
+    static constexpr int W[ozfft_plan_s::HOST_PARTS] = {1, 6, 6, 1};
+    int64_t cut[ozfft_plan_s::HOST_PARTS + 1] = {0};
+    const int wsum = W[0] + W[1] + W[2] + W[3];
+    for (int i = 0, acc = 0; i < parts; ++i) {
+        acc += W[i];
+        cut[i + 1] = p->B >= 2 * wsum ? p->B * acc / wsum : std::min<int64_t>(p->B, (i + 1) * ((p->B + parts - 1) / parts));
+    }
     for (int i = 0; i < parts; ++i) {
-        const int64_t b0 = i * per, nb = std::min<int64_t>(per, p->B - b0);
-        if (nb <= 0) break;
+        const int64_t b0 = cut[i], nb = cut[i + 1] - cut[i];
+        if (nb <= 0) continue;
         const size_t off = (size_t)(b0 * p->n), cnt = (size_t)(nb * p->n);
         CUDA_TRY(cudaMemcpyAsync(p->stage_in + off, (const double2*)in + off, sizeof(double2) * cnt,
                                  cudaMemcpyHostToDevice, p->cs_in));

@@ -275,10 +275,11 @@ def test_in_place_and_host_buffers(oz):
     assert np.array_equal(out.view(np.uint64), ref.view(np.uint64))
 
 
-@pytest.mark.parametrize("B", [8, 13])
+@pytest.mark.parametrize("B", [8, 13, 28, 45])
 def test_host_buffer_pipeline(oz, B):
     """Batches of 8 or more signals run the host-buffer path as a pipeline of parts
-    (copies overlapping computation): same bits as the device-buffer execution."""
+    (copies overlapping computation; from 28 signals the first and last parts are
+    small): same bits as the device-buffer execution."""
     n = 3000
     x = synth.complex_signal("phi", n, 16, batch=B, phi=1.0)
     ref, plan = run_gpu(oz, x)
