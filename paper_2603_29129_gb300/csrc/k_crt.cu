@@ -1040,13 +1040,13 @@ cudaError_t launch_colcrt(const CrtArgs& a, int m1, int m2, const uint2* tw, cud
 {
     cudaError_t e = crt_init();
     if (e != cudaSuccess) return e;
-    const bool sd = a.sd != nullptr;
+    if (a.sd) return cudaErrorInvalidValue;   // plans over uneven lengths keep the unfused kernels
     switch (m1) {
-    case 4: return sd ? launch_colcrt_m<true, 4>(a, m2, tw, s) : launch_colcrt_m<false, 4>(a, m2, tw, s);
-    case 5: return sd ? launch_colcrt_m<true, 5>(a, m2, tw, s) : launch_colcrt_m<false, 5>(a, m2, tw, s);
-    case 6: return sd ? launch_colcrt_m<true, 6>(a, m2, tw, s) : launch_colcrt_m<false, 6>(a, m2, tw, s);
-    case 7: return sd ? launch_colcrt_m<true, 7>(a, m2, tw, s) : launch_colcrt_m<false, 7>(a, m2, tw, s);
-    case 8: return sd ? launch_colcrt_m<true, 8>(a, m2, tw, s) : launch_colcrt_m<false, 8>(a, m2, tw, s);
+    case 4: return launch_colcrt_m<false, 4>(a, m2, tw, s);
+    case 5: return launch_colcrt_m<false, 5>(a, m2, tw, s);
+    case 6: return launch_colcrt_m<false, 6>(a, m2, tw, s);
+    case 7: return launch_colcrt_m<false, 7>(a, m2, tw, s);
+    case 8: return launch_colcrt_m<false, 8>(a, m2, tw, s);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -445,7 +445,7 @@ __global__ void __launch_bounds__(NTT_THREADS, (INV && MAC) ? 9 : 10) ntt_row_ke
         const int pi = (int)(vec % (unsigned)g.P);
         const int64_t j0 = gbase - ((int64_t)vec << g.lgN);   // offset inside the vector
         if constexpr (INV && MAC && Part<M2>::NR >= 2 && M2 <= TILE_LOG) {
-            if (rows == RPC) {
+            if (rows == RPC && g.mac_reg) {   // groups of several products keep the coalesced staged loads
                 const MacVec mv = mac_decode(g, vec, mac.ym_stride);
                 const int rin0 = (int)(row0 & ((int64_t(1) << lg_rpv) - 1));
                 row_inv_mac<M2, RPC>(sm, data + gbase, tw_all, pi, g.N, (1 << g.m1) + rin0, mv, mac, j0);

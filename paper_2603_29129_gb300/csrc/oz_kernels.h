@@ -40,6 +40,8 @@ struct NttGeom {
     const int32_t* kcnt;   // [B][2] live split levels of x~' (forward skip test)
     const Sched* sched;    // [B][4] flush schedules (inverse skip test and MAC)
     int merged;            // schedules merge the two convolutions of each output part
+    int mac_reg;           // L = 1 (one product per group): the inverse row pass forms the
+                           // Alg. 8 products in registers instead of staging them
     const CUtensorMap* tmap;   // column pass by tensor memory access: [vectors][2^m1][2^m2] map of the
                                // buffer (null: per-thread loads); host memory, passed by value
     int64_t vec0;          // index of the launch's first vector in that map
@@ -118,7 +120,8 @@ cudaError_t crt_init();    // uploads the Garner constants (once; call before an
 cudaError_t launch_crt_post(const CrtArgs& a, cudaStream_t s);
 cudaError_t launch_crt_ts(const CrtArgs& a, cudaStream_t s);   // TS variant (two primes)
 // the inverse NTT's column pass (stages 0..m1-1 of Z, table tw) fused with the
-// CRT for the Horner-path signals; the others get the column pass only
+// CRT for the Horner-path signals; the others get the column pass only (plain
+// plans: a.sd must be null)
 bool colcrt_supported(int P, int m1, int m2, bool merged);
 cudaError_t launch_colcrt(const CrtArgs& a, int m1, int m2, const uint2* tw, cudaStream_t s);
 

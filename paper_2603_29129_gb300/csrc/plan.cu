@@ -470,6 +470,7 @@ static int plan_build(ozfft_plan_s* p)
     p->geom_fwd.K = K;
     p->geom_fwd.G = p->G;
     p->geom_fwd.merged = p->merge;
+    p->geom_fwd.mac_reg = p->L == 1;
     p->geom_inv = p->geom_fwd;
 
     // chirp tables, then w~* split + forward NTTs (§4.5: precomputed once); the
@@ -741,8 +742,10 @@ static int run_plan_range(ozfft_plan_s* p, const void* in, void* out, cudaStream
                    P, p->G, p->direction, p->status, sd ? sd + b0 : nullptr, p->io_ref, p->merge,
                    p->garner_u, 0};
         // the column pass fused with the CRT (Z stays on chip), unless the
-        // stage dumps need Z or the schedule is one the fused kernel does not take
-        const bool fuse = !p->ts && !p->debug && gi.m1 > 0 && colcrt_supported(P, gi.m1, gi.m2, p->merge);
+        // stage dumps need Z, the schedule is one the fused kernel does not take,
+        // or the plan is a length class of uneven lengths (measured slower there:
+        // 4096 log-uniform lengths, 188 against 198-205 ms per execution at L = 3)
+        const bool fuse = !p->ts && !p->debug && !sd && gi.m1 > 0 && colcrt_supported(P, gi.m1, gi.m2, p->merge);
         if (fuse) {
             CUDA_TRY(launch_colcrt(ca, gi.m1, gi.m2, p->twinv, s));
             ca.fused = 1;
@@ -1400,6 +1403,7 @@ static int noalloc_setup(NoallocState& st, int dev, int64_t n, int64_t N, int al
     p.geom_fwd.P = P;
     p.geom_fwd.K = K;
     p.geom_fwd.G = p.G;
+    p.geom_fwd.mac_reg = 1;   // L = 1
     p.geom_inv = p.geom_fwd;
     NttGeom gw = p.geom_fwd;
     gw.nvec = (int64_t)2 * K * P;
