@@ -40,8 +40,8 @@ struct NttGeom {
     const int32_t* kcnt;   // [B][2] live split levels of x~' (forward skip test)
     const Sched* sched;    // [B][4] flush schedules (inverse skip test and MAC)
     int merged;            // schedules merge the two convolutions of each output part
-    int mac_reg;           // L = 1 (one product per group): the inverse row pass forms the
-                           // Alg. 8 products in registers instead of staging them
+    int mac_reg;           // L = 1 or merged schedules: the inverse row pass forms the Alg. 8
+                           // sums in registers instead of staging them in shared memory
     const CUtensorMap* tmap;   // column pass by tensor memory access: [vectors][2^m1][2^m2] map of the
                                // buffer (null: per-thread loads); host memory, passed by value
     int64_t vec0;          // index of the launch's first vector in that map

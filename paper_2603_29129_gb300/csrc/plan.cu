@@ -470,7 +470,7 @@ static int plan_build(ozfft_plan_s* p)
     p->geom_fwd.K = K;
     p->geom_fwd.G = p->G;
     p->geom_fwd.merged = p->merge;
-    p->geom_fwd.mac_reg = p->L == 1;
+    p->geom_fwd.mac_reg = p->L == 1 || p->merge;   // measured: staged loads win only for unmerged L > 1
     p->geom_inv = p->geom_fwd;
 
     // chirp tables, then w~* split + forward NTTs (§4.5: precomputed once); the
