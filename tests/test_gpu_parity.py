@@ -180,6 +180,36 @@ def test_split_exponent_guess_redone(oz):
         assert np.array_equal(y[b].view(np.uint64), yo.view(np.uint64)), b
 
 
+@pytest.mark.parametrize("n,row_log", [(1 << 16, 0), (1 << 16, 11), (1 << 17, 10)])
+def test_gap_spans_in_two_pass_sizes(oz, n, row_log):
+    """Gap-producing inputs at two-pass lengths (4, 5 and 7 column stages), so that the
+    inverse column pass fused with the CRT meets signals off its Horner path (column pass
+    only, written back for the limb kernels) next to signals on it."""
+    xs = synth.complex_signal("uniform", n, 18, batch=4)
+    xs[1, 1:] *= 1e-12
+    xs[1, 0] = 1.0 - 0.5j
+    xs[2, 1:] *= 1e-100
+    xs[2, 0] = 1.0
+    y, plan = run_gpu(oz, xs, row_log=row_log) if row_log else run_gpu(oz, xs)
+    assert plan.status() == oz.OK
+    for b in range(4):
+        yo, _ = oracle_vs(xs[b], plan)
+        assert np.array_equal(y[b].view(np.uint64), yo.view(np.uint64)), (row_log, b)
+
+
+def test_fused_column_stage_counts_agree(oz):
+    """The fused column pass + CRT with 6, 7 and 8 column stages (row passes of 12, 11,
+    10 stages) and the unfused kernels (stage dumps on) give the same bits."""
+    n, B = 1 << 18, 2
+    x = torch.from_numpy(synth.complex_signal("phi", n, 19, batch=B, phi=4.0)).cuda()
+    ref = oz.Plan(n, B, debug=True).execute(x).cpu().numpy()
+    for m2 in (12, 11, 10):
+        p = oz.Plan(n, B, row_log=m2)
+        assert p.stats()["row_log_inv"] == m2
+        y = p.execute(x).cpu().numpy()
+        assert np.array_equal(y.view(np.uint64), ref.view(np.uint64)), m2
+
+
 def test_batch_mixed_distributions(oz):
     n = 2048
     xs = np.concatenate([synth.complex_signal(k, n, 7, phi=4.0) for k in
