@@ -210,6 +210,29 @@ def test_fused_column_stage_counts_agree(oz):
         assert np.array_equal(y.view(np.uint64), ref.view(np.uint64)), m2
 
 
+def test_premultiply_tiny_subnormal_and_signed_zero_parts(oz):
+    """x~' = x w (the fma form of the complex product) for parts down to the subnormal
+    range, signed zeros and exact zeros, against the oracle bit for bit, and the whole
+    transform."""
+    n = 1000
+    rng = np.random.default_rng(20)
+    mag = 10.0 ** rng.uniform(-322, -290, size=(2, n, 2))
+    sgn = rng.choice([-1.0, 1.0], size=(2, n, 2))
+    parts = mag * sgn
+    parts[0, ::7, 0] = 0.0
+    parts[0, ::11, 1] = -0.0
+    parts[1, :5] = [[1e-300, -3e-310], [5e-324, -5e-324], [2.2250738585072014e-308, 0.0], [-0.0, 1e-320], [0.0, -0.0]]
+    xs = np.empty((2, n), dtype=np.complex128)
+    xs.real = parts[..., 0]
+    xs.imag = parts[..., 1]
+    y, plan = run_gpu(oz, xs, debug=True)
+    assert plan.status() == oz.OK
+    for b in range(2):
+        yo, info = oracle_vs(xs[b], plan, trace={"xprime"})
+        assert np.array_equal(plan.dump(oz.DUMP_XPRIME, b).view(np.uint64), info["xprime"].view(np.uint64)), b
+        assert np.array_equal(y[b].view(np.uint64), yo.view(np.uint64)), b
+
+
 def test_batch_mixed_distributions(oz):
     n = 2048
     xs = np.concatenate([synth.complex_signal(k, n, 7, phi=4.0) for k in
