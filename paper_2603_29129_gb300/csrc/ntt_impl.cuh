@@ -136,9 +136,20 @@ template <bool INV, int ML, int S0, int RL>
 __device__ __forceinline__ void row_round(uint32_t* sm, const PassArgs& a)
 {
     constexpr int LOG_H = ML - S0 - RL, H = 1 << LOG_H, LOG_GPC = ML - RL;
+    // stride-16 rounds: adjacent blocks lie 2^(ML-S0) words (+ pad) apart, which
+    // puts the two half-warps on overlapping banks; pairing block b with b + 2^D
+    // (D = 9 - (ML - S0)), by swapping bits 0 and D of the block index, puts them
+    // 16 banks apart
+    constexpr bool PERM = LOG_H == 4 && ML - S0 >= 6 && ML - S0 <= 8;
+    constexpr int D = 9 - (ML - S0);
     const int ngroups = a.cols << LOG_GPC;
     for (int gid = threadIdx.x; gid < ngroups; gid += blockDim.x) {
-        const int grp = gid & ((1 << LOG_GPC) - 1);
+        int grp = gid & ((1 << LOG_GPC) - 1);
+        if constexpr (PERM) {
+            const int b = grp >> 4;
+            const int sw = (b ^ (b >> D)) & 1;             // bits 0 and D differ: flip both
+            grp ^= (sw | (sw << D)) << 4;
+        }
         const int c = gid >> LOG_GPC;
         const int blk = grp >> LOG_H;
         const int base = (c << ML) + (blk << (ML - S0)) + (grp & (H - 1));
