@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--cpu-signals", type=int, default=0,
                     help="oracle transforms timed for cpu_baseline (default: one per host core)")
+    ap.add_argument("--cpu-runs", type=int, default=5,
+                    help="timed runs of the oracle sample for cpu_baseline (median reported, after one warm-up)")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="keep the default NTT column/row split instead of timing the candidates at plan time")
     ap.add_argument("--merge", action="store_true", help="merged schedules across the convolutions of a part")
@@ -165,6 +167,81 @@ def host_cores():
         return os.cpu_count() or 1
 
 
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo; Arm parts by implementer/part id)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        info = open("/proc/cpuinfo").read()
+    except OSError:
+        return None
+    for line in info.splitlines():
+        if line.lower().startswith("model name"):
+            return line.split(":", 1)[1].strip()
+    impl = [l.split(":", 1)[1].strip() for l in info.splitlines() if l.startswith("CPU implementer")]
+    part = [l.split(":", 1)[1].strip() for l in info.splitlines() if l.startswith("CPU part")]
+    return f"implementer {impl[0]} part {part[0]}" if impl and part else None
+
+
+def _parse_cpulist(text):
+    cpus = set()
+    for tok in text.strip().split(","):
+        if "-" in tok:
+            a, b = tok.split("-")
+            cpus.update(range(int(a), int(b) + 1))
+        elif tok:
+            cpus.add(int(tok))
+    return cpus
+
+
+def gpu_host_locality(local):
+    """NUMA node and local CPUs of GPU `local` from sysfs (None where unknown)."""
+    info = {"gpu_numa_node": None, "gpu_local_cpus": None}
+    try:
+        import torch
+        props = torch.cuda.get_device_properties(local)
+        bus = "%04x:%02x:%02x.0" % (props.pci_domain_id, props.pci_bus_id, props.pci_device_id)
+    except Exception:   # noqa: BLE001 - older torch without PCI ids
+        return info
+    base = os.path.join("/sys/bus/pci/devices", bus)
+    try:
+        node = int(open(os.path.join(base, "numa_node")).read())
+        info["gpu_numa_node"] = node if node >= 0 else None
+    except (OSError, ValueError):
+        pass
+    try:
+        cpus = _parse_cpulist(open(os.path.join(base, "local_cpulist")).read())
+        info["gpu_local_cpus"] = sorted(cpus) if cpus else None
+    except (OSError, ValueError):
+        pass
+    return info
+
+
+def numa_nodes_of(addr):
+    """Pages per NUMA node of the host mapping that holds `addr` (/proc/self/numa_maps)."""
+    try:
+        start = None
+        for line in open("/proc/self/maps"):
+            lo, hi = (int(v, 16) for v in line.split()[0].split("-"))
+            if lo <= addr < hi:
+                start = lo
+                break
+        if start is None:
+            return None
+        for line in open("/proc/self/numa_maps"):
+            f = line.split()
+            if int(f[0], 16) == start:
+                return {k[1:]: int(v) for k, v in (t.split("=") for t in f[1:] if t[0] == "N" and "=" in t)}
+    except (OSError, ValueError):
+        pass
+    return None
+
+
 def _oracle_one(job):
     """One oracle transform (worker of the spawned pool; the oracle is single-threaded C)."""
     import oracle
@@ -223,6 +300,8 @@ def run_reference(a, rank, world):
                       "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                       "config": cfg, "impl": "reference",
                       "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                       "cpu_model": cpu_model(),
+                                       "build": "gcc -O3 -ffp-contract=off (no -march=native: portable host code)",
                                        "sample": f"{cores} transforms of n={a.n} per step, one single-threaded C "
                                                  f"oracle process per core"},
                       "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}),
@@ -579,6 +658,15 @@ def main():
         return max_over_ranks(dist, v, dev)
 
     B, n = a.batch, a.n
+    # host buffers on the GPU's own NUMA node: this thread runs on the GPU's local
+    # CPUs before the pinned buffers are allocated (the oracle's pool was spawned
+    # earlier and keeps every core)
+    loc = gpu_host_locality(local)
+    if loc["gpu_local_cpus"]:
+        try:
+            os.sched_setaffinity(0, loc["gpu_local_cpus"])
+        except OSError:
+            pass
     x_host = synth.complex_signal("uniform", n, a.seed + 1000 * rank, batch=B)
     x_pin = torch.from_numpy(x_host).pin_memory()
     x = x_pin.to(dev)
@@ -642,16 +730,81 @@ def main():
     e2e = None
     out_pin = torch.empty_like(x_pin).pin_memory()
     if not a.skip_e2e:
+        nbytes = B * n * 16
+        # standalone pinned copies of one step's input and output, the bounds of the pipeline
+        dbuf = torch.empty_like(x)
+        s_in, s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+
+        def copy_ms(fn, reps=5):
+            best = None
+            for _ in range(reps + 1):
+                torch.cuda.synchronize(dev)
+                c0 = torch.cuda.Event(enable_timing=True)
+                c1 = torch.cuda.Event(enable_timing=True)
+                c0.record(stream)
+                fn()
+                c1.record(stream)
+                torch.cuda.synchronize(dev)
+                t = c0.elapsed_time(c1)
+                best = t if best is None else min(best, t)
+            return best
+
+        def both():
+            ev = torch.cuda.Event()
+            ev.record(stream)
+            s_in.wait_event(ev)
+            s_out.wait_event(ev)
+            with torch.cuda.stream(s_in):
+                dbuf.copy_(x_pin, non_blocking=True)
+            with torch.cuda.stream(s_out):
+                out_pin.copy_(y, non_blocking=True)
+            stream.wait_stream(s_in)
+            stream.wait_stream(s_out)
+
+        h2d_ms = copy_ms(lambda: dbuf.copy_(x_pin, non_blocking=True))
+        d2h_ms = copy_ms(lambda: out_pin.copy_(y, non_blocking=True))
+        both_ms = copy_ms(both)
+        copy_gbs = {"h2d": nbytes / (h2d_ms / 1e3) / 1e9, "d2h": nbytes / (d2h_ms / 1e3) / 1e9,
+                    "h2d_d2h_concurrent_each": nbytes / (both_ms / 1e3) / 1e9, "bytes": nbytes,
+                    "how": "best of 5 pinned copies of one step's input (and output), CUDA events"}
+        del dbuf
         for _ in range(a.warmup):
             plan.execute_host(x_pin, out_pin)
-        esteps = max(1, a.steps // 3)
+        esteps = max(20, a.steps)
         barrier()
         t0 = time.perf_counter()
         for _ in range(esteps):
             plan.execute_host(x_pin, out_pin)
         dt = rank_max(time.perf_counter() - t0)
-        e2e = {"value": job_value(esteps, B, world, 1e3 * dt), "unit": UNIT, "h2d_bytes_per_step": B * n * 16,
-               "d2h_bytes_per_step": B * n * 16, "steps": esteps}
+        # the host pipeline of ozfft_execute_host: parts of 1/14, 6/14, 6/14 and 1/14 of the batch;
+        # copies in on one stream, computation on the caller's, copies out on a third
+        wts = [1, 6, 6, 1] if B >= 28 else [1, 1, 1, 1]
+        dev_ms = ms / a.steps
+        r_in = h2d_ms / B
+        r_out = d2h_ms / B
+        cuts = [0]
+        acc_w = 0
+        for w_ in wts:
+            acc_w += w_
+            cuts.append(B * acc_w // sum(wts) if B >= 28 else min(B, len(cuts) * ((B + 3) // 4)))
+        t_in = t_comp = t_out = 0.0
+        for i in range(4):
+            nb = cuts[i + 1] - cuts[i]
+            if nb <= 0:
+                continue
+            t_in += nb * r_in
+            t_comp = max(t_comp, t_in) + nb * dev_ms / B
+            t_out = max(t_out, t_comp) + nb * r_out
+        e2e = {"value": job_value(esteps, B, world, 1e3 * dt), "unit": UNIT, "h2d_bytes_per_step": nbytes,
+               "d2h_bytes_per_step": nbytes, "steps": esteps, "ms_per_step": 1e3 * dt / esteps,
+               "copy_gbs": copy_gbs,
+               "model_ms_per_step": t_out,
+               "model": "four-part pipeline from the measured copy times and the device step time",
+               "host": {"cpu_model": cpu_model(), "cores": host_cores(),
+                        "gpu_numa_node": loc["gpu_numa_node"],
+                        "thread_cpus": len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else None,
+                        "pinned_in_numa_pages": numa_nodes_of(x_pin.data_ptr()),
+                        "pinned_out_numa_pages": numa_nodes_of(out_pin.data_ptr())}}
 
     if rank != 0:
         if dist:
@@ -664,13 +817,18 @@ def main():
     runtime_fwd = stats["ntt_forward_runtime"]        # live forward vectors per execution
     inv_vecs = stats["ntt_inverse"]                   # live inverse vectors per execution
     m2f, m2i = stats["row_log_fwd"], stats["row_log_inv"]
-    # algorithmic bytes per execution: every pass reads and writes each live vector once (4N + 4N);
-    # the fused multiply-accumulate reads X_s and Ym_t (4N each) per product instead of Z
+    # algorithmic bytes per execution (stage-minimal: every input read once, every output written
+    # once).  A pass of the NTT reads and writes each live vector (4N + 4N).  The inverse row pass
+    # with the fused multiply-accumulate reads each signal's forward spectra X once (4N per live
+    # forward vector) and the w~* spectra Ym once per transform (4N per w~* vector), and writes the
+    # inverse vectors (4N each): 384N per transform at K = 3, L = 1.  The fused column pass + CRT
+    # reads the inverse vectors and writes the output (with the chirp).
     prods = sum(len(pairs) for b in range(B) for conv in plan.dump(ozfft.DUMP_SCHED, b)
                 for _, pairs in conv) * a.nprimes
+    wvecs = (stats["wstar_levels"][0] + stats["wstar_levels"][1]) * a.nprimes
     alg = {"ntt_fwd_col": 8 * N * runtime_fwd, "ntt_fwd_row": 8 * N * runtime_fwd,
-           "ntt_inv_col": 8 * N * inv_vecs, "ntt_inv_row": 8 * N * prods + 4 * N * inv_vecs,
-           "premul": B * (16 * n + 16 * n + 16 * N), "crt": 4 * n * inv_vecs + B * 32 * n}
+           "ntt_inv_col": 8 * N * inv_vecs, "ntt_inv_row": 4 * N * runtime_fwd + 4 * N * wvecs * B + 4 * N * inv_vecs,
+           "premul": B * (16 * n + 16 * n + 16 * N), "crt": 4 * N * inv_vecs + B * 32 * n}
     # algorithmic modular multiplications per execution: one per radix-2 butterfly
     # ((N/2) per stage and vector) and one per NTT-domain product and element
     mm = {"ntt_fwd_col": runtime_fwd * (lgN - m2f) * N // 2, "ntt_fwd_row": runtime_fwd * m2f * N // 2,
@@ -696,6 +854,7 @@ def main():
         hbm_view = {"achieved": alg_launch / (dom_ms / 1e3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
                     "frac": alg_launch / (dom_ms / 1e3) / 1e9 / hbm_peak,
                     "algorithmic_bytes_per_launch": alg_launch,
+                    "traffic_frac": (traffic / (dom_ms / 1e3) / 1e9 / hbm_peak) if traffic else None,
                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if pk else "fallback 6.8 TB/s"}
     if mm.get(dom):
         # integer roofline: the NTT kernels are bound by integer issue (ncu: DRAM well below
@@ -709,9 +868,12 @@ def main():
         achieved = mm_launch / (dom_ms / 1e3) / 1e12
         roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak_derived, "unit": "Tmodmul/s",
                 "frac": achieved / peak_derived, "traffic": traffic,
+                "traffic_frac": hbm_view["traffic_frac"] if hbm_view else None,
                 "peak_source": f"derived: 152 SMs x 4 x 32 lanes x 2.07 GHz / {BUTTERFLY_INSTR} lane instructions "
                                "per butterfly (ncu count of the register-only butterfly kernel)",
-                "peak_measured_registers": measured, "frac_of_measured": achieved / measured,
+                "register_only_rate_floor": measured,
+                "register_only_rate_note": "rate of the register-only butterfly kernel: a floor of the "
+                                           "attainable rate, not the roof",
                 "modmuls_per_launch": mm_launch, "launch_ms": dom_ms, "hbm_view": hbm_view}
     elif hbm_view:
         roof = dict(hbm_view, bound="hbm", kernel=dom, traffic=traffic, launch_ms=dom_ms)
@@ -729,15 +891,23 @@ def main():
         hi, lo = oracle.fft_q(x_host[0])
         acc["rel_l2_err_signal0"] = oracle.rel_l2_error(y0, hi, lo)
         cnt = min(a.cpu_signals or cpu_pool.workers, B)
-        t0 = time.perf_counter()
-        ys = cpu_pool.run([x_host[i] for i in range(cnt)], a.K, a.L, a.nprimes, a.ts)
-        dt = time.perf_counter() - t0
+        sig = [x_host[i] for i in range(cnt)]
+        ys = cpu_pool.run(sig, a.K, a.L, a.nprimes, a.ts)          # warm-up (and the parity sample)
+        runs = []
+        for _ in range(a.cpu_runs):
+            t0 = time.perf_counter()
+            cpu_pool.run(sig, a.K, a.L, a.nprimes, a.ts)
+            runs.append(time.perf_counter() - t0)
         cpu_pool.close()
+        dt = statistics.median(runs)
         yg = y[:cnt].cpu().numpy()
         same = all(np.array_equal(ys[i].view(np.uint64), yg[i].view(np.uint64)) for i in range(cnt))
         acc["bit_exact_vs_oracle"] = f"{cnt} signals: {'yes' if same else 'NO'}"
         cpu = {"value": cnt / dt, "unit": UNIT, "cores": min(cnt, cpu_pool.workers), "kind": "oracle",
-               "sample": f"{cnt} of the {B} signals (n={n}), one single-threaded C oracle process per host core"}
+               "cpu_model": cpu_model(), "runs": len(runs), "warmup_runs": 1, "statistic": "median",
+               "run_seconds": runs, "build": "gcc -O3 -ffp-contract=off (no -march=native: portable host code)",
+               "sample": f"{cnt} of the {B} signals (n={n}) per run, one single-threaded C oracle process "
+                         f"per host core"}
 
     cfg = workload(a)
     cfg.update({"mode": "batched (one ozfft_execute per step)", "parallelism": f"replicas x{world}",

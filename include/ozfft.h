@@ -14,7 +14,9 @@
  *      slice products with equal scale are summed in the NTT domain, at most
  *      L at a time (Alg. 8), and each sum is inverse-transformed           §4.4
  *   6. Garner CRT of the per-prime results (symmetric digits, Eq. (1))     §3.3
- *   7. rescale by 1/(c_x c_y), accumulate in double-word arithmetic, round  Alg. 8
+ *   7. rescale by 1/(c_x c_y) and accumulate: the exact integer sum of every
+ *      group's term, rounded once to binary64 (the sum Alg. 8's TSAdd
+ *      accumulation approximates)                                        Alg. 8
  *   8. y(k) = y'(k) * w(k)                                               Alg. 1
  * The inverse direction is conj -> forward -> conj -> divide by n (Eq. (4)).
  * Steps 1-8 all run in this library's CUDA kernels; w~*'s split and forward
@@ -63,7 +65,8 @@ enum {
     OZFFT_ERR_CUDA = 4,      /* a CUDA runtime call failed (ozfft_last_error has the text) */
     OZFFT_ERR_NONFINITE = 5, /* device status: the input held a NaN or an infinity */
     OZFFT_ERR_RANGE = 6,     /* device status: 2^(ceil(log2 max|v|) + 53 - alpha) overflows binary64 */
-    OZFFT_ERR_TIMEOUT = 7    /* reserved for bounded device-side waits */
+    OZFFT_ERR_TIMEOUT = 7    /* device status: a bounded device-side wait (the column pass's tile
+                                barrier) gave up; the output of that execution is not valid */
 };
 
 /* Plan options.  A zero field selects the default. */
@@ -146,8 +149,9 @@ int ozfft_execute(ozfft_plan_t plan, const void* in, void* out, void* stream);
 int ozfft_execute_host(ozfft_plan_t plan, const void* in, void* out, void* stream);
 
 /* Synchronize `stream`, return the data-dependent status recorded by the
-   executions since the previous call (OZFFT_OK, OZFFT_ERR_NONFINITE or
-   OZFFT_ERR_RANGE), and clear it. */
+   executions since the previous call (OZFFT_OK, OZFFT_ERR_NONFINITE,
+   OZFFT_ERR_RANGE or OZFFT_ERR_TIMEOUT, in that order of precedence when
+   several were recorded), and clear it. */
 int ozfft_get_status(ozfft_plan_t plan, void* stream);
 
 /* Plan facts and the transform counts of the most recent execution.
@@ -228,7 +232,10 @@ int ozfft_selftest_wait_timeout(void* stream);
    the first call after a call with another n, builds the tables of n in the
    array and synchronizes the device: make that call before any stream capture.
    Later calls only enqueue kernels on `stream`.  All calls share the array and
-   it keeps the last call's contents; calls that overlap on the GPU race on it.
+   it keeps the last call's contents; a call for another n first waits for the
+   device to finish earlier work, so calls in a row (on one stream) are safe,
+   but calls that overlap on the GPU (two streams at once) race on it.  The
+   call runs on the current CUDA device, which must hold `in` and `out`.
    Data-dependent status is recorded in the array and not reported. */
 int ozfft_execute_noalloc(int64_t n, int direction, const void* in, void* out, void* stream);
 

@@ -26,7 +26,10 @@ ADJOINT, INVERSE_ADJOINT = 2, -2   # F^H x and (1/n) F x (reverse-mode adjoints)
 
 
 def build_command():
-    cmd = ["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+    # -O3 without -march=native (the library must build and agree on x86-64 and
+    # aarch64 hosts); -ffp-contract=off and -fno-fast-math keep every binary64
+    # operation as written, so the optimisation level cannot change a result
+    cmd = ["gcc", "-O3", "-std=gnu11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
            "-shared", SRC, "-o", LIB, "-lm"]
     if platform.machine() not in ("aarch64", "arm64"):
         cmd.insert(-1, "-lquadmath")
@@ -35,7 +38,7 @@ def build_command():
 
 def build(force: bool = False) -> str:
     """Compile ozoracle.c into liboracle.so (idempotent)."""
-    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
+    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(SRC), os.path.getmtime(__file__)):
         subprocess.run(build_command(), check=True)
     return LIB
 

@@ -31,6 +31,8 @@
 //                    memory.
 // One carry pass and an integer round-to-nearest-even at the end produce the
 // binary64 bit pattern.
+#include <mutex>
+
 #include "ntt_impl.cuh"
 #include "ts_arith.cuh"
 
@@ -731,7 +733,14 @@ __global__ void __launch_bounds__(WIDE_THREADS) crt_wide_kernel(CrtArgs a)
     }
 }
 
-static bool s_garner_ready = false;
+// Per-device state: the __constant__ Garner constants and the wide kernel's
+// shared-memory attribute belong to each device's copy of the module, so each
+// device is set up once, under a mutex (plans may be created from several
+// threads and on several devices).
+constexpr int CRT_MAX_DEVICES = 64;
+static bool s_garner_ready[CRT_MAX_DEVICES] = {};
+static bool s_wide_attr[CRT_MAX_DEVICES] = {};
+static std::mutex s_crt_mutex;
 
 static uint64_t host_powmod(uint64_t b, uint64_t e, uint64_t m)
 {
@@ -748,7 +757,12 @@ int crt_launches() { return 2; }
 
 cudaError_t crt_init()
 {
-    if (!s_garner_ready) {
+    int dev = 0;
+    cudaError_t de = cudaGetDevice(&dev);
+    if (de != cudaSuccess) return de;
+    if (dev < 0 || dev >= CRT_MAX_DEVICES) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(s_crt_mutex);
+    if (!s_garner_ready[dev]) {
         GarnerConst gc;
         gc.inv01 = (uint32_t)host_powmod(P0 % P1, P1 - 2, P1);
         gc.inv01q = (uint32_t)(((uint64_t)gc.inv01 << 32) / P1);
@@ -758,7 +772,16 @@ cudaError_t crt_init()
         gc.p0_mod2 = P0 % P2;
         cudaError_t e = cudaMemcpyToSymbol(c_garner, &gc, sizeof(gc));
         if (e != cudaSuccess) return e;
-        s_garner_ready = true;
+        s_garner_ready[dev] = true;
+    }
+    if (!s_wide_attr[dev]) {
+        // crt_wide_kernel's limb columns exceed the default 48 KiB of dynamic shared memory
+        const int smem = (int)(sizeof(long long) * WIDE_LIMBS * WIDE_THREADS);
+        cudaError_t e = cudaFuncSetAttribute(crt_wide_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(crt_wide_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        s_wide_attr[dev] = true;
     }
     return cudaSuccess;
 }
@@ -1074,14 +1097,6 @@ cudaError_t launch_crt_post(const CrtArgs& a, cudaStream_t s)
     if (e != cudaSuccess) return e;
     // signals with three primes or a wide scale span: small blocks, limb columns in shared memory
     const size_t smem = sizeof(long long) * WIDE_LIMBS * WIDE_THREADS;
-    static bool attr = false;
-    if (!attr) {
-        e = cudaFuncSetAttribute(crt_wide_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(crt_wide_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
     const int64_t grid = a.B * chunks < 304 ? a.B * chunks : 304;
     if (sd) crt_wide_kernel<true><<<(unsigned)grid, WIDE_THREADS, smem, s>>>(a);
     else crt_wide_kernel<false><<<(unsigned)grid, WIDE_THREADS, smem, s>>>(a);

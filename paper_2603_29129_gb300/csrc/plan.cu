@@ -1280,9 +1280,9 @@ int64_t ozfft_debug_dump(ozfft_plan_t p, int stage, int64_t index, void* dst, vo
 // the length's tables in the array and synchronizes the device, so it should
 // come before any stream capture; later calls with the same n only enqueue
 // kernels on `stream`.  All calls share the array, which keeps the last call's
-// contents: each call clears what must start at zero, and calls that overlap on
-// the GPU (two streams, or a call for another n before the previous finished)
-// race on it.
+// contents: each call clears what must start at zero.  A call for another n
+// first waits for the device to finish earlier work, so calls in a row stay
+// safe; calls that overlap on the GPU (two streams at once) race on it.
 // ============================================================================
 #include <mutex>
 
@@ -1345,6 +1345,10 @@ static int noalloc_setup(NoallocState& st, int dev, int64_t n, int64_t N, int al
         st.base = (unsigned char*)ptr;
         st.have_base = true;
     }
+    // a previous call's kernels (on any stream) may still read the tables that
+    // are about to be rewritten: wait for them, so that calls in a row on one
+    // stream stay safe when n changes
+    CUDA_TRY(cudaDeviceSynchronize());
     st.n = 0;
     ozfft_plan_s& p = st.plan;
     const int K = 3, P = 2, NM = (int)NOALLOC_MAX_N;
@@ -1429,6 +1433,7 @@ static int noalloc_setup(NoallocState& st, int dev, int64_t n, int64_t N, int al
     p.geom_inv.nvec = 4 * p.G * P;
     p.geom_inv.kcnt = p.kcnt;
     p.geom_inv.sched = p.sched;
+    CUDA_TRY(crt_init());   // Garner constants of this device (per device, once)
     st.n = n;
     return OZFFT_OK;
 }

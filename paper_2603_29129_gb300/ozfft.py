@@ -258,9 +258,15 @@ def execute_noalloc(x, out, direction=FORWARD, stream=None):
     which allocates no device memory (its workspace is a static device array;
     n <= 8192 for powers of two, n <= 4096 otherwise)."""
     import torch
-    if x.dtype != torch.complex128 or not x.is_cuda or not x.is_contiguous() or out.shape != x.shape:
-        raise OzfftError(ERR_ARG, "input and output must be contiguous CUDA complex128 tensors of one shape")
-    _check(load().ozfft_execute_noalloc(x.numel(), int(direction), x.data_ptr(), out.data_ptr(), _stream_ptr(stream)))
+    for t in (x, out):
+        if t.dtype != torch.complex128 or not t.is_cuda or not t.is_contiguous():
+            raise OzfftError(ERR_ARG, "input and output must be contiguous CUDA complex128 tensors")
+    if out.shape != x.shape or out.device != x.device:
+        raise OzfftError(ERR_ARG, "input and output must have one shape and one device")
+    # the C call runs on the current device: make it the tensors' device
+    with torch.cuda.device(x.device):
+        _check(load().ozfft_execute_noalloc(x.numel(), int(direction), x.data_ptr(), out.data_ptr(),
+                                            _stream_ptr(stream)))
     return out
 
 
