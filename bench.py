@@ -451,8 +451,9 @@ def run_stress(a, rank, world, local):
         y = torch.empty_like(x)
         if rank == 0 and not a.skip_cpu:
             hi, lo = oracle.fft_q(xh[0])
-        for L, merge in ((1, False), (3, False), (3, True)):
-            plan = ozfft.Plan(n, B, ozfft.FORWARD, K=a.K, L=L, nprimes=a.nprimes, merge=merge)
+        for L, merge, K in ((1, False, a.K), (3, False, a.K), (3, True, a.K), (1, False, ozfft.K_INF),
+                            (3, False, ozfft.K_INF)):
+            plan = ozfft.Plan(n, B, ozfft.FORWARD, K=K, L=L, nprimes=a.nprimes, merge=merge)
             for _ in range(a.warmup):
                 plan.execute(x, y)
             if dist:
@@ -467,8 +468,10 @@ def run_stress(a, rank, world, local):
             ms = max_over_ranks(dist, e0.elapsed_time(e1), dev)
             st = plan.stats()
             ok = plan.status() == ozfft.OK
-            r = {"n": n, "L": L, "merge": merge, "value": job_value(a.steps, B, world, ms), "unit": UNIT,
+            r = {"n": n, "K": "inf" if K == ozfft.K_INF else K, "L": L, "merge": merge,
+                 "value": job_value(a.steps, B, world, ms), "unit": UNIT,
                  "ms_per_step": ms / a.steps, "status_ok": ok, "alpha": st["alpha"],
+                 "x_split_levels_mean": st["ntt_forward_runtime"] / (2 * B * a.nprimes),
                  "ntt_per_transform_runtime": (st["ntt_forward_runtime"] + st["ntt_inverse"]) / B,
                  "ntt_per_transform_total": (st["ntt_forward_runtime"] + st["ntt_inverse"]) / B
                  + st["ntt_forward_plan"]}
@@ -487,7 +490,7 @@ def run_stress(a, rank, world, local):
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": tot_ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "complex128 n=2^20 and n=2^22 x 8 signals, uniform[-1,1) parts with 1% spikes "
-                                   "of +-1e12, forward, K=3, L=1 and L=3, two primes",
+                                   "of +-1e12, forward, K=3 (L=1, L=3, L=3 merged) and K=inf (L=1, L=3), two primes",
                        "batch_per_gpu": B, "seed": a.seed, "parallelism": f"replicas x{world}",
                        "l2": "inputs (8 x n x 16 B) exceed L2 each step; no flush"},
             "results": results, "clocks": clk}
@@ -776,6 +779,14 @@ def main():
         for _ in range(esteps):
             plan.execute_host(x_pin, out_pin)
         dt = rank_max(time.perf_counter() - t0)
+        # device time of the kernels inside those calls (per-kernel events, all four parts)
+        plan.profile()
+        plan.set_profiling(True)
+        for _ in range(5):
+            plan.execute_host(x_pin, out_pin)
+        plan.set_profiling(False)
+        hprof = plan.profile()
+        host_kernel_ms = sum(v["ms"] for v in hprof["slots"].values()) / 5
         # the host pipeline of ozfft_execute_host: parts of 1/14, 6/14, 6/14 and 1/14 of the batch;
         # copies in on one stream, computation on the caller's, copies out on a third
         wts = [1, 6, 6, 1] if B >= 28 else [1, 1, 1, 1]
@@ -799,6 +810,7 @@ def main():
                "d2h_bytes_per_step": nbytes, "steps": esteps, "ms_per_step": 1e3 * dt / esteps,
                "copy_gbs": copy_gbs,
                "model_ms_per_step": t_out,
+               "kernel_ms_per_step_in_pipeline": host_kernel_ms,
                "model": "four-part pipeline from the measured copy times and the device step time",
                "host": {"cpu_model": cpu_model(), "cores": host_cores(),
                         "gpu_numa_node": loc["gpu_numa_node"],

@@ -65,13 +65,22 @@ enum {
     OZFFT_ERR_CUDA = 4,      /* a CUDA runtime call failed (ozfft_last_error has the text) */
     OZFFT_ERR_NONFINITE = 5, /* device status: the input held a NaN or an infinity */
     OZFFT_ERR_RANGE = 6,     /* device status: 2^(ceil(log2 max|v|) + 53 - alpha) overflows binary64 */
-    OZFFT_ERR_TIMEOUT = 7    /* device status: a bounded device-side wait (the column pass's tile
+    OZFFT_ERR_TIMEOUT = 7,   /* device status: a bounded device-side wait (the column pass's tile
                                 barrier) gave up; the output of that execution is not valid */
+    OZFFT_ERR_LEVELS = 8     /* device status (K = OZFFT_K_INF): a real vector still had a nonzero
+                                residual after OZFFT_K_INF_CAP split levels; its result is that of
+                                K = OZFFT_K_INF_CAP, not of K = infinity */
 };
+
+/* ozfft_options.K = OZFFT_K_INF selects K = infinity of §4.4 (Alg. 3 runs until the
+   residual is zero, so the split is error free): every real vector gets as many
+   levels as it needs, at most OZFFT_K_INF_CAP; the workspace is sized for the
+   cap (G = 64 flush groups per convolution). */
+enum { OZFFT_K_INF = -1, OZFFT_K_INF_CAP = 8 };
 
 /* Plan options.  A zero field selects the default. */
 typedef struct {
-    int32_t K;        /* split cap K of §4.4 (default 3; 1..8) */
+    int32_t K;        /* split cap K of §4.4 (default 3; 1..8, or OZFFT_K_INF for K = infinity) */
     int32_t L;        /* NTT-domain accumulation bound L of §4.4 (default 1 = none; 1..8) */
     int32_t nprimes;  /* 2 (default: p0 = 2130706433, p1 = 2113929217, §5.1) or 3 (adds 2013265921) */
     int64_t conv_len; /* cyclic length N (default: n if n is a power of two, else the least power of
@@ -150,15 +159,15 @@ int ozfft_execute_host(ozfft_plan_t plan, const void* in, void* out, void* strea
 
 /* Synchronize `stream`, return the data-dependent status recorded by the
    executions since the previous call (OZFFT_OK, OZFFT_ERR_NONFINITE,
-   OZFFT_ERR_RANGE or OZFFT_ERR_TIMEOUT, in that order of precedence when
-   several were recorded), and clear it. */
+   OZFFT_ERR_RANGE, OZFFT_ERR_TIMEOUT or OZFFT_ERR_LEVELS, in that order of
+   precedence when several were recorded), and clear it. */
 int ozfft_get_status(ozfft_plan_t plan, void* stream);
 
 /* Plan facts and the transform counts of the most recent execution.
    Synchronizes `stream` (the counts are computed on the device). */
 typedef struct {
     int64_t n, N, batch;
-    int32_t K, L, nprimes, alpha, direction;
+    int32_t K, L, nprimes, alpha, direction;   /* K = OZFFT_K_INF for K = infinity */
     int32_t wstar_levels[2];      /* split levels of Re w~*, Im w~* */
     int64_t ntt_forward_runtime;  /* forward NTTs of x~' slices, summed over the batch */
     int64_t ntt_forward_plan;     /* forward NTTs of w~* slices (once per plan) */
@@ -238,6 +247,28 @@ int ozfft_selftest_wait_timeout(void* stream);
    call runs on the current CUDA device, which must hold `in` and `out`.
    Data-dependent status is recorded in the array and not reported. */
 int ozfft_execute_noalloc(int64_t n, int direction, const void* in, void* out, void* stream);
+
+/* Host-side fault hook for tests of failure handling (the paper has no
+   counterpart; nothing it does faults or stalls a GPU).  The environment
+   variable OZFFT_FAULT, read at every plan creation and execution, makes the
+   library take its own error paths:
+     "alloc"     every device allocation of libozfft fails as a failed
+                 cudaMalloc would: plan creation returns NULL (ozfft_last_error
+                 names the injection) and a first host-buffer execution returns
+                 OZFFT_ERR_ALLOC; the plan and the CUDA context stay usable;
+     "alloc:N"   only the N-th allocation (N >= 1) of each plan creation, or of a
+                 host-buffer execution's staging buffers, fails (the cleanup of a
+                 partly built plan);
+     "status:C"  every execution records the device status of code C (one of
+                 OZFFT_ERR_NONFINITE, _RANGE, _TIMEOUT, _LEVELS) after its
+                 kernels, as its kernels would on such data; ozfft_get_status
+                 then returns C once.
+   Unset or empty: no injection.  Any other value makes plan creation and
+   executions fail with OZFFT_ERR_ARG.  ozfft_fault_config parses the current
+   value without touching a GPU: *kind = 0 (none), 1 (alloc) or 2 (status),
+   *arg = N (0 for plain "alloc") or C; returns OZFFT_OK or OZFFT_ERR_ARG. */
+enum { OZFFT_FAULT_NONE = 0, OZFFT_FAULT_ALLOC = 1, OZFFT_FAULT_STATUS = 2 };
+int ozfft_fault_config(int32_t* kind, int64_t* arg);
 
 /* Release every resource of the plan (synchronizes its device first). */
 void ozfft_destroy(ozfft_plan_t plan);

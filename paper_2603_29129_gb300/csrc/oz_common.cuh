@@ -21,6 +21,7 @@ constexpr int MAX_L = 8;                      // products per flush group
 constexpr int ST_NONFINITE = 1;
 constexpr int ST_RANGE = 2;
 constexpr int ST_TIMEOUT = 4;   // a bounded device-side wait gave up
+constexpr int ST_LEVELS = 8;    // K = infinity: a vector's residual is nonzero after MAX_K levels
 
 struct PrimeInfo {
     uint32_t p;

@@ -25,6 +25,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/ozfft.h"
 #include "oz_common.cuh"
 #include "oz_kernels.h"
@@ -39,6 +41,86 @@ static int fail(int code, const std::string& msg)
     return code;
 }
 
+// NVTX range around one stage of an execution (or plan creation), so that a
+// timeline tool (Nsight Systems) labels the kernels by stage; with no tool
+// attached a range costs a few nanoseconds.
+struct StageRange {
+    explicit StageRange(const char* name) { nvtxRangePushA(name); }
+    ~StageRange() { nvtxRangePop(); }
+    StageRange(const StageRange&) = delete;
+    StageRange& operator=(const StageRange&) = delete;
+};
+
+// ------------------------------------------------------- host-side fault hook
+// OZFFT_FAULT (read at every plan creation and execution) makes libozfft take
+// its own error paths without any GPU fault:
+//   alloc       every device allocation of libozfft fails as a failed
+//               cudaMalloc would (OZFFT_ERR_ALLOC);
+//   alloc:N     the N-th device allocation (N >= 1) of each plan creation, or
+//               of a host-buffer execution's staging, fails;
+//   status:C    every execution records the device status of error code C
+//               (OZFFT_ERR_NONFINITE, _RANGE, _TIMEOUT or _LEVELS) after its
+//               kernels, as the kernels would on such data.
+// Anything else (set and not empty) is an argument error of the call.
+enum { FAULT_NONE = 0, FAULT_ALLOC = 1, FAULT_STATUS = 2 };
+static thread_local int64_t g_alloc_seq = 0;   // allocations since the current plan creation / staging began
+
+static int fault_read(int32_t* kind, int64_t* arg)
+{
+    *kind = FAULT_NONE;
+    *arg = 0;
+    const char* v = std::getenv("OZFFT_FAULT");
+    if (!v || !*v) return OZFFT_OK;
+    const std::string s(v);
+    auto number = [](const std::string& t, int64_t* out) {
+        if (t.empty() || t.size() > 18) return false;
+        int64_t x = 0;
+        for (char c : t) {
+            if (c < '0' || c > '9') return false;
+            x = x * 10 + (c - '0');
+        }
+        *out = x;
+        return true;
+    };
+    if (s == "alloc") { *kind = FAULT_ALLOC; return OZFFT_OK; }
+    if (s.rfind("alloc:", 0) == 0 && number(s.substr(6), arg) && *arg >= 1) { *kind = FAULT_ALLOC; return OZFFT_OK; }
+    if (s.rfind("status:", 0) == 0 && number(s.substr(7), arg) && *arg >= OZFFT_ERR_NONFINITE &&
+        *arg <= OZFFT_ERR_LEVELS) {
+        *kind = FAULT_STATUS;
+        return OZFFT_OK;
+    }
+    *arg = 0;
+    return fail(OZFFT_ERR_ARG, "OZFFT_FAULT: unknown setting '" + s + "' (alloc, alloc:N, status:C)");
+}
+
+static int fault_status_bit(int64_t code)
+{
+    switch (code) {
+    case OZFFT_ERR_NONFINITE: return ST_NONFINITE;
+    case OZFFT_ERR_RANGE: return ST_RANGE;
+    case OZFFT_ERR_TIMEOUT: return ST_TIMEOUT;
+    case OZFFT_ERR_LEVELS: return ST_LEVELS;
+    default: return 0;
+    }
+}
+
+__global__ void fault_status_kernel(int* status, int bit) { atomicOr(status, bit); }
+
+// after an execution's kernels: the status that OZFFT_FAULT=status:C asks for
+static int fault_after_execution(int* status, cudaStream_t s)
+{
+    int32_t kind;
+    int64_t arg;
+    const int rc = fault_read(&kind, &arg);
+    if (rc) return rc;
+    if (kind == FAULT_STATUS) {
+        fault_status_kernel<<<1, 1, 0, s>>>(status, fault_status_bit(arg));
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return fail(OZFFT_ERR_CUDA, std::string("fault hook: ") + cudaGetErrorString(e));
+    }
+    return OZFFT_OK;
+}
+
 #define CUDA_TRY(call)                                                                          \
     do {                                                                                        \
         cudaError_t e_ = (call);                                                                \
@@ -49,6 +131,7 @@ static int fail(int code, const std::string& msg)
 struct ozfft_plan_s {
     int64_t n = 0, N = 0, B = 0;
     int direction = -1, K = 3, L = 1, P = 2, alpha = 0, G = 9, debug = 0, merge = 0, ts = 0;
+    int kinf = 0;                // K = infinity: K holds the level cap MAX_K
     int garner_u = 0;            // every convolution value |z| < p0 p1 / 2 - p0 (CRT without centering z0)
     int64_t chunk = 1;           // signals per inverse-stage chunk (Z holds one chunk)
     int device = 0;
@@ -213,7 +296,8 @@ static int ceil_log2_h(double mu)
 __global__ void schedule_kernel(const uint64_t* __restrict__ mu, int64_t B, int K, int L, int alpha,
                                 const SigDesc* __restrict__ sd, const int32_t* __restrict__ wk,
                                 const int32_t* __restrict__ wsexp, Sched* __restrict__ sched,
-                                int32_t* __restrict__ kcnt, int32_t* __restrict__ span, int merge)
+                                int32_t* __restrict__ kcnt, int32_t* __restrict__ span, int merge, int kinf,
+                                int* __restrict__ status)
 {
     const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (b >= B) return;
@@ -233,6 +317,9 @@ __global__ void schedule_kernel(const uint64_t* __restrict__ mu, int64_t B, int 
         }
         kxv[v] = kx;
         kcnt[b * 2 + v] = kx;
+        // K = infinity (Alg. 3 until the residual is zero) under the level cap: a
+        // residual left after the last level means the split was not error free
+        if (kinf && mu[(b * 2 + v) * (K + 1) + K] != 0) atomicOr(status, ST_LEVELS);
     }
     int smin = 0, smax = 0, any = 0, mono = 1;   // mono: every convolution's scales non-increasing
     if (merge) {
@@ -364,6 +451,19 @@ template <typename T>
 static int dalloc(ozfft_plan_s* p, T** ptr, size_t count)
 {
     const size_t bytes = sizeof(T) * (count ? count : 1);
+    int32_t fk;
+    int64_t fa;
+    const int frc = fault_read(&fk, &fa);
+    ++g_alloc_seq;
+    if (frc) {
+        *ptr = nullptr;
+        return frc;
+    }
+    if (fk == FAULT_ALLOC && (fa == 0 || fa == g_alloc_seq)) {
+        *ptr = nullptr;
+        return fail(OZFFT_ERR_ALLOC, std::string("cudaMalloc of ") + std::to_string(bytes) +
+                                         " bytes: failure injected by OZFFT_FAULT");
+    }
     cudaError_t e = cudaMalloc((void**)ptr, bytes);
     if (e != cudaSuccess) {
         *ptr = nullptr;
@@ -512,6 +612,8 @@ static int plan_build(ozfft_plan_s* p)
                 }
                 wk[b * 2 + v] = k;
                 p->fwd_plan += (int64_t)k * P;
+                if (p->kinf && hmu[(b * 2 + v) * (K + 1) + K] != 0)
+                    return fail(OZFFT_ERR_LEVELS, "w* needs more than " + std::to_string(K) + " split levels");
             }
         }
         p->wk_host[0] = wk[0];
@@ -583,6 +685,7 @@ static int force_split(ozfft_plan_s* p, int m2)
 // results are bit-identical.
 static int autotune_ntt(ozfft_plan_s* p)
 {
+    StageRange range("ozfft_autotune");
     const int lg = p->geom_fwd.lgN;
     std::vector<int> cands;
     for (int m2 = 10; m2 <= 14; ++m2) {
@@ -692,28 +795,34 @@ static int run_plan_range(ozfft_plan_s* p, const void* in, void* out, cudaStream
             p->cur = &p->pending.back();
         }
     }
-    if (p->ts)
-        CUDA_TRY(launch_ts_premul((const double2*)in, p->chirp, p->n, N, B, p->direction > 0, (float*)r, mu, K,
-                                  p->status, s));
-    else
-        CUDA_TRY(launch_premul((const double2*)in, p->chirp, p->n, N, B, p->direction > 0, sd, p->io_ref, r, mu, K,
-                               p->status, s));
-    mark(p, OZFFT_PROF_PREMUL, s);
+    {
+        StageRange range("premultiply (chirp, Alg. 1)");
+        if (p->ts)
+            CUDA_TRY(launch_ts_premul((const double2*)in, p->chirp, p->n, N, B, p->direction > 0, (float*)r, mu, K,
+                                      p->status, s));
+        else
+            CUDA_TRY(launch_premul((const double2*)in, p->chirp, p->n, N, B, p->direction > 0, sd, p->io_ref, r, mu,
+                                   K, p->status, s));
+        mark(p, OZFFT_PROF_PREMUL, s);
+    }
     if (p->debug && whole && !p->ts)
         CUDA_TRY(cudaMemcpyAsync(p->dbg_r, p->r, sizeof(double) * B * 2 * N, cudaMemcpyDeviceToDevice, s));
-    if (p->ts) {
-        for (int k = 0; k < K; ++k) {
-            CUDA_TRY(launch_ts_split_level(k, (float*)r, mu, N, B * 2, K, p->alpha, P, X, k + 1 < K, p->status, s));
+    {
+        StageRange range("split (Alg. 3) and residues");
+        if (p->ts) {
+            for (int k = 0; k < K; ++k) {
+                CUDA_TRY(launch_ts_split_level(k, (float*)r, mu, N, B * 2, K, p->alpha, P, X, k + 1 < K, p->status, s));
+                mark(p, OZFFT_PROF_SPLIT, s);
+            }
+        } else {
+            CUDA_TRY(launch_split_spec(r, mu, N, B * 2, K, p->alpha, sd, P, X, p->status, s));
             mark(p, OZFFT_PROF_SPLIT, s);
         }
-    } else {
-        CUDA_TRY(launch_split_spec(r, mu, N, B * 2, K, p->alpha, sd, P, X, p->status, s));
-        mark(p, OZFFT_PROF_SPLIT, s);
     }
     if (p->debug && whole)
         CUDA_TRY(cudaMemcpyAsync(p->dbg_X, p->X, sizeof(uint32_t) * B * 2 * K * P * N, cudaMemcpyDeviceToDevice, s));
     schedule_kernel<<<(unsigned)((B + 127) / 128), 128, 0, s>>>(mu, B, K, p->L, p->alpha, sd, p->wk, p->wsexp, sched,
-                                                                 kcnt, span, p->merge);
+                                                                 kcnt, span, p->merge, p->kinf, p->status);
     CUDA_TRY(cudaGetLastError());
     mark(p, OZFFT_PROF_SCHEDULE, s);
     NttGeom gf = p->geom_fwd;
@@ -721,6 +830,7 @@ static int run_plan_range(ozfft_plan_s* p, const void* in, void* out, cudaStream
     gf.kcnt = kcnt;
     gf.sched = sched;
     gf.vec0 = sb0 * 2 * K * P;   // the launch's first vector in the tensor map of X
+    StageRange range_fwd("forward NTTs");
     if (gf.m1 > 0) {
         CUDA_TRY(launch_ntt_fwd_col(gf, X, p->tw, s));
         mark(p, OZFFT_PROF_NTT_FWD_COL, s);
@@ -729,6 +839,7 @@ static int run_plan_range(ozfft_plan_s* p, const void* in, void* out, cudaStream
     mark(p, OZFFT_PROF_NTT_FWD_ROW, s);
     // inverse stages chunk by chunk: Z of one chunk stays in L2 between the passes
     for (int64_t b0 = 0; b0 < B; b0 += p->chunk) {
+        StageRange range_inv("Alg. 8 MAC, inverse NTTs, Garner CRT, accumulation, post-multiply");
         const int64_t nb = std::min<int64_t>(p->chunk, B - b0);
         NttGeom gi = p->geom_inv;
         gi.nvec = nb * 4 * p->G * P;
@@ -807,7 +918,8 @@ ozfft_plan_t ozfft_plan_ex(int64_t n, int64_t batch, int direction, const ozfft_
 {
     ozfft_options o{};
     if (opt) o = *opt;
-    const int K = o.K ? o.K : 3, L = o.L ? o.L : 1, P = o.nprimes ? o.nprimes : 2;
+    const int kinf = o.K == OZFFT_K_INF;
+    const int K = kinf ? MAX_K : (o.K ? o.K : 3), L = o.L ? o.L : 1, P = o.nprimes ? o.nprimes : 2;
     if (n < 1 || batch < 1 || (direction != OZFFT_FORWARD && direction != OZFFT_INVERSE && direction != OZFFT_ADJOINT &&
                                direction != OZFFT_INVERSE_ADJOINT) || K < 1 || K > MAX_K ||
         L < 1 || L > MAX_L || P < 2 || P > 3) {
@@ -823,8 +935,8 @@ ozfft_plan_t ozfft_plan_ex(int64_t n, int64_t batch, int direction, const ozfft_
         fail(OZFFT_ERR_LENGTH, "ozfft_plan: convolution length must be a power of two <= 2^24, equal to n or >= 2n-1");
         return nullptr;
     }
-    if (o.ts && (P != 2 || o.merge)) {
-        fail(OZFFT_ERR_ARG, "ozfft_plan: the TS variant takes two primes and no merged schedules");
+    if (o.ts && (P != 2 || o.merge || kinf)) {
+        fail(OZFFT_ERR_ARG, "ozfft_plan: the TS variant takes two primes, no merged schedules and a finite K");
         return nullptr;
     }
     int alpha = alpha_h(n, L, P);
@@ -833,12 +945,20 @@ ozfft_plan_t ozfft_plan_ex(int64_t n, int64_t batch, int direction, const ozfft_
         fail(OZFFT_ERR_LENGTH, "ozfft_plan: no split width alpha >= 1 for this n, L and prime count");
         return nullptr;
     }
+    StageRange range("ozfft_plan");
+    g_alloc_seq = 0;
+    {
+        int32_t fk;
+        int64_t fa;
+        if (fault_read(&fk, &fa)) return nullptr;   // a malformed OZFFT_FAULT
+    }
     ozfft_plan_s* p = new ozfft_plan_s;
     p->n = n;
     p->N = N;
     p->B = batch;
     p->direction = direction;
     p->K = K;
+    p->kinf = kinf;
     p->L = L;
     p->P = P;
     p->G = K * K;
@@ -875,7 +995,8 @@ ozfft_plan_t ozfft_plan_many(const int64_t* lengths, int64_t count, int directio
 {
     ozfft_options o{};
     if (opt) o = *opt;
-    const int K = o.K ? o.K : 3, L = o.L ? o.L : 1, P = o.nprimes ? o.nprimes : 2;
+    const int kinf = o.K == OZFFT_K_INF;
+    const int K = kinf ? MAX_K : (o.K ? o.K : 3), L = o.L ? o.L : 1, P = o.nprimes ? o.nprimes : 2;
     if (!lengths || count < 1 || (direction != OZFFT_FORWARD && direction != OZFFT_INVERSE &&
                                   direction != OZFFT_ADJOINT && direction != OZFFT_INVERSE_ADJOINT) ||
         K < 1 || K > MAX_K || L < 1 || L > MAX_L || P < 2 || P > 3 || o.conv_len != 0 || o.debug != 0 || o.chunk < 0 ||
@@ -916,6 +1037,13 @@ ozfft_plan_t ozfft_plan_many(const int64_t* lengths, int64_t count, int directio
     for (auto& c : cls) zdemand += (double)c.second.size() * 4.0 * G * P * c.first * 4.0;
     const double frac = std::min(1.0, (double)(int64_t(16) << 30) / zdemand);
 
+    StageRange range("ozfft_plan_many");
+    g_alloc_seq = 0;
+    {
+        int32_t fk;
+        int64_t fa;
+        if (fault_read(&fk, &fa)) return nullptr;   // a malformed OZFFT_FAULT
+    }
     ozfft_plan_s* p = new ozfft_plan_s;
     p->B = count;
     p->n = off[count];
@@ -923,6 +1051,7 @@ ozfft_plan_t ozfft_plan_many(const int64_t* lengths, int64_t count, int directio
     p->N = cls.front().first;
     p->direction = direction;
     p->K = K;
+    p->kinf = kinf;
     p->L = L;
     p->P = P;
     p->G = G;
@@ -942,6 +1071,7 @@ ozfft_plan_t ozfft_plan_many(const int64_t* lengths, int64_t count, int directio
         q->B = (int64_t)c.second.size();
         q->direction = direction;
         q->K = K;
+        q->kinf = kinf;
         q->L = L;
         q->P = P;
         q->G = G;
@@ -980,8 +1110,9 @@ ozfft_plan_t ozfft_plan_many(const int64_t* lengths, int64_t count, int directio
     p->launches += 1;   // the in/out pointer update
     if (cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming) != cudaSuccess)
         return bail(OZFFT_ERR_CUDA, "ozfft_plan_many: event");
-    if (cudaMalloc((void**)&p->status, sizeof(int)) != cudaSuccess || cudaMemset(p->status, 0, sizeof(int)) != cudaSuccess)
-        return bail(OZFFT_ERR_ALLOC, "ozfft_plan_many: status word");
+    if (dalloc(p, &p->status, 1)) return bail(0, "");
+    if (cudaMemset(p->status, 0, sizeof(int)) != cudaSuccess)
+        return bail(OZFFT_ERR_CUDA, "ozfft_plan_many: status word");
     if (!o.no_graph) {
         // capture every class's kernels once; executions replay the graph
         if (cudaStreamCreateWithFlags(&p->capture, cudaStreamNonBlocking) != cudaSuccess)
@@ -1005,8 +1136,11 @@ ozfft_plan_t ozfft_plan_many(const int64_t* lengths, int64_t count, int directio
 int ozfft_execute(ozfft_plan_t p, const void* in, void* out, void* stream)
 {
     if (!p || !in || !out) return fail(OZFFT_ERR_ARG, "ozfft_execute: null argument");
-    if (!p->classes.empty()) return run_many(p, in, out, (cudaStream_t)stream);
-    return run_plan(p, in, out, (cudaStream_t)stream);
+    StageRange range("ozfft_execute");
+    const int rc = p->classes.empty() ? run_plan(p, in, out, (cudaStream_t)stream)
+                                      : run_many(p, in, out, (cudaStream_t)stream);
+    if (rc) return rc;
+    return fault_after_execution(p->status, (cudaStream_t)stream);
 }
 
 int ozfft_set_profiling(ozfft_plan_t p, int enable)
@@ -1069,10 +1203,19 @@ int ozfft_execute_host(ozfft_plan_t p, const void* in, void* out, void* stream)
     if (!p || !in || !out) return fail(OZFFT_ERR_ARG, "ozfft_execute_host: null argument");
     cudaStream_t s = (cudaStream_t)stream;
     const size_t bytes = sizeof(double2) * p->total;
-    if (!p->stage_in) {
-        int rc;
-        if ((rc = dalloc(p, &p->stage_in, p->total))) return rc;
-        if ((rc = dalloc(p, &p->stage_out, p->total))) return rc;
+    StageRange range("ozfft_execute_host");
+    if (!p->stage_in || !p->stage_out) {
+        g_alloc_seq = 0;
+        int rc = OZFFT_OK;
+        if (!p->stage_in) rc = dalloc(p, &p->stage_in, p->total);
+        if (!rc && !p->stage_out) rc = dalloc(p, &p->stage_out, p->total);
+        if (rc) {   // keep neither half: the next call allocates both again
+            const int64_t bytes_each = (int64_t)sizeof(double2) * p->total;
+            if (p->stage_in) { cudaFree(p->stage_in); p->bytes -= bytes_each; }
+            if (p->stage_out) { cudaFree(p->stage_out); p->bytes -= bytes_each; }
+            p->stage_in = p->stage_out = nullptr;
+            return rc;
+        }
     }
     const int parts = (p->classes.empty() && !p->debug && p->B >= 8) ? ozfft_plan_s::HOST_PARTS : 1;
     if (parts == 1) {
@@ -1121,9 +1264,10 @@ int ozfft_execute_host(ozfft_plan_t p, const void* in, void* out, void* stream)
         CUDA_TRY(cudaMemcpyAsync((double2*)out + off, p->stage_out + off, sizeof(double2) * cnt,
                                  cudaMemcpyDeviceToHost, p->cs_out));
     }
+    const int frc = fault_after_execution(p->status, s);
     CUDA_TRY(cudaStreamSynchronize(p->cs_out));
     CUDA_TRY(cudaStreamSynchronize(s));
-    return OZFFT_OK;
+    return frc;
 }
 
 int ozfft_get_status(ozfft_plan_t p, void* stream)
@@ -1143,6 +1287,7 @@ int ozfft_get_status(ozfft_plan_t p, void* stream)
     if (st & ST_NONFINITE) return OZFFT_ERR_NONFINITE;
     if (st & ST_RANGE) return OZFFT_ERR_RANGE;
     if (st & ST_TIMEOUT) return OZFFT_ERR_TIMEOUT;
+    if (st & ST_LEVELS) return OZFFT_ERR_LEVELS;
     return OZFFT_OK;
 }
 
@@ -1153,7 +1298,7 @@ int ozfft_get_stats(ozfft_plan_t p, void* stream, ozfft_stats* out)
     out->n = p->n;
     out->N = p->N;
     out->batch = p->B;
-    out->K = p->K;
+    out->K = p->kinf ? OZFFT_K_INF : p->K;
     out->L = p->L;
     out->nprimes = p->P;
     out->alpha = p->alpha;
@@ -1199,11 +1344,18 @@ const char* ozfft_error_string(int code)
     case OZFFT_ERR_NONFINITE: return "non-finite input";
     case OZFFT_ERR_RANGE: return "input magnitude out of range";
     case OZFFT_ERR_TIMEOUT: return "device wait timed out";
+    case OZFFT_ERR_LEVELS: return "K = infinity: a vector needs more split levels than the cap";
     default: return "unknown error";
     }
 }
 
 const char* ozfft_last_error(void) { return g_last_error.c_str(); }
+
+int ozfft_fault_config(int32_t* kind, int64_t* arg)
+{
+    if (!kind || !arg) return fail(OZFFT_ERR_ARG, "ozfft_fault_config: null argument");
+    return fault_read(kind, arg);
+}
 
 // bit reversal of the low lg bits
 static int64_t bitrev(int64_t v, int lg)

@@ -17,7 +17,8 @@ LIB_PATH = os.path.join(HERE, "libozfft.so")
 
 FORWARD, INVERSE = -1, 1
 ADJOINT, INVERSE_ADJOINT = 2, -2   # F^H x and (1/n) F x: the adjoints of FORWARD and INVERSE
-OK, ERR_ARG, ERR_LENGTH, ERR_ALLOC, ERR_CUDA, ERR_NONFINITE, ERR_RANGE, ERR_TIMEOUT = range(8)
+OK, ERR_ARG, ERR_LENGTH, ERR_ALLOC, ERR_CUDA, ERR_NONFINITE, ERR_RANGE, ERR_TIMEOUT, ERR_LEVELS = range(9)
+K_INF, K_INF_CAP = -1, 8   # K = infinity of the paper (split until the residual is zero), level cap
 DUMP_CHIRP, DUMP_XPRIME, DUMP_MU, DUMP_XRES, DUMP_XSPEC, DUMP_YSPEC, DUMP_SCHED, DUMP_ZRES = range(8)
 MAX_GROUPS, MAX_L = 64, 8
 
@@ -25,7 +26,7 @@ MAX_GROUPS, MAX_L = 64, 8
 EXPORTS = ("ozfft_plan", "ozfft_plan_ex", "ozfft_execute", "ozfft_execute_host", "ozfft_get_status",
            "ozfft_get_stats", "ozfft_set_profiling", "ozfft_get_profile", "ozfft_destroy", "ozfft_error_string",
            "ozfft_last_error", "ozfft_debug_dump", "ozfft_execute_noalloc", "ozfft_plan_many",
-           "ozfft_measure_butterfly_rate", "ozfft_selftest_wait_timeout")
+           "ozfft_measure_butterfly_rate", "ozfft_selftest_wait_timeout", "ozfft_fault_config")
 PROF_SLOTS = ("premul", "split", "schedule", "ntt_fwd_col", "ntt_fwd_row", "ntt_inv_row", "ntt_inv_col", "crt")
 
 
@@ -85,6 +86,8 @@ def load(path: str = LIB_PATH):
             L.ozfft_measure_butterfly_rate.argtypes = [C.c_int, C.POINTER(C.c_double), P]
             L.ozfft_selftest_wait_timeout.restype = C.c_int
             L.ozfft_selftest_wait_timeout.argtypes = [P]
+            L.ozfft_fault_config.restype = C.c_int
+            L.ozfft_fault_config.argtypes = [C.POINTER(C.c_int32), C.POINTER(i64)]
             L.ozfft_plan_many.restype = P
             L.ozfft_plan_many.argtypes = [C.POINTER(i64), i64, C.c_int, C.POINTER(Options)]
             _lib = L
@@ -112,6 +115,7 @@ class Plan:
         lib = load()
         self.n, self.batch, self.direction = int(n), int(batch), int(direction)
         self.K, self.L, self.nprimes, self.merge, self.ts = int(K), int(L), int(nprimes), bool(merge), bool(ts)
+        self.levels = K_INF_CAP if self.K == K_INF else self.K   # level dimension of the buffers
         opt = Options(self.K, self.L, self.nprimes, int(conv_len), int(bool(debug)), int(chunk), int(bool(autotune)), 0,
                       int(self.merge), int(row_log), int(self.ts))
         self._h = lib.ozfft_plan_ex(self.n, self.batch, self.direction, C.byref(opt))
@@ -188,7 +192,9 @@ class Plan:
         got = lib.ozfft_debug_dump(self._h, stage, index, buf.ctypes.data, sp)
         if got < 0:
             _check(-got)
-        N, K, P, G = self.N, self.K, self.nprimes, self.K * self.K
+        N, P = self.N, self.nprimes
+        K = self.levels
+        G = K * K
         if stage == DUMP_CHIRP:
             return buf.view(np.complex128)
         if stage == DUMP_XPRIME:
@@ -223,6 +229,7 @@ class PlanMany(Plan):
         self.lengths = lens
         self.offsets = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
         self.direction, self.K, self.L, self.nprimes = int(direction), int(K), int(L), int(nprimes)
+        self.levels = K_INF_CAP if self.K == K_INF else self.K
         self.merge = bool(merge)
         opt = Options(self.K, self.L, self.nprimes, 0, 0, int(chunk), int(bool(autotune)), int(not graph),
                       int(self.merge), 0, 0)
@@ -245,6 +252,14 @@ def butterfly_rate(inverse=False, stream=None):
     r = C.c_double(0.0)
     _check(load().ozfft_measure_butterfly_rate(int(bool(inverse)), C.byref(r), _stream_ptr(stream)))
     return r.value
+
+
+def fault_config():
+    """(rc, kind, arg) of the host-side fault hook that OZFFT_FAULT selects now
+    (ozfft_fault_config; kind 0 none, 1 alloc, 2 status)."""
+    k, a = C.c_int32(0), C.c_int64(0)
+    rc = load().ozfft_fault_config(C.byref(k), C.byref(a))
+    return rc, k.value, a.value
 
 
 def selftest_wait_timeout(stream=None):

@@ -51,3 +51,39 @@ def test_binding_loads_and_reports_errors_without_gpu(lib):
 def test_kernels_are_built_for_sm_103a():
     # the link step embeds sm_103a SASS; check the build flags rather than the binary
     assert "arch=compute_103a,code=sm_103a" in " ".join(build.NVCC_FLAGS)
+
+
+@pytest.mark.parametrize("value,expect", [
+    (None, (ozfft.OK, 0, 0)),
+    ("", (ozfft.OK, 0, 0)),
+    ("alloc", (ozfft.OK, 1, 0)),
+    ("alloc:3", (ozfft.OK, 1, 3)),
+    ("status:6", (ozfft.OK, 2, 6)),
+    ("status:8", (ozfft.OK, 2, 8)),
+    ("alloc:0", (ozfft.ERR_ARG, 0, 0)),
+    ("alloc:-1", (ozfft.ERR_ARG, 0, 0)),
+    ("status:4", (ozfft.ERR_ARG, 0, 0)),     # not a device status code
+    ("status:9", (ozfft.ERR_ARG, 0, 0)),
+    ("bogus", (ozfft.ERR_ARG, 0, 0)),
+])
+def test_fault_hook_parsing_without_gpu(lib, monkeypatch, value, expect):
+    """OZFFT_FAULT is parsed on the host: the settings the failure tests use and
+    malformed ones, which are argument errors rather than silently ignored."""
+    ozfft.load(build.LIB)
+    if value is None:
+        monkeypatch.delenv("OZFFT_FAULT", raising=False)
+    else:
+        monkeypatch.setenv("OZFFT_FAULT", value)
+    assert ozfft.fault_config() == expect
+    if expect[0] != ozfft.OK:
+        assert b"OZFFT_FAULT" in ozfft.load().ozfft_last_error()
+
+
+def test_plan_creation_rejects_bad_fault_setting_without_gpu(lib, monkeypatch):
+    """A malformed OZFFT_FAULT stops plan creation on the host (before any
+    device allocation) with the hook's message."""
+    L = ozfft.load(build.LIB)
+    monkeypatch.setenv("OZFFT_FAULT", "alloc:x")
+    opt = ozfft.Options(3, 1, 2, 0, 0)
+    assert L.ozfft_plan_ex(1024, 1, ozfft.FORWARD, ctypes.byref(opt)) is None
+    assert b"OZFFT_FAULT" in L.ozfft_last_error()
