@@ -61,6 +61,10 @@ def parse():
     ap.add_argument("--row-log", type=int, default=0,
                     help="force the NTT row pass to 2^row_log residues (profiling runs without plan-time tuning)")
     ap.add_argument("--ts", action="store_true", help="the TS (triple-single) variant of the method")
+    ap.add_argument("--inv-vecs", type=int, default=0,
+                    help="force 1 or 2 vectors per CTA in the inverse row pass (0: default or autotuned)")
+    ap.add_argument("--crt-fuse", type=int, default=0,
+                    help="force the inverse column pass fused with the CRT (1) or apart (2); 0: default or autotuned")
     ap.add_argument("--uneven-count", type=int, default=4096, help="signals of the uneven workload")
     ap.add_argument("--plain-sample", type=int, default=256,
                     help="signals of the uneven workload timed through per-signal plans")
@@ -85,6 +89,7 @@ def workload(a):
                         f"forward, K={a.K}, L={a.L}, {a.nprimes} primes",
             "n": a.n, "batch_per_gpu": a.batch, "K": a.K, "L": a.L, "nprimes": a.nprimes, "seed": a.seed,
             "autotune": a.autotune, "merge": a.merge, "ts": a.ts, "row_log": a.row_log,
+            "inv_vecs": a.inv_vecs, "crt_fuse": a.crt_fuse,
             "l2": "inputs (batch x n x 16 B) exceed L2 each step; no flush"}
 
 
@@ -507,6 +512,7 @@ def run_uneven(a, rank, world, local):
     and L = 1; against the plain pipeline (one batch-1 plan per signal) on a
     sample of the same signals."""
     import numpy as np
+    cpu_pool = OraclePool(host_cores()) if (rank == 0 and not a.skip_cpu) else None
     import torch
     dist = init_dist(world)
     torch.cuda.set_device(local)
@@ -552,11 +558,36 @@ def run_uneven(a, rank, world, local):
         tplan = time.perf_counter() - t0
         ms = timed(lambda: plan.execute(x, y), a.steps)
         st = plan.stats()
+        # whole-step roofline (the graph's kernels of every length class together): modular
+        # multiplications of the NTT butterflies and of the Alg. 8 products, live vectors per
+        # signal taken as the plan's mean, each signal at its own N
+        Ns = np.array([n if n & (n - 1) == 0 else 1 << int(2 * n - 2).bit_length() for n in lens], dtype=np.float64)
+        fwd_v, inv_v = st["ntt_forward_runtime"] / cnt, st["ntt_inverse"] / cnt
+        prods = inv_v * (L if L > 1 else 1)   # products per signal: at most L per group (upper bound)
+        mm = float(np.sum((fwd_v + inv_v) * Ns / 2 * np.log2(Ns) + prods * Ns))
+        peak_alu = 152 * 4 * 32 * 2.07e9 / BUTTERFLY_INSTR / 1e12
+        # stage-minimal bytes per signal (the fused pipeline's count, 856 N at n = N, K = 3, L = 1):
+        # split 32 n + 8 K N, forward NTTs 8 N per vector, MAC reads X and Y (4 N per vector, 2 K P
+        # w~* vectors per signal here), inverse outputs written and read once (4 N each), output 32 n
+        wv = 2 * a.K * a.nprimes
+        alg_bytes = float(np.sum(64 * lens + Ns * (8 * a.K + 8 * fwd_v + 4 * fwd_v + 4 * wv + 8 * inv_v)))
+        pk = peaks()
         r = {"value": job_value(a.steps, cnt, world, ms), "unit": "signal/s", "ms_per_step": ms / a.steps,
+             "roofline": {"bound": "alu", "kernel": "whole step (CUDA graph of every length class)",
+                          "achieved": mm / (ms / a.steps / 1e3) / 1e12, "peak": peak_alu, "unit": "Tmodmul/s",
+                          "frac": mm / (ms / a.steps / 1e3) / 1e12 / peak_alu, "traffic": None,
+                          "modmuls_per_step": mm,
+                          "hbm_view": {"algorithmic_bytes_per_step": alg_bytes,
+                                       "achieved": alg_bytes / (ms / a.steps / 1e3) / 1e9,
+                                       "peak": pk["hbm_gbs"] if pk else 6800.0, "unit": "GB/s"},
+                          "note": "live vectors per signal are the plan's means; products per group counted "
+                                  "as L (an upper bound for L > 1)"},
              "bytes_per_s": 2 * 16 * total * world * a.steps / (ms / 1e3), "status_ok": plan.status() == ozfft.OK,
              "plan_seconds": tplan, "workspace_GB": st["workspace_bytes"] / 1e9,
              "ntt_runtime_per_signal": (st["ntt_forward_runtime"] + st["ntt_inverse"]) / cnt,
-             "gpu_launches_per_step": st["kernel_launches"]}
+             "gpu_launches_per_step": st["kernel_launches"],
+             "tuning": {"classes": st["classes"], "crt_fused_classes": st["crt_fused_classes"],
+                        "inv_vecs_largest_class": st["inv_vecs"], "row_log_inv_largest_class": st["row_log_inv"]}}
         if rank == 0 and not a.skip_cpu:
             yh = y.cpu().numpy()
             xs, ys = plan.split(xh), plan.split(yh)
@@ -595,6 +626,20 @@ def run_uneven(a, rank, world, local):
     ys_ = y[:offs[m]]
     sms = timed(lambda: sub.execute(xs_, ys_), psteps)
     del sub
+    cpu = None
+    if cpu_pool is not None:
+        # the oracle on a seeded sample of the same signals, one process per host core
+        rng = np.random.default_rng(11)
+        pick = rng.choice(cnt, size=min(cnt, 4 * cpu_pool.workers), replace=False)
+        xs_all = [xh[offs[i]:offs[i + 1]] for i in pick]
+        t0 = time.perf_counter()
+        cpu_pool.run(xs_all, a.K, 3, a.nprimes)
+        dt = time.perf_counter() - t0
+        cpu_pool.close()
+        cpu = {"value": len(pick) / dt, "unit": "signal/s", "cores": cpu_pool.workers, "kind": "oracle",
+               "cpu_model": cpu_model(),
+               "sample": f"{len(pick)} signals drawn (seed 11) from the {cnt} of the workload, L=3, one "
+                         f"single-threaded C oracle process per host core, one timed run"}
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -612,7 +657,8 @@ def run_uneven(a, rank, world, local):
             "plain": {"signals": m, "value": job_value(psteps, m, world, pms), "unit": "signal/s",
                       "executions_per_step": m},
             "uneven_plan_same_sample": {"signals": m, "value": job_value(psteps, m, world, sms), "unit": "signal/s"},
-            "clocks": clk}
+            "roofline": out["L=3"]["roofline"], "cpu_baseline": cpu,
+            "tuning": out["L=3"]["tuning"], "clocks": clk}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -676,7 +722,7 @@ def main():
     y = torch.empty_like(x)
     stream = torch.cuda.current_stream(dev)
     plan = ozfft.Plan(n, B, ozfft.FORWARD, K=a.K, L=a.L, nprimes=a.nprimes, autotune=a.autotune, merge=a.merge,
-                      ts=a.ts, row_log=a.row_log)
+                      ts=a.ts, row_log=a.row_log, inv_vecs=a.inv_vecs, crt_fuse=a.crt_fuse)
 
     # ---- batched, device-resident (the headline value), with per-kernel events
     for _ in range(a.warmup):
@@ -708,7 +754,7 @@ def main():
     plain = None
     if not a.skip_plain:
         p1 = ozfft.Plan(n, 1, ozfft.FORWARD, K=a.K, L=a.L, nprimes=a.nprimes, autotune=a.autotune, merge=a.merge,
-                        ts=a.ts, row_log=a.row_log)
+                        ts=a.ts, row_log=a.row_log, inv_vecs=a.inv_vecs, crt_fuse=a.crt_fuse)
         xs = [x[i:i + 1] for i in range(B)]
         ys = [y[i:i + 1] for i in range(B)]
         for _ in range(a.warmup):
@@ -771,13 +817,28 @@ def main():
                     "h2d_d2h_concurrent_each": nbytes / (both_ms / 1e3) / 1e9, "bytes": nbytes,
                     "how": "best of 5 pinned copies of one step's input (and output), CUDA events"}
         del dbuf
+        esteps = max(20, a.steps)
+        # synchronous calls (ozfft_execute_host: a four-part pipeline inside each call)
         for _ in range(a.warmup):
             plan.execute_host(x_pin, out_pin)
-        esteps = max(20, a.steps)
+        barrier()
+        call_ms = []
+        t0 = time.perf_counter()
+        for _ in range(esteps):
+            tc = time.perf_counter()
+            plan.execute_host(x_pin, out_pin)
+            call_ms.append(1e3 * (time.perf_counter() - tc))
+        dt_sync = rank_max(time.perf_counter() - t0)
+        # asynchronous calls (ozfft_execute_host_async: each call's copies overlap the
+        # neighbouring calls' computation), all waited for inside the timed region
+        for _ in range(a.warmup):
+            plan.execute_host_async(x_pin, out_pin)
+        plan.host_wait()
         barrier()
         t0 = time.perf_counter()
         for _ in range(esteps):
-            plan.execute_host(x_pin, out_pin)
+            plan.execute_host_async(x_pin, out_pin)
+        plan.host_wait()
         dt = rank_max(time.perf_counter() - t0)
         # device time of the kernels inside those calls (per-kernel events, all four parts)
         plan.profile()
@@ -806,12 +867,23 @@ def main():
             t_in += nb * r_in
             t_comp = max(t_comp, t_in) + nb * dev_ms / B
             t_out = max(t_out, t_comp) + nb * r_out
+        # async steady state: a step costs the longest of device time, copy in and copy out,
+        # and the first copy in and the last copy out are exposed once per run
+        model_async = max(dev_ms, h2d_ms, d2h_ms) + (h2d_ms + d2h_ms) / esteps
         e2e = {"value": job_value(esteps, B, world, 1e3 * dt), "unit": UNIT, "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": nbytes, "steps": esteps, "ms_per_step": 1e3 * dt / esteps,
+               "api": "ozfft_execute_host_async per step, ozfft_execute_host_wait at the end (copies in and "
+                      "out of every step inside the timed region)",
+               "model_ms_per_step": model_async,
+               "model": "max(device step, copy in, copy out) + (copy in + copy out) / steps",
                "copy_gbs": copy_gbs,
-               "model_ms_per_step": t_out,
-               "kernel_ms_per_step_in_pipeline": host_kernel_ms,
-               "model": "four-part pipeline from the measured copy times and the device step time",
+               "sync": {"value": job_value(esteps, B, world, 1e3 * dt_sync), "ms_per_step": 1e3 * dt_sync / esteps,
+                        "api": "ozfft_execute_host per step (returns after its copy out)",
+                        "model_ms_per_step": t_out,
+                        "model": "four-part pipeline inside a call from the measured copy times and the device "
+                                 "step time",
+                        "kernel_ms_per_step_in_pipeline": host_kernel_ms,
+                        "call_ms": {"min": min(call_ms), "median": statistics.median(call_ms), "max": max(call_ms)}},
                "host": {"cpu_model": cpu_model(), "cores": host_cores(),
                         "gpu_numa_node": loc["gpu_numa_node"],
                         "thread_cpus": len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else None,
@@ -934,6 +1006,8 @@ def main():
                 "row_pass_stages": {"forward": m2f, "inverse": m2i},
                 "GBps_algorithmic": total_ntt * 8 * N / (ntt_ms / 1e3) / 1e9},
         "kernel_ms_per_step": breakdown, "accuracy": acc,
+        "tuning": {"row_log_fwd": stats["row_log_fwd"], "row_log_inv": stats["row_log_inv"],
+                   "inv_vecs": stats["inv_vecs"], "crt_fused": bool(stats["crt_fused_classes"])},
     }
     print(json.dumps(line), flush=True)
     if dist:

@@ -112,6 +112,15 @@ typedef struct {
                          accumulated per real convolution with TSAdd, the post-multiply in TS and
                          the result rounded to binary64.  Two primes, plain plans only; inputs
                          must stay inside the binary32 exponent range (else OZFFT_ERR_RANGE) */
+    int32_t inv_vecs; /* inverse NTT row pass with the Alg. 8 sums formed in registers (L = 1 or
+                         merged schedules, N >= 2^12, row tiles up to 2^12): vectors of one prime per
+                         CTA, sharing every twiddle load.  0: 2 where it applies (or the autotuner's
+                         choice), 1 or 2 to force; results are bit-identical */
+    int32_t crt_fuse; /* inverse NTT column pass fused with Garner's CRT and the exact accumulation
+                         (two primes, 4..8 column stages): 0 = default (fused for plain plans,
+                         separate kernels for the length classes of uneven plans, or the
+                         autotuner's choice per class), 1 = fused wherever supported, 2 = never
+                         fused; results are bit-identical */
 } ozfft_options;
 
 /* Create a plan for `batch` transforms of length n in `direction`, with default
@@ -157,6 +166,23 @@ int ozfft_execute(ozfft_plan_t plan, const void* in, void* out, void* stream);
    copies and the overlap. */
 int ozfft_execute_host(ozfft_plan_t plan, const void* in, void* out, void* stream);
 
+/* Throughput form of ozfft_execute_host: enqueues the copy of `in` (host) to the
+   plan's device staging buffer on an internal stream, the transform of the whole
+   batch on `stream`, and the copy of the result to `out` (host) on a second
+   internal stream, and returns without waiting.  Consecutive calls overlap: a
+   call's copy in runs while the previous call computes (it waits only until
+   that call's pre-multiply has read the staging buffer), and its copy out runs
+   while the next call computes (whose CRT stage waits for it before writing
+   the staging buffer).  `in` and `out` must stay valid and untouched until
+   ozfft_execute_host_wait returns; with pinned host memory the copies are
+   asynchronous.  A plan over uneven lengths, or a debug plan, runs
+   ozfft_execute_host instead (synchronous). */
+int ozfft_execute_host_async(ozfft_plan_t plan, const void* in, void* out, void* stream);
+
+/* Wait until every ozfft_execute_host_async call of the plan has completed (its
+   result is in its `out`), and until `stream` has synchronized. */
+int ozfft_execute_host_wait(ozfft_plan_t plan, void* stream);
+
 /* Synchronize `stream`, return the data-dependent status recorded by the
    executions since the previous call (OZFFT_OK, OZFFT_ERR_NONFINITE,
    OZFFT_ERR_RANGE, OZFFT_ERR_TIMEOUT or OZFFT_ERR_LEVELS, in that order of
@@ -176,6 +202,11 @@ typedef struct {
     int64_t workspace_bytes;      /* device memory held by the plan */
     int32_t row_log_fwd;          /* forward NTT: stages in the row pass (the rest in the column pass) */
     int32_t row_log_inv;          /* inverse NTT: stages in the row pass (uneven plans: of the largest N) */
+    int32_t inv_vecs;             /* vectors per CTA of the inverse row pass (uneven plans: of the largest
+                                     N; 1 where the two-vector kernel does not apply) */
+    int32_t crt_fused_classes;    /* length classes (1 for a plain plan) whose inverse column pass runs
+                                     fused with the CRT */
+    int32_t classes;              /* length classes (1 for a plain plan) */
 } ozfft_stats;
 int ozfft_get_stats(ozfft_plan_t plan, void* stream, ozfft_stats* out);
 

@@ -946,8 +946,11 @@ __global__ void __launch_bounds__(FC_THREADS, 4) colcrt_kernel(CrtArgs a, int m2
         }
         asm volatile("cp.async.commit_group;" ::: "memory");
     };
-#pragma unroll
-    for (int i = 0; i < FC_STAGES - 1; ++i) issue(i);
+    static_assert(FC_STAGES == 2, "the copies of step i + 1 go to the buffer step i - 1 used");
+    issue(0);
+    // stages 1 and 0 (the register round): table entries 1 and 2 are 1 (block 0
+    // of stages 0 and 1), entry 3 is w^(N/4), the same for every step
+    const uint2 w3_0 = __ldg(tw0 + 3), w3_1 = __ldg(tw1 + 3);
     Acc192 acc[FC_E];
     __shared__ double s_yr[FC_E][FC_THREADS];           // the real parts, kept out of the registers
 #pragma unroll
@@ -956,9 +959,10 @@ __global__ void __launch_bounds__(FC_THREADS, 4) colcrt_kernel(CrtArgs a, int m2
         s_yr[e][threadIdx.x] = 0.0;
     }
     for (int i = 0; i < nsteps; ++i) {
-        issue(i + FC_STAGES - 1);
-        asm volatile("cp.async.wait_group %0;" ::"n"(FC_STAGES - 1) : "memory");
-        __syncthreads();                                  // step i's tiles are in shared memory
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        __syncthreads();                                  // step i's tiles are in shared memory, and every
+                                                          // thread is done with step i - 1's buffer
+        issue(i + 1);                                     // into that buffer, during this step's arithmetic
         uint32_t* st = fc_sm + (i % FC_STAGES) * SW;
         if constexpr (REG01) fc_rounds_hi<M1, LOG_T, 2 * TB>(st, tw0, tw1);   // ends with a barrier
         else fc_rounds<M1, LOG_T, 2 * TB, 0>(st, tw0, tw1);
@@ -977,8 +981,12 @@ __global__ void __launch_bounds__(FC_THREADS, 4) colcrt_kernel(CrtArgs a, int m2
                     v0[u] = gp[o];
                     v1[u] = gp[PW + o];
                 }
-                radix_group<true, 2>(v0, tw0, 1, P0);     // stages 1 and 0 (table entries 1..3)
-                radix_group<true, 2>(v1, tw1, 1, P1);
+                // stage 1: (0, 1) with entry 2 = 1, (2, 3) with entry 3; stage 0: (0, 2) and
+                // (1, 3) with entry 1 = 1 (a unit twiddle: the difference reduced mod p)
+                bfly_gs_unit(v0[0], v0[1], P0); bfly_gs(v0[2], v0[3], w3_0, P0);
+                bfly_gs_unit(v1[0], v1[1], P1); bfly_gs(v1[2], v1[3], w3_1, P1);
+                bfly_gs_unit(v0[0], v0[2], P0); bfly_gs_unit(v0[1], v0[3], P0);
+                bfly_gs_unit(v1[0], v1[2], P1); bfly_gs_unit(v1[1], v1[3], P1);
             } else {
 #pragma unroll
                 for (int e = 0; e < FC_E; ++e) {
@@ -1015,7 +1023,6 @@ __global__ void __launch_bounds__(FC_THREADS, 4) colcrt_kernel(CrtArgs a, int m2
                 }
             }
         }
-        __syncthreads();                                  // the stage is read before it is refilled
     }
     asm volatile("cp.async.wait_group 0;" ::: "memory");
     if (!fast) return;
@@ -1063,7 +1070,16 @@ cudaError_t launch_colcrt(const CrtArgs& a, int m1, int m2, const uint2* tw, cud
 {
     cudaError_t e = crt_init();
     if (e != cudaSuccess) return e;
-    if (a.sd) return cudaErrorInvalidValue;   // plans over uneven lengths keep the unfused kernels
+    if (a.sd) {   // a length class of a plan over uneven lengths: per-signal lengths and outputs
+        switch (m1) {
+        case 4: return launch_colcrt_m<true, 4>(a, m2, tw, s);
+        case 5: return launch_colcrt_m<true, 5>(a, m2, tw, s);
+        case 6: return launch_colcrt_m<true, 6>(a, m2, tw, s);
+        case 7: return launch_colcrt_m<true, 7>(a, m2, tw, s);
+        case 8: return launch_colcrt_m<true, 8>(a, m2, tw, s);
+        default: return cudaErrorInvalidValue;
+        }
+    }
     switch (m1) {
     case 4: return launch_colcrt_m<false, 4>(a, m2, tw, s);
     case 5: return launch_colcrt_m<false, 5>(a, m2, tw, s);

@@ -56,6 +56,14 @@ __device__ __forceinline__ void bfly_gs(uint32_t& a, uint32_t& b, uint2 w, uint3
     b = shoup(a - b + p, w.x, w.y, p);
     a = s;
 }
+// the same with W = 1 (block 0 of a stage): (a - b) mod p, the value the Shoup
+// product by 1 gives
+__device__ __forceinline__ void bfly_gs_unit(uint32_t& a, uint32_t& b, uint32_t p)
+{
+    const uint32_t s = mod_add(a, b, p);
+    b = mod_sub(a, b, p);
+    a = s;
+}
 
 // RL stages on v[0 .. 2^RL) in registers; the stage-j twiddles are
 // tw[(B0 << j) + q], q < 2^j (q = sub-block of the element).  All 2^RL - 1 of
@@ -434,6 +442,186 @@ __device__ __forceinline__ void row_inv_mac(uint32_t* sm, uint32_t* __restrict__
     }
 }
 
+// ----------------------------------------------- inverse row pass, V vectors
+// The same inverse row pass (MAC in registers, a full tile of ROWS rows) on V
+// vectors that use one prime: every twiddle a thread loads serves the V
+// vectors' groups at once, and the V groups' butterflies give the scheduler
+// V independent chains.  V = 2 halves the twiddle loads and the index work per
+// residue (the vectors' tiles sit TW words apart in shared memory).
+template <int RL, int V>
+__device__ __forceinline__ void radix_group_inv_v(uint32_t (&x)[V][1 << RL], const uint2* __restrict__ tw, int B0,
+                                                  uint32_t p)
+{
+    constexpr int R = 1 << RL;
+    uint2 w[R];
+    w[1] = __ldg(tw + B0);
+#pragma unroll
+    for (int j = 1; j < RL; ++j)
+#pragma unroll
+        for (int q = 0; q < (1 << j); q += 2) {
+            const uint4 t = __ldg(reinterpret_cast<const uint4*>(tw + (B0 << j) + q));
+            w[(1 << j) + q] = make_uint2(t.x, t.y);
+            w[(1 << j) + q + 1] = make_uint2(t.z, t.w);
+        }
+#pragma unroll
+    for (int j = RL - 1; j >= 0; --j) {
+        const int half = R >> (j + 1);
+#pragma unroll
+        for (int u = 0; u < R; ++u) {
+            if (u & half) continue;
+            const int q = u >> (RL - j);
+#pragma unroll
+            for (int i = 0; i < V; ++i) bfly_gs(x[i][u], x[i][u + half], w[(1 << j) + q], p);
+        }
+    }
+}
+
+// middle round of the inverse row pass on V tiles (the row_round index map)
+template <int ML, int S0, int RL, int V, int TW, int ROWS>
+__device__ __forceinline__ void row_round_inv_v(uint32_t* sm, int rbase, const uint2* __restrict__ tw, uint32_t p)
+{
+    constexpr int LOG_H = ML - S0 - RL, H = 1 << LOG_H, LOG_GPC = ML - RL, R = 1 << RL;
+    constexpr bool PERM = LOG_H == 4 && ML - S0 >= 6 && ML - S0 <= 8;
+    constexpr int D = 9 - (ML - S0);
+    constexpr int ngroups = ROWS << LOG_GPC;
+#pragma unroll 1
+    for (int gid = threadIdx.x; gid < ngroups; gid += NTT_THREADS) {
+        int grp = ROWS == 1 ? gid : gid & ((1 << LOG_GPC) - 1);
+        if constexpr (PERM) {
+            const int b = grp >> 4;
+            const int sw = (b ^ (b >> D)) & 1;
+            grp ^= (sw | (sw << D)) << 4;
+        }
+        const int c = ROWS == 1 ? 0 : gid >> LOG_GPC;
+        const int blk = grp >> LOG_H;
+        const int base = (c << ML) + (blk << (ML - S0)) + (grp & (H - 1));
+        uint32_t x[V][R];
+#pragma unroll
+        for (int i = 0; i < V; ++i) {
+            const uint32_t* s = sm + i * TW + pad_idx(base);
+#pragma unroll
+            for (int u = 0; u < R; ++u) x[i][u] = s[u * H + (u * H) / 32];
+        }
+        radix_group_inv_v<RL, V>(x, tw, ((rbase + c) << S0) + blk, p);
+#pragma unroll
+        for (int i = 0; i < V; ++i) {
+            uint32_t* s = sm + i * TW + pad_idx(base);
+#pragma unroll
+            for (int u = 0; u < R; ++u) s[u * H + (u * H) / 32] = x[i][u];
+        }
+    }
+}
+
+template <int ML, int V, int TW, int ROWS, int I>
+__device__ __forceinline__ void inv_middle_rounds_v(uint32_t* sm, int rbase, const uint2* tw, uint32_t p)
+{
+    if constexpr (I < Part<ML>::NR - 1) {
+        constexpr int R_ = Part<ML>::NR - 1 - I;
+        row_round_inv_v<ML, Part<ML>::start(R_), Part<ML>::size(R_), V, TW, ROWS>(sm, rbase, tw, p);
+        __syncthreads();
+        inv_middle_rounds_v<ML, V, TW, ROWS, I + 1>(sm, rbase, tw, p);
+    }
+}
+
+// one CTA: rows [row0, row0 + RPC) of the V vectors vbase + i P (i < V), which
+// share the prime vbase mod P; nvec is a multiple of V P
+constexpr int INV_PAIR_V = INV_ROW_VECS;
+template <int M2, bool MERGED>
+__global__ void __launch_bounds__(NTT_THREADS, 6) ntt_inv_row_v_kernel(NttGeom g, uint32_t* __restrict__ data,
+                                                                      const uint2* __restrict__ tw_all, MacSrc mac)
+{
+    constexpr int V = INV_PAIR_V;
+    constexpr int RPC = 1 << (TILE_LOG - M2);
+    constexpr int TW = (RPC << M2) + ((RPC << M2) >> 5);      // words of one vector's padded tile
+    using PT = Part<M2>;
+    extern __shared__ uint32_t sm[];
+    const int lg_rb = g.lgN - TILE_LOG;                     // row blocks per vector = 2^lg_rb
+    const unsigned k = blockIdx.x >> lg_rb;
+    const int row0 = (int)(blockIdx.x & ((1u << lg_rb) - 1)) * RPC;
+    const unsigned P = (unsigned)g.P;
+    const unsigned vbase = (k / P) * (V * P) + (k % P);
+    const int pi = (int)(k % P);
+    const uint32_t p = prime_of(pi);
+    const uint2* tw = tw_all + (int64_t)pi * g.N;
+    const int rbase = (1 << g.m1) + row0;
+    const int64_t j0 = (int64_t)row0 << M2;
+    MacVec mv[V];
+    bool live[V];
+    bool any = false;
+    const uint32_t* xrow[V];   // unmerged (one product): the rows of X_s and Ym_t this CTA reads
+    const uint32_t* yrow[V];
+#pragma unroll
+    for (int i = 0; i < V; ++i) {
+        const unsigned vec = vbase + i * P;
+        live[i] = inv_live(g, vec);
+        any = any || live[i];
+        mv[i] = mac_decode(g, vec, mac.ym_stride);
+        int64_t xo = 0, yo = 0;
+        if (!MERGED && mv[i].n > 0) mac_offsets<false>(mv[i], 0, xo, yo);
+        xrow[i] = mac.X + xo + j0;
+        yrow[i] = mac.Ym + yo + j0;
+    }
+    if (!any) return;
+    const uint32_t pn = pneg_inv_of(pi);
+    {   // first round: groups of 2^RL contiguous residues, the Alg. 8 sums formed from X and Ym
+        constexpr int R_ = PT::NR - 1, S0 = PT::start(R_), RL = PT::size(R_), R = 1 << RL, LOG_GPC = M2 - RL;
+        static_assert(S0 + RL == M2 && RL >= 2 && RL <= 4, "first inverse round: contiguous groups");
+#pragma unroll 1
+        for (int gid = threadIdx.x; gid < (RPC << LOG_GPC); gid += NTT_THREADS) {
+            const int grp = RPC == 1 ? gid : gid & ((1 << LOG_GPC) - 1), c = RPC == 1 ? 0 : gid >> LOG_GPC;
+            const int base = (c << M2) + (grp << RL);
+            uint32_t x[V][R];
+#pragma unroll
+            for (int i = 0; i < V; ++i)
+#pragma unroll
+                for (int q = 0; q < R; q += 4) {
+                    uint4 t = make_uint4(0u, 0u, 0u, 0u);
+                    if (MERGED) {
+                        if (live[i]) t = mac_sum4<true>(mv[i], mac, j0 + base + q);
+                    } else if (live[i]) {
+                        const uint4 a = __ldg(reinterpret_cast<const uint4*>(xrow[i] + base + q));
+                        const uint4 b = __ldg(reinterpret_cast<const uint4*>(yrow[i] + base + q));
+                        t = make_uint4(mont_mul(a.x, b.x, p, pn), mont_mul(a.y, b.y, p, pn),
+                                       mont_mul(a.z, b.z, p, pn), mont_mul(a.w, b.w, p, pn));
+                    }
+                    x[i][q] = t.x; x[i][q + 1] = t.y; x[i][q + 2] = t.z; x[i][q + 3] = t.w;
+                }
+            radix_group_inv_v<RL, V>(x, tw, ((rbase + c) << S0) + grp, p);
+#pragma unroll
+            for (int i = 0; i < V; ++i) {
+                uint32_t* s = sm + i * TW + pad_idx(base);
+#pragma unroll
+                for (int u = 0; u < R; ++u) s[u] = x[i][u];
+            }
+        }
+    }
+    __syncthreads();
+    inv_middle_rounds_v<M2, V, TW, RPC, 1>(sm, rbase, tw, p);
+    {   // last round: stride 2^(M2 - RL), stored straight to HBM
+        constexpr int RL = PT::size(0), R = 1 << RL, LOG_H = M2 - RL, H = 1 << LOG_H;
+#pragma unroll 1
+        for (int gid = threadIdx.x; gid < (RPC << LOG_H); gid += NTT_THREADS) {
+            const int l0 = RPC == 1 ? gid : gid & (H - 1), c = RPC == 1 ? 0 : gid >> LOG_H;
+            const int base = (c << M2) + l0;
+            uint32_t x[V][R];
+#pragma unroll
+            for (int i = 0; i < V; ++i) {
+                const uint32_t* s = sm + i * TW + pad_idx(base);
+#pragma unroll
+                for (int u = 0; u < R; ++u) x[i][u] = s[u * H + (u * H) / 32];
+            }
+            radix_group_inv_v<RL, V>(x, tw, rbase + c, p);
+#pragma unroll
+            for (int i = 0; i < V; ++i) {
+                if (!live[i]) continue;
+                uint32_t* out = data + ((int64_t)(vbase + i * P) << g.lgN) + j0 + base;
+#pragma unroll
+                for (int u = 0; u < R; ++u) out[u * H] = x[i][u];
+            }
+        }
+    }
+}
+
 // 10 CTAs per SM (48 registers); the inverse pass with the MAC in registers
 // needs 56 (9 CTAs) to stay free of spills
 template <bool INV, bool MAC, int M2>
@@ -570,9 +758,37 @@ cudaError_t launch_col_m(const NttGeom& g, uint32_t* data, const uint2* tw, cuda
     return cudaGetLastError();
 }
 
+// the V-vector inverse row pass applies to full tiles of one vector (2^12 <= N,
+// rows of 2^5 .. 2^12 residues) with the MAC in registers and whole groups of
+// V vectors per prime
+inline bool inv_row_v_ok(const NttGeom& g, int M2)
+{
+    return g.mac_reg && M2 >= 5 && M2 <= TILE_LOG && g.lgN >= TILE_LOG && g.nvec % (INV_PAIR_V * g.P) == 0;
+}
+
+template <int M2>
+cudaError_t launch_inv_row_v(const NttGeom& g, uint32_t* data, const uint2* tw, MacSrc mac, cudaStream_t s)
+{
+    const size_t smem = (size_t)INV_PAIR_V * ntt_smem_for(int64_t(1) << TILE_LOG);
+    const int64_t grid = (g.nvec / INV_PAIR_V) << (g.lgN - TILE_LOG);
+    if (g.merged) {
+        cudaError_t e = ntt_prep(ntt_inv_row_v_kernel<M2, true>, smem);
+        if (e != cudaSuccess) return e;
+        ntt_inv_row_v_kernel<M2, true><<<(unsigned)grid, NTT_THREADS, smem, s>>>(g, data, tw, mac);
+    } else {
+        cudaError_t e = ntt_prep(ntt_inv_row_v_kernel<M2, false>, smem);
+        if (e != cudaSuccess) return e;
+        ntt_inv_row_v_kernel<M2, false><<<(unsigned)grid, NTT_THREADS, smem, s>>>(g, data, tw, mac);
+    }
+    return cudaGetLastError();
+}
+
 template <bool INV, bool MAC, int M2>
 cudaError_t launch_row_m(const NttGeom& g, uint32_t* data, const uint2* tw, MacSrc mac, cudaStream_t s)
 {
+    if constexpr (INV && MAC && M2 >= 5 && M2 <= TILE_LOG) {
+        if (g.inv_vecs_per_cta == INV_PAIR_V && inv_row_v_ok(g, M2)) return launch_inv_row_v<M2>(g, data, tw, mac, s);
+    }
     constexpr int RPC = M2 <= TILE_LOG ? (1 << (TILE_LOG - M2)) : 1;
     constexpr int64_t tile = (int64_t(1) << M2) * RPC;
     const size_t smem = ntt_smem_for(tile);

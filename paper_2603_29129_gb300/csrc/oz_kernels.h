@@ -42,6 +42,8 @@ struct NttGeom {
     int merged;            // schedules merge the two convolutions of each output part
     int mac_reg;           // L = 1 or merged schedules: the inverse row pass forms the Alg. 8
                            // sums in registers instead of staging them in shared memory
+    int inv_vecs_per_cta;  // inverse row pass with the MAC in registers: vectors of one prime
+                           // per CTA (1, or 2 to share every twiddle load between two vectors)
     const CUtensorMap* tmap;   // column pass by tensor memory access: [vectors][2^m1][2^m2] map of the
                                // buffer (null: per-thread loads); host memory, passed by value
     int64_t vec0;          // index of the launch's first vector in that map
@@ -58,6 +60,10 @@ bool launch_col_tma(bool inv, const NttGeom& g, const uint2* tw, cudaStream_t s,
 // self-test of the bounded wait: one forward column-pass tile (N = 2^16) whose
 // barrier expects more bytes than its copy brings; *status receives the status bits
 cudaError_t col_tma_timeout_selftest(int* status_host, cudaStream_t s);
+
+// vectors of one prime per CTA of the inverse row pass with the MAC in registers
+// when the plan does not choose (the autotuner times 1 and 2)
+constexpr int INV_ROW_VECS = 2;
 
 // Inputs of the multiply-accumulate fused into the inverse NTT's load.
 struct MacSrc {

@@ -132,6 +132,9 @@ struct ozfft_plan_s {
     int64_t n = 0, N = 0, B = 0;
     int direction = -1, K = 3, L = 1, P = 2, alpha = 0, G = 9, debug = 0, merge = 0, ts = 0;
     int kinf = 0;                // K = infinity: K holds the level cap MAX_K
+    int crt_fused = 1;           // inverse column pass fused with the CRT where colcrt_supported
+    int tune_vecs = 1;           // the autotuner may choose the inverse row pass's vectors per CTA
+    int tune_fuse = 1;           // ... and whether the inverse column pass is fused with the CRT
     int garner_u = 0;            // every convolution value |z| < p0 p1 / 2 - p0 (CRT without centering z0)
     int64_t chunk = 1;           // signals per inverse-stage chunk (Z holds one chunk)
     int device = 0;
@@ -162,6 +165,12 @@ struct ozfft_plan_s {
     static constexpr int HOST_PARTS = 4;
     cudaStream_t cs_in = nullptr, cs_out = nullptr;
     cudaEvent_t ev_go = nullptr, ev_in[HOST_PARTS] = {}, ev_done[HOST_PARTS] = {};
+    // asynchronous host-buffer executions (ozfft_execute_host_async): the previous call's
+    // premultiply (done reading stage_in) and copy out (done reading stage_out)
+    cudaEvent_t ev_a_premul = nullptr, ev_a_in = nullptr, ev_a_done = nullptr, ev_a_out = nullptr;
+    bool async_pending = false;      // an asynchronous call may still be copying out
+    cudaEvent_t rec_after_premul = nullptr;   // run_plan_range: record after the premultiply
+    cudaEvent_t wait_before_out = nullptr;    // run_plan_range: wait before the first kernel writing out
     bool executed = false;
     int64_t total = 0;           // complex elements per execution (B n, or the packed lengths)
     int64_t fwd_plan = 0;        // forward NTTs of the w~* slices
@@ -428,6 +437,8 @@ static void plan_free(ozfft_plan_s* p)
     if (p->cs_in) cudaStreamDestroy(p->cs_in);
     if (p->cs_out) cudaStreamDestroy(p->cs_out);
     if (p->ev_go) cudaEventDestroy(p->ev_go);
+    for (cudaEvent_t e : {p->ev_a_premul, p->ev_a_in, p->ev_a_done, p->ev_a_out})
+        if (e) cudaEventDestroy(e);
     for (int i = 0; i < ozfft_plan_s::HOST_PARTS; ++i) {
         if (p->ev_in[i]) cudaEventDestroy(p->ev_in[i]);
         if (p->ev_done[i]) cudaEventDestroy(p->ev_done[i]);
@@ -571,6 +582,7 @@ static int plan_build(ozfft_plan_s* p)
     p->geom_fwd.G = p->G;
     p->geom_fwd.merged = p->merge;
     p->geom_fwd.mac_reg = p->L == 1 || p->merge;   // measured: staged loads win only for unmerged L > 1
+    p->geom_fwd.inv_vecs_per_cta = INV_ROW_VECS;
     p->geom_inv = p->geom_fwd;
 
     // chirp tables, then w~* split + forward NTTs (§4.5: precomputed once); the
@@ -671,6 +683,7 @@ static int force_split(ozfft_plan_s* p, int m2)
         return fail(OZFFT_ERR_ARG, "ozfft_plan: no kernel for a row pass of 2^" + std::to_string(m2) + " residues");
     p->geom_fwd.nvec = gf.nvec; p->geom_fwd.kcnt = gf.kcnt; p->geom_fwd.sched = gf.sched;
     p->geom_inv.nvec = gi.nvec; p->geom_inv.kcnt = gi.kcnt; p->geom_inv.sched = gi.sched;
+    p->geom_inv.inv_vecs_per_cta = gi.inv_vecs_per_cta;
     const int64_t nchunks = (p->B + p->chunk - 1) / p->chunk;
     p->launches = 1 + (p->ts ? p->K : SPLIT_SPEC_LAUNCHES) + 1 + ntt_launches(p->geom_fwd) +
                   nchunks * (ntt_launches(p->geom_inv) + (p->ts ? 1 : crt_launches()));
@@ -681,8 +694,11 @@ static int force_split(ozfft_plan_s* p, int m2)
 // Autotuning (ozfft_options.autotune): time every supported split of the
 // plan's NTT length into column and row passes, forward and inverse, on the
 // plan's own buffers with every vector live, and keep the fastest of each.
-// The split changes only the order in which the same butterflies run, so the
-// results are bit-identical.
+// The inverse side is timed with what follows it: the inverse column pass
+// fused with the CRT or the column pass and the CRT apart (each where allowed),
+// so the split and the fusion are chosen together; then, at that choice, one
+// or two vectors per CTA in the inverse row pass.  Each choice changes only
+// the order in which the same operations run, so results are bit-identical.
 static int autotune_ntt(ozfft_plan_s* p)
 {
     StageRange range("ozfft_autotune");
@@ -697,10 +713,12 @@ static int autotune_ntt(ozfft_plan_s* p)
         if (ntt_configure_split(g, p->N, lg) && std::find(cands.begin(), cands.end(), lg) == cands.end())
             cands.push_back(lg);
     }
-    if (cands.size() < 2) return OZFFT_OK;
+    if (std::find(cands.begin(), cands.end(), p->geom_inv.m2) == cands.end()) cands.push_back(p->geom_inv.m2);
     const int64_t B = p->B, K = p->K, G = p->G;
-    // every vector live: K levels, G groups of one product (s, t) each
-    std::vector<int32_t> kc((size_t)B * 2, (int32_t)K);
+    // every vector live: K levels, G groups of one product (s, t) each, all
+    // scales equal (every signal on the Horner path of the CRT)
+    std::vector<int32_t> kc((size_t)B * 2, (int32_t)K), sp((size_t)B * 3, 0);
+    for (int64_t b = 0; b < B; ++b) sp[b * 3 + 2] = 3;
     std::vector<Sched> sc((size_t)B * 4);
     for (Sched& S : sc) {
         std::memset(&S, 0, sizeof S);
@@ -712,13 +730,40 @@ static int autotune_ntt(ozfft_plan_s* p)
     }
     CUDA_TRY(cudaMemcpy(p->kcnt, kc.data(), sizeof(int32_t) * kc.size(), cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(p->sched, sc.data(), sizeof(Sched) * sc.size(), cudaMemcpyHostToDevice));
-    cudaEvent_t e0, e1;
-    CUDA_TRY(cudaEventCreate(&e0));
-    CUDA_TRY(cudaEventCreate(&e1));
+    CUDA_TRY(cudaMemcpy(p->span, sp.data(), sizeof(int32_t) * sp.size(), cudaMemcpyHostToDevice));
+    // the CRT's output while timing: the signals' packed range (length classes) or chunk x n
+    const bool with_crt = !p->ts && !p->debug;
+    double2* tout = nullptr;
+    if (with_crt) {
+        int64_t out_elems = p->chunk * p->n;
+        for (const SigDesc& d : p->sd_host) out_elems = std::max(out_elems, d.io_off + d.n);
+        int rc = dalloc(p, &tout, (size_t)out_elems);
+        if (rc) return rc;
+        p->bytes -= (int64_t)sizeof(double2) * out_elems;   // temporary
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t err = cudaEventCreate(&e0);
+    if (err == cudaSuccess) err = cudaEventCreate(&e1);
+    auto time_ms = [&](auto&& launch) {
+        float best = 1e30f;
+        for (int rep = 0; rep < 3 && err == cudaSuccess; ++rep) {
+            float ms = 0.f;
+            err = cudaEventRecord(e0, 0);
+            if (err == cudaSuccess) err = launch();
+            if (err == cudaSuccess) err = cudaEventRecord(e1, 0);
+            if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+            if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0) best = std::min(best, ms);
+        }
+        return best;
+    };
+    const MacSrc mac{p->X, p->Ym, p->ym_stride};
+    const CrtArgs ca0{p->Z, p->sched, p->span, p->chirp, tout, p->n, p->N, p->chunk, p->P, p->G, p->direction,
+                      p->status, p->sd, nullptr, p->merge, p->garner_u, 0};
     float best_f = 1e30f, best_i = 1e30f;
-    int m2f = p->geom_fwd.m2, m2i = p->geom_inv.m2;
-    cudaError_t err = cudaSuccess;
+    int m2f = p->geom_fwd.m2, m2i = p->geom_inv.m2, fused = p->crt_fused;
     for (int m2 : cands) {
+        if (err != cudaSuccess) break;
         NttGeom gf = p->geom_fwd, gi = p->geom_inv;
         ntt_configure_split(gf, p->N, m2);
         ntt_configure_split(gi, p->N, m2);
@@ -727,40 +772,61 @@ static int autotune_ntt(ozfft_plan_s* p)
         CUtensorMap tx{}, tz{};   // this split's tensor maps, so the candidates run the kernels they would use
         gf.tmap = ntt_make_tmap(&tx, gf, p->X, gf.nvec) ? &tx : nullptr;
         gi.tmap = ntt_make_tmap(&tz, gi, p->Z, gi.nvec) ? &tz : nullptr;
-        const MacSrc mac{p->X, p->Ym, p->ym_stride};
-        float tf = 1e30f, ti = 1e30f;
-        for (int rep = 0; rep < 3 && err == cudaSuccess; ++rep) {
-            float ms = 0.f;
-            err = cudaEventRecord(e0, 0);
-            if (err == cudaSuccess) err = launch_ntt_forward(gf, p->X, p->tw, 0);
-            if (err == cudaSuccess) err = cudaEventRecord(e1, 0);
-            if (err == cudaSuccess) err = cudaEventSynchronize(e1);
-            if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
-            if (rep > 0) tf = std::min(tf, ms);
-            if (err == cudaSuccess) err = cudaEventRecord(e0, 0);
-            if (err == cudaSuccess) err = launch_ntt_inv_row(gi, p->Z, p->twinv, mac, 0);
-            if (err == cudaSuccess && gi.m1 > 0) err = launch_ntt_inv_col(gi, p->Z, p->twinv, 0);
-            if (err == cudaSuccess) err = cudaEventRecord(e1, 0);
-            if (err == cudaSuccess) err = cudaEventSynchronize(e1);
-            if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
-            if (rep > 0) ti = std::min(ti, ms);
-        }
-        if (err != cudaSuccess) break;
+        const float tf = time_ms([&] { return launch_ntt_forward(gf, p->X, p->tw, 0); });
         if (tf < best_f) { best_f = tf; m2f = m2; }
-        if (ti < best_i) { best_i = ti; m2i = m2; }
+        const bool can_fuse = with_crt && gi.m1 > 0 && colcrt_supported(p->P, gi.m1, gi.m2, p->merge);
+        for (int f = 0; f <= 1; ++f) {
+            if (f && !(can_fuse && (p->tune_fuse || p->crt_fused))) continue;
+            if (!f && !p->tune_fuse && p->crt_fused && can_fuse) continue;   // fusion forced where it applies
+            const float ti = time_ms([&] {
+                cudaError_t e = launch_ntt_inv_row(gi, p->Z, p->twinv, mac, 0);
+                if (e != cudaSuccess || !with_crt) {
+                    if (e == cudaSuccess && gi.m1 > 0) e = launch_ntt_inv_col(gi, p->Z, p->twinv, 0);
+                    return e;
+                }
+                CrtArgs c = ca0;
+                if (f) {
+                    e = launch_colcrt(c, gi.m1, gi.m2, p->twinv, 0);
+                    c.fused = 1;
+                } else if (gi.m1 > 0) {
+                    e = launch_ntt_inv_col(gi, p->Z, p->twinv, 0);
+                }
+                return e != cudaSuccess ? e : launch_crt_post(c, 0);
+            });
+            if (ti < best_i) { best_i = ti; m2i = m2; fused = f; }
+        }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    NttGeom gf = p->geom_fwd, gi = p->geom_inv;
+    if (err == cudaSuccess) {
+        ntt_configure_split(p->geom_fwd, p->N, m2f);
+        ntt_configure_split(p->geom_inv, p->N, m2i);
+        if (p->tune_fuse && with_crt) p->crt_fused = fused;
+    }
+    // at the chosen split and fusion: one or two vectors per CTA in the inverse row pass
+    if (err == cudaSuccess && p->tune_vecs) {
+        NttGeom g2 = p->geom_inv;
+        g2.nvec = gi.nvec; g2.P = p->P; g2.K = p->K; g2.G = p->G; g2.kcnt = p->kcnt; g2.sched = p->sched;
+        if (g2.mac_reg && g2.lgN >= 12 && g2.m2 >= 5 && g2.m2 <= 12 && g2.nvec % (2 * p->P) == 0) {
+            float t[3] = {0.f, 0.f, 0.f};
+            for (int v = 1; v <= 2; ++v) {
+                g2.inv_vecs_per_cta = v;
+                t[v] = time_ms([&] { return launch_ntt_inv_row(g2, p->Z, p->twinv, mac, 0); });
+            }
+            if (err == cudaSuccess) gi.inv_vecs_per_cta = t[1] < t[2] ? 1 : 2;
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (tout) cudaFree(tout);
     if (err != cudaSuccess) return fail(OZFFT_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(err));
     CUDA_TRY(cudaMemset(p->kcnt, 0, sizeof(int32_t) * B * 2));
     CUDA_TRY(cudaMemset(p->sched, 0, sizeof(Sched) * B * 4));
-    NttGeom gf = p->geom_fwd, gi = p->geom_inv;
-    ntt_configure_split(p->geom_fwd, p->N, m2f);
-    ntt_configure_split(p->geom_inv, p->N, m2i);
+    CUDA_TRY(cudaMemset(p->span, 0, sizeof(int32_t) * B * 3));
+    CUDA_TRY(cudaMemset(p->status, 0, sizeof(int)));
     p->geom_fwd.nvec = gf.nvec; p->geom_fwd.P = gf.P; p->geom_fwd.K = gf.K; p->geom_fwd.G = gf.G;
     p->geom_fwd.kcnt = gf.kcnt; p->geom_fwd.sched = gf.sched;
     p->geom_inv.nvec = gi.nvec; p->geom_inv.P = gi.P; p->geom_inv.K = gi.K; p->geom_inv.G = gi.G;
-    p->geom_inv.kcnt = gi.kcnt; p->geom_inv.sched = gi.sched;
+    p->geom_inv.kcnt = gi.kcnt; p->geom_inv.sched = gi.sched; p->geom_inv.inv_vecs_per_cta = gi.inv_vecs_per_cta;
     const int64_t nchunks = (B + p->chunk - 1) / p->chunk;
     p->launches = 1 + (p->ts ? K : SPLIT_SPEC_LAUNCHES) + 1 + ntt_launches(p->geom_fwd) +
                   nchunks * (ntt_launches(p->geom_inv) + (p->ts ? 1 : crt_launches()));
@@ -804,6 +870,7 @@ static int run_plan_range(ozfft_plan_s* p, const void* in, void* out, cudaStream
             CUDA_TRY(launch_premul((const double2*)in, p->chirp, p->n, N, B, p->direction > 0, sd, p->io_ref, r, mu,
                                    K, p->status, s));
         mark(p, OZFFT_PROF_PREMUL, s);
+        if (p->rec_after_premul) CUDA_TRY(cudaEventRecord(p->rec_after_premul, s));
     }
     if (p->debug && whole && !p->ts)
         CUDA_TRY(cudaMemcpyAsync(p->dbg_r, p->r, sizeof(double) * B * 2 * N, cudaMemcpyDeviceToDevice, s));
@@ -854,9 +921,10 @@ static int run_plan_range(ozfft_plan_s* p, const void* in, void* out, cudaStream
                    p->garner_u, 0};
         // the column pass fused with the CRT (Z stays on chip), unless the
         // stage dumps need Z, the schedule is one the fused kernel does not take,
-        // or the plan is a length class of uneven lengths (measured slower there:
-        // 4096 log-uniform lengths, 188 against 198-205 ms per execution at L = 3)
-        const bool fuse = !p->ts && !p->debug && !sd && gi.m1 > 0 && colcrt_supported(P, gi.m1, gi.m2, p->merge);
+        // or the plan (a length class) runs them apart (crt_fused: the default
+        // for uneven plans, measured faster there overall, or the autotuner's choice)
+        const bool fuse = !p->ts && !p->debug && p->crt_fused && gi.m1 > 0 && colcrt_supported(P, gi.m1, gi.m2, p->merge);
+        if (b0 == 0 && p->wait_before_out) CUDA_TRY(cudaStreamWaitEvent(s, p->wait_before_out, 0));
         if (fuse) {
             CUDA_TRY(launch_colcrt(ca, gi.m1, gi.m2, p->twinv, s));
             ca.fused = 1;
@@ -935,6 +1003,10 @@ ozfft_plan_t ozfft_plan_ex(int64_t n, int64_t batch, int direction, const ozfft_
         fail(OZFFT_ERR_LENGTH, "ozfft_plan: convolution length must be a power of two <= 2^24, equal to n or >= 2n-1");
         return nullptr;
     }
+    if (o.inv_vecs < 0 || o.inv_vecs > 2 || o.crt_fuse < 0 || o.crt_fuse > 2) {
+        fail(OZFFT_ERR_ARG, "ozfft_plan: inv_vecs must be 0..2 and crt_fuse 0..2");
+        return nullptr;
+    }
     if (o.ts && (P != 2 || o.merge || kinf)) {
         fail(OZFFT_ERR_ARG, "ozfft_plan: the TS variant takes two primes, no merged schedules and a finite K");
         return nullptr;
@@ -973,7 +1045,15 @@ ozfft_plan_t ozfft_plan_ex(int64_t n, int64_t batch, int direction, const ozfft_
         p->chunk = std::min<int64_t>(c, batch);
     }
     p->total = n * batch;
-    if (plan_build(p) != OZFFT_OK || (o.autotune && !o.row_log && autotune_ntt(p) != OZFFT_OK) ||
+    p->crt_fused = o.crt_fuse != 2;
+    p->tune_fuse = o.crt_fuse == 0;
+    p->tune_vecs = o.inv_vecs == 0;
+    if (plan_build(p) != OZFFT_OK) {
+        plan_free(p);
+        return nullptr;
+    }
+    if (o.inv_vecs) p->geom_inv.inv_vecs_per_cta = o.inv_vecs;
+    if ((o.autotune && !o.row_log && autotune_ntt(p) != OZFFT_OK) ||
         (o.row_log && force_split(p, o.row_log) != OZFFT_OK)) {
         plan_free(p);
         return nullptr;
@@ -1000,7 +1080,7 @@ ozfft_plan_t ozfft_plan_many(const int64_t* lengths, int64_t count, int directio
     if (!lengths || count < 1 || (direction != OZFFT_FORWARD && direction != OZFFT_INVERSE &&
                                   direction != OZFFT_ADJOINT && direction != OZFFT_INVERSE_ADJOINT) ||
         K < 1 || K > MAX_K || L < 1 || L > MAX_L || P < 2 || P > 3 || o.conv_len != 0 || o.debug != 0 || o.chunk < 0 ||
-        o.ts != 0) {
+        o.ts != 0 || o.inv_vecs < 0 || o.inv_vecs > 2 || o.crt_fuse < 0 || o.crt_fuse > 2) {
         fail(OZFFT_ERR_ARG, "ozfft_plan_many: argument out of range");
         return nullptr;
     }
@@ -1093,7 +1173,16 @@ ozfft_plan_t ozfft_plan_many(const int64_t* lengths, int64_t count, int directio
         q->total = chirp_off;
         q->chunk = o.chunk > 0 ? std::min<int64_t>(o.chunk, q->B)
                                : std::max<int64_t>(1, std::min<int64_t>(q->B, (int64_t)(q->B * frac)));
-        if (plan_build(q) != OZFFT_OK || (o.autotune && autotune_ntt(q) != OZFFT_OK)) return bail(0, "");
+        q->crt_fused = o.crt_fuse == 1;   // length classes keep the CRT apart unless forced or tuned
+        q->tune_fuse = o.crt_fuse == 0;
+        q->tune_vecs = o.inv_vecs == 0;
+        if (plan_build(q) != OZFFT_OK) return bail(0, "");
+        if (o.inv_vecs) q->geom_inv.inv_vecs_per_cta = o.inv_vecs;
+        if (o.autotune && !o.row_log && autotune_ntt(q) != OZFFT_OK) return bail(0, "");
+        if (o.row_log) {   // the forced split, for every class whose N admits it
+            NttGeom t{};
+            if (ntt_configure_split(t, q->N, o.row_log) && force_split(q, o.row_log) != OZFFT_OK) return bail(0, "");
+        }
         p->bytes += q->bytes;
         p->launches += q->launches;
         p->fwd_plan += q->fwd_plan;
@@ -1198,12 +1287,9 @@ int ozfft_selftest_wait_timeout(void* stream)
     return (st & ST_TIMEOUT) ? OZFFT_ERR_TIMEOUT : OZFFT_OK;
 }
 
-int ozfft_execute_host(ozfft_plan_t p, const void* in, void* out, void* stream)
+// the device staging buffers of host-buffer executions (both, or neither)
+static int ensure_staging(ozfft_plan_s* p)
 {
-    if (!p || !in || !out) return fail(OZFFT_ERR_ARG, "ozfft_execute_host: null argument");
-    cudaStream_t s = (cudaStream_t)stream;
-    const size_t bytes = sizeof(double2) * p->total;
-    StageRange range("ozfft_execute_host");
     if (!p->stage_in || !p->stage_out) {
         g_alloc_seq = 0;
         int rc = OZFFT_OK;
@@ -1216,6 +1302,23 @@ int ozfft_execute_host(ozfft_plan_t p, const void* in, void* out, void* stream)
             p->stage_in = p->stage_out = nullptr;
             return rc;
         }
+    }
+    return OZFFT_OK;
+}
+
+int ozfft_execute_host(ozfft_plan_t p, const void* in, void* out, void* stream)
+{
+    if (!p || !in || !out) return fail(OZFFT_ERR_ARG, "ozfft_execute_host: null argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t bytes = sizeof(double2) * p->total;
+    StageRange range("ozfft_execute_host");
+    {
+        const int rc = ensure_staging(p);
+        if (rc) return rc;
+    }
+    if (p->async_pending) {   // an asynchronous call's copy out may still read stage_out
+        CUDA_TRY(cudaEventSynchronize(p->ev_a_out));
+        p->async_pending = false;
     }
     const int parts = (p->classes.empty() && !p->debug && p->B >= 8) ? ozfft_plan_s::HOST_PARTS : 1;
     if (parts == 1) {
@@ -1231,11 +1334,11 @@ int ozfft_execute_host(ozfft_plan_t p, const void* in, void* out, void* stream)
     if (!p->cs_in) {
         CUDA_TRY(cudaStreamCreateWithFlags(&p->cs_in, cudaStreamNonBlocking));
         CUDA_TRY(cudaStreamCreateWithFlags(&p->cs_out, cudaStreamNonBlocking));
-        CUDA_TRY(cudaEventCreateWithFlags(&p->ev_go, cudaEventDisableTiming));
-        for (int i = 0; i < parts; ++i) {
-            CUDA_TRY(cudaEventCreateWithFlags(&p->ev_in[i], cudaEventDisableTiming));
-            CUDA_TRY(cudaEventCreateWithFlags(&p->ev_done[i], cudaEventDisableTiming));
-        }
+    }
+    if (!p->ev_go) CUDA_TRY(cudaEventCreateWithFlags(&p->ev_go, cudaEventDisableTiming));
+    for (int i = 0; i < parts; ++i) {
+        if (!p->ev_in[i]) CUDA_TRY(cudaEventCreateWithFlags(&p->ev_in[i], cudaEventDisableTiming));
+        if (!p->ev_done[i]) CUDA_TRY(cudaEventCreateWithFlags(&p->ev_done[i], cudaEventDisableTiming));
     }
     CUDA_TRY(cudaEventRecord(p->ev_go, s));             // earlier work on s may still use the staging
     CUDA_TRY(cudaStreamWaitEvent(p->cs_in, p->ev_go, 0));
@@ -1268,6 +1371,64 @@ int ozfft_execute_host(ozfft_plan_t p, const void* in, void* out, void* stream)
     CUDA_TRY(cudaStreamSynchronize(p->cs_out));
     CUDA_TRY(cudaStreamSynchronize(s));
     return frc;
+}
+
+int ozfft_execute_host_async(ozfft_plan_t p, const void* in, void* out, void* stream)
+{
+    if (!p || !in || !out) return fail(OZFFT_ERR_ARG, "ozfft_execute_host_async: null argument");
+    if (!p->classes.empty() || p->debug) return ozfft_execute_host(p, in, out, stream);
+    StageRange range("ozfft_execute_host_async");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t bytes = sizeof(double2) * p->total;
+    {
+        const int rc = ensure_staging(p);
+        if (rc) return rc;
+    }
+    if (!p->ev_a_out) {
+        if (!p->cs_in) {
+            CUDA_TRY(cudaStreamCreateWithFlags(&p->cs_in, cudaStreamNonBlocking));
+            CUDA_TRY(cudaStreamCreateWithFlags(&p->cs_out, cudaStreamNonBlocking));
+        }
+        if (!p->ev_go) CUDA_TRY(cudaEventCreateWithFlags(&p->ev_go, cudaEventDisableTiming));
+        CUDA_TRY(cudaEventCreateWithFlags(&p->ev_a_premul, cudaEventDisableTiming));
+        CUDA_TRY(cudaEventCreateWithFlags(&p->ev_a_in, cudaEventDisableTiming));
+        CUDA_TRY(cudaEventCreateWithFlags(&p->ev_a_done, cudaEventDisableTiming));
+        CUDA_TRY(cudaEventCreateWithFlags(&p->ev_a_out, cudaEventDisableTiming));
+    }
+    // copy in once the previous call's premultiply has read stage_in (the first
+    // asynchronous call: once earlier work on the stream is done with it)
+    if (p->async_pending) {
+        CUDA_TRY(cudaStreamWaitEvent(p->cs_in, p->ev_a_premul, 0));
+    } else {
+        CUDA_TRY(cudaEventRecord(p->ev_go, s));
+        CUDA_TRY(cudaStreamWaitEvent(p->cs_in, p->ev_go, 0));
+    }
+    CUDA_TRY(cudaMemcpyAsync(p->stage_in, in, bytes, cudaMemcpyHostToDevice, p->cs_in));
+    CUDA_TRY(cudaEventRecord(p->ev_a_in, p->cs_in));
+    CUDA_TRY(cudaStreamWaitEvent(s, p->ev_a_in, 0));
+    // the transform on the caller's stream; its CRT stage, which writes stage_out,
+    // waits for the previous call's copy out (long done when the CRT starts)
+    p->rec_after_premul = p->ev_a_premul;
+    p->wait_before_out = p->async_pending ? p->ev_a_out : nullptr;
+    int rc = run_plan(p, p->stage_in, p->stage_out, s);
+    p->rec_after_premul = p->wait_before_out = nullptr;
+    if (!rc) rc = fault_after_execution(p->status, s);
+    if (rc) return rc;
+    CUDA_TRY(cudaEventRecord(p->ev_a_done, s));
+    CUDA_TRY(cudaStreamWaitEvent(p->cs_out, p->ev_a_done, 0));
+    CUDA_TRY(cudaMemcpyAsync(out, p->stage_out, bytes, cudaMemcpyDeviceToHost, p->cs_out));
+    CUDA_TRY(cudaEventRecord(p->ev_a_out, p->cs_out));
+    p->async_pending = true;
+    return OZFFT_OK;
+}
+
+int ozfft_execute_host_wait(ozfft_plan_t p, void* stream)
+{
+    if (!p) return fail(OZFFT_ERR_ARG, "ozfft_execute_host_wait: null plan");
+    CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    if (p->async_pending) CUDA_TRY(cudaEventSynchronize(p->ev_a_out));
+    p->async_pending = false;
+    return OZFFT_OK;
 }
 
 int ozfft_get_status(ozfft_plan_t p, void* stream)
@@ -1311,6 +1472,18 @@ int ozfft_get_stats(ozfft_plan_t p, void* stream, ozfft_stats* out)
     const ozfft_plan_s* g0 = p->classes.empty() ? p : p->classes.front();
     out->row_log_fwd = g0->geom_fwd.m2;
     out->row_log_inv = g0->geom_inv.m2;
+    {
+        const NttGeom& gi = g0->geom_inv;
+        const bool vk = gi.mac_reg && gi.lgN >= 12 && gi.m2 >= 5 && gi.m2 <= 12 &&
+                        (g0->chunk * 4 * g0->G * g0->P) % (2 * g0->P) == 0;
+        out->inv_vecs = vk ? gi.inv_vecs_per_cta : 1;
+    }
+    out->classes = p->classes.empty() ? 1 : (int32_t)p->classes.size();
+    for (const ozfft_plan_s* q : (p->classes.empty() ? std::vector<ozfft_plan_s*>{p} : p->classes)) {
+        const NttGeom& gi = q->geom_inv;
+        out->crt_fused_classes += !q->ts && !q->debug && q->crt_fused && gi.m1 > 0 &&
+                                  colcrt_supported(q->P, gi.m1, gi.m2, q->merge);
+    }
     std::vector<ozfft_plan_s*> parts = p->classes;
     if (parts.empty()) parts.push_back(p);
     if (p->executed) CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
@@ -1560,6 +1733,7 @@ static int noalloc_setup(NoallocState& st, int dev, int64_t n, int64_t N, int al
     p.geom_fwd.K = K;
     p.geom_fwd.G = p.G;
     p.geom_fwd.mac_reg = 1;   // L = 1
+    p.geom_fwd.inv_vecs_per_cta = INV_ROW_VECS;
     p.geom_inv = p.geom_fwd;
     NttGeom gw = p.geom_fwd;
     gw.nvec = (int64_t)2 * K * P;

@@ -26,14 +26,16 @@ MAX_GROUPS, MAX_L = 64, 8
 EXPORTS = ("ozfft_plan", "ozfft_plan_ex", "ozfft_execute", "ozfft_execute_host", "ozfft_get_status",
            "ozfft_get_stats", "ozfft_set_profiling", "ozfft_get_profile", "ozfft_destroy", "ozfft_error_string",
            "ozfft_last_error", "ozfft_debug_dump", "ozfft_execute_noalloc", "ozfft_plan_many",
-           "ozfft_measure_butterfly_rate", "ozfft_selftest_wait_timeout", "ozfft_fault_config")
+           "ozfft_measure_butterfly_rate", "ozfft_selftest_wait_timeout", "ozfft_fault_config",
+           "ozfft_execute_host_async", "ozfft_execute_host_wait")
 PROF_SLOTS = ("premul", "split", "schedule", "ntt_fwd_col", "ntt_fwd_row", "ntt_inv_row", "ntt_inv_col", "crt")
 
 
 class Options(C.Structure):
     _fields_ = [("K", C.c_int32), ("L", C.c_int32), ("nprimes", C.c_int32), ("conv_len", C.c_int64),
                 ("debug", C.c_int32), ("chunk", C.c_int32), ("autotune", C.c_int32), ("no_graph", C.c_int32),
-                ("merge", C.c_int32), ("row_log", C.c_int32), ("ts", C.c_int32)]
+                ("merge", C.c_int32), ("row_log", C.c_int32), ("ts", C.c_int32), ("inv_vecs", C.c_int32),
+                ("crt_fuse", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -42,7 +44,8 @@ class Stats(C.Structure):
                 ("direction", C.c_int32), ("wstar_levels", C.c_int32 * 2),
                 ("ntt_forward_runtime", C.c_int64), ("ntt_forward_plan", C.c_int64), ("ntt_inverse", C.c_int64),
                 ("kernel_launches", C.c_int64), ("workspace_bytes", C.c_int64),
-                ("row_log_fwd", C.c_int32), ("row_log_inv", C.c_int32)]
+                ("row_log_fwd", C.c_int32), ("row_log_inv", C.c_int32), ("inv_vecs", C.c_int32),
+                ("crt_fused_classes", C.c_int32), ("classes", C.c_int32)]
 
 
 class Profile(C.Structure):
@@ -72,6 +75,8 @@ def load(path: str = LIB_PATH):
             L.ozfft_plan_ex.restype = P; L.ozfft_plan_ex.argtypes = [i64, i64, C.c_int, C.POINTER(Options)]
             L.ozfft_execute.restype = C.c_int; L.ozfft_execute.argtypes = [P, P, P, P]
             L.ozfft_execute_host.restype = C.c_int; L.ozfft_execute_host.argtypes = [P, P, P, P]
+            L.ozfft_execute_host_async.restype = C.c_int; L.ozfft_execute_host_async.argtypes = [P, P, P, P]
+            L.ozfft_execute_host_wait.restype = C.c_int; L.ozfft_execute_host_wait.argtypes = [P, P]
             L.ozfft_get_status.restype = C.c_int; L.ozfft_get_status.argtypes = [P, P]
             L.ozfft_get_stats.restype = C.c_int; L.ozfft_get_stats.argtypes = [P, P, C.POINTER(Stats)]
             L.ozfft_set_profiling.restype = C.c_int; L.ozfft_set_profiling.argtypes = [P, C.c_int]
@@ -111,13 +116,13 @@ class Plan:
     """A plan for `batch` transforms of length n (see ozfft_plan_ex)."""
 
     def __init__(self, n, batch=1, direction=FORWARD, K=3, L=1, nprimes=2, conv_len=0, debug=False, chunk=0,
-                 autotune=False, merge=False, ts=False, row_log=0):
+                 autotune=False, merge=False, ts=False, row_log=0, inv_vecs=0, crt_fuse=0):
         lib = load()
         self.n, self.batch, self.direction = int(n), int(batch), int(direction)
         self.K, self.L, self.nprimes, self.merge, self.ts = int(K), int(L), int(nprimes), bool(merge), bool(ts)
         self.levels = K_INF_CAP if self.K == K_INF else self.K   # level dimension of the buffers
         opt = Options(self.K, self.L, self.nprimes, int(conv_len), int(bool(debug)), int(chunk), int(bool(autotune)), 0,
-                      int(self.merge), int(row_log), int(self.ts))
+                      int(self.merge), int(row_log), int(self.ts), int(inv_vecs), int(crt_fuse))
         self._h = lib.ozfft_plan_ex(self.n, self.batch, self.direction, C.byref(opt))
         if not self._h:
             raise OzfftError(-1, lib.ozfft_last_error().decode())
@@ -151,15 +156,38 @@ class Plan:
     def execute_ptr(self, in_ptr, out_ptr, stream_ptr):
         _check(load().ozfft_execute(self._h, in_ptr, out_ptr, stream_ptr))
 
+    def _host_ptrs(self, x, out):
+        ptrs = []
+        for a in (x, out):
+            if isinstance(a, np.ndarray):
+                ok = a.dtype == np.complex128 and a.flags.c_contiguous and a.size == self.total
+                ptrs.append(a.ctypes.data)
+            else:
+                import torch
+                ok = a.dtype == torch.complex128 and a.is_contiguous() and not a.is_cuda and a.numel() == self.total
+                ptrs.append(a.data_ptr())
+            if not ok:
+                raise OzfftError(ERR_ARG, f"host buffers must be contiguous complex128 with {self.total} elements")
+        return ptrs
+
     def execute_host(self, x, out, stream=None):
         """x, out: host buffers (numpy complex128 arrays or pinned CPU tensors) of `total` elements."""
-        for a in (x, out):
-            if (a.size if isinstance(a, np.ndarray) else a.numel()) != self.total:
-                raise OzfftError(ERR_ARG, f"host buffers must hold {self.total} elements")
-        xp = x.ctypes.data if isinstance(x, np.ndarray) else x.data_ptr()
-        op = out.ctypes.data if isinstance(out, np.ndarray) else out.data_ptr()
+        xp, op = self._host_ptrs(x, out)
         _check(load().ozfft_execute_host(self._h, xp, op, _stream_ptr(stream)))
         return out
+
+    def execute_host_async(self, x, out, stream=None):
+        """Enqueue a host-buffer transform (ozfft_execute_host_async); x and out
+        are kept alive here and must not be touched until host_wait()."""
+        xp, op = self._host_ptrs(x, out)
+        _check(load().ozfft_execute_host_async(self._h, xp, op, _stream_ptr(stream)))
+        self.__dict__.setdefault("_pending", []).append((x, out))
+        return out
+
+    def host_wait(self, stream=None):
+        """Wait for every execute_host_async call (ozfft_execute_host_wait)."""
+        _check(load().ozfft_execute_host_wait(self._h, _stream_ptr(stream)))
+        self.__dict__["_pending"] = []
 
     def status(self, stream=None):
         return load().ozfft_get_status(self._h, _stream_ptr(stream))
@@ -223,7 +251,7 @@ class PlanMany(Plan):
     output are packed, signal i at elements [offsets[i], offsets[i+1])."""
 
     def __init__(self, lengths, direction=FORWARD, K=3, L=1, nprimes=2, chunk=0, autotune=False, graph=True,
-                 merge=False):
+                 merge=False, row_log=0, inv_vecs=0, crt_fuse=0):
         lib = load()
         lens = np.ascontiguousarray(np.asarray(lengths, dtype=np.int64))
         self.lengths = lens
@@ -232,7 +260,7 @@ class PlanMany(Plan):
         self.levels = K_INF_CAP if self.K == K_INF else self.K
         self.merge = bool(merge)
         opt = Options(self.K, self.L, self.nprimes, 0, 0, int(chunk), int(bool(autotune)), int(not graph),
-                      int(self.merge), 0, 0)
+                      int(self.merge), int(row_log), 0, int(inv_vecs), int(crt_fuse))
         self._h = lib.ozfft_plan_many(lens.ctypes.data_as(C.POINTER(C.c_int64)), lens.size, self.direction,
                                       C.byref(opt))
         if not self._h:

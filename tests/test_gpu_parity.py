@@ -343,3 +343,37 @@ def test_host_buffer_pipeline(oz, B):
             plan.execute_host(hin, hout)
             got = hout.numpy() if pinned else hout
             assert np.array_equal(got.view(np.uint64), ref.view(np.uint64)), (B, pinned)
+
+
+def test_async_host_execution_pipelined(oz):
+    """ozfft_execute_host_async: several calls in flight with different inputs
+    and outputs (each call's copies overlapping its neighbours' computation),
+    then ozfft_execute_host_wait; every output equals the synchronous call's,
+    bit for bit, and the oracle's.  A synchronous call after asynchronous ones
+    (and the reverse) shares the staging buffers safely."""
+    n, B = 4096, 9
+    xs = [synth.complex_signal(kind, n, 80 + i, batch=B) for i, kind in enumerate(("uniform", "phi", "gaussian"))]
+    plan = oz.Plan(n, B)
+    ref = []
+    for x in xs:
+        out = np.empty_like(x)
+        plan.execute_host(x, out)
+        ref.append(out)
+    pins = [torch.from_numpy(x).pin_memory() for x in xs]
+    outs = [torch.empty_like(t).pin_memory() for t in pins]
+    for rep in range(2):
+        for xin, o in zip(pins, outs):
+            plan.execute_host_async(xin, o)
+        plan.host_wait()
+        for o, r in zip(outs, ref):
+            assert np.array_equal(o.numpy().view(np.uint64), r.view(np.uint64)), rep
+    plan.execute_host_async(pins[0], outs[1])
+    out = np.empty_like(xs[2])
+    plan.execute_host(xs[2], out)                       # waits for the asynchronous call's copy out
+    plan.host_wait()
+    assert np.array_equal(out.view(np.uint64), ref[2].view(np.uint64))
+    assert np.array_equal(outs[1].numpy().view(np.uint64), ref[0].view(np.uint64))
+    for b in (0, B - 1):
+        yo, _ = oracle.ozfft(xs[1][b])
+        assert np.array_equal(ref[1][b].view(np.uint64), yo.view(np.uint64))
+    assert plan.status() == oz.OK

@@ -140,3 +140,65 @@ def test_log_uniform_batch_sampled(oz):
         bins = np.array([0, 1, len(xs[i]) // 2, len(xs[i]) - 1])
         hi, lo = oracle.dft_q(xs[i], bins=bins)
         assert np.max(np.abs(ys[i][bins] - (hi + lo))) <= 1e-14 * np.linalg.norm(xs[i]), i
+
+
+@pytest.mark.parametrize("opts", [dict(crt_fuse=1), dict(crt_fuse=2), dict(inv_vecs=1), dict(inv_vecs=2),
+                                  dict(row_log=11), dict(crt_fuse=1, inv_vecs=1, L=3),
+                                  dict(crt_fuse=1, L=3, merge=True), dict(autotune=True)])
+def test_each_tuned_choice_forced(oz, opts):
+    """Every choice the autotuner makes per length class, forced in turn: the
+    inverse column pass fused with the CRT or not, one or two vectors per CTA
+    in the inverse row pass, a forced NTT split; each plan is bit-exact against
+    the oracle's transform of every signal alone, and stats report the choice."""
+    lens = [3000, 70000, 5000, 1024, 40000, 131072, 2500, 100000, 777, 16]
+    x = packed(lens, "phi", 68)
+    plan = oz.PlanMany(lens, **opts)
+    y = plan.execute(torch.from_numpy(x).cuda()).cpu().numpy()
+    assert plan.status() == oz.OK
+    check_against_oracle(plan, x, y)
+    st = plan.stats()
+    assert st["classes"] == len({1 << (2 * n - 2).bit_length() if n & (n - 1) else n for n in lens})
+    if opts.get("crt_fuse") == 2:
+        assert st["crt_fused_classes"] == 0
+    if opts.get("crt_fuse") == 1:
+        assert st["crt_fused_classes"] >= 1
+    if "inv_vecs" in opts and not opts.get("L", 1) > 1:
+        assert st["inv_vecs"] == opts["inv_vecs"]
+
+
+@pytest.mark.parametrize("n,kw", [(4096, {}), (1 << 14, {}), (1 << 16, {}), (3000, {}), (1 << 14, dict(L=3, merge=True)),
+                                  (4096, dict(K=-1)), (1 << 16, dict(nprimes=3, K=2))])
+def test_inverse_row_vectors_per_cta_agree(oz, n, kw):
+    """The inverse row pass with one and with two vectors of a prime per CTA
+    (twiddle loads shared): bit-identical, and bit-exact against the oracle."""
+    B = 3
+    x = synth.complex_signal("phi", n, 69, batch=B, phi=1.0)
+    xt = torch.from_numpy(x).cuda()
+    ys = []
+    for v in (1, 2):
+        p = oz.Plan(n, B, inv_vecs=v, **kw)
+        ys.append(p.execute(xt).cpu().numpy())
+        assert p.status() == oz.OK
+    assert np.array_equal(ys[0].view(np.uint64), ys[1].view(np.uint64))
+    K = kw.get("K", 3)
+    for b in range(B):
+        yo, _ = oracle.ozfft(x[b], K=0 if K == -1 else K, L=kw.get("L", 1), nprimes=kw.get("nprimes", 2))
+        assert np.array_equal(ys[1][b].view(np.uint64), yo.view(np.uint64)), b
+
+
+def test_plain_plan_crt_fusion_forced(oz):
+    """A plain plan with the inverse column pass fused with the CRT and without
+    it, and the autotuned choice: the same bits."""
+    n, B = 1 << 16, 4
+    x = torch.from_numpy(synth.complex_signal("uniform", n, 70, batch=B)).cuda()
+    outs = []
+    for kw in (dict(crt_fuse=1), dict(crt_fuse=2), dict(autotune=True)):
+        p = oz.Plan(n, B, **kw)
+        outs.append(p.execute(x).cpu().numpy())
+        st = p.stats()
+        if kw.get("crt_fuse") == 1:
+            assert st["crt_fused_classes"] == 1
+        if kw.get("crt_fuse") == 2:
+            assert st["crt_fused_classes"] == 0
+    for o in outs[1:]:
+        assert np.array_equal(outs[0].view(np.uint64), o.view(np.uint64))
