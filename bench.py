@@ -36,7 +36,7 @@ BUTTERFLY_INSTR = 7.17   # lane instructions per radix-2 butterfly of the NTT ke
 UNIT = "FFT/s"
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=30)
@@ -73,13 +73,14 @@ def parse():
                          "sum |FFT(x) w|^2 over 256 Gaussian signals of n = 2^16; stress: n = 2^20 and "
                          "2^22, batch 8, 1%% spikes of 1e12, L = 1 (96 NTTs) vs L = 3 (64 NTTs); uneven: "
                          "4096 signals of log-uniform lengths in [1000, 300000] in one plan")
-    a = ap.parse_args()
+    a = ap.parse_args(argv)
+    given = sys.argv if argv is None else argv
     if a.workload == "autograd":
-        if "--n" not in sys.argv:
+        if "--n" not in given:
             a.n = 1 << 16
-        if "--batch" not in sys.argv:
+        if "--batch" not in given:
             a.batch = 256
-        if "--seed" not in sys.argv:
+        if "--seed" not in given:
             a.seed = 5
     return a
 

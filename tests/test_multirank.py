@@ -33,10 +33,8 @@ def _rank_main(rank, world, port, out):
     ms = bench.max_over_ranks(d, 100.0 * (rank + 1), "cpu")
     val = bench.job_value(10, 64, world, ms)
 
-    class A:   # a bounded reference-arm run: only rank 0 times and prints
-        n, K, L, nprimes, seed, steps, warmup, batch = 64, 3, 1, 2, 2, 1, 0, 64
-        autotune = merge = ts = False
-        row_log = 0
+    # a bounded reference-arm run (bench's own argument defaults): only rank 0 times and prints
+    A = bench.parse(["--n", "64", "--steps", "1", "--warmup", "0", "--batch", "64"])
     buf = io.StringIO()
     with redirect_stdout(buf):
         bench.run_reference(A, rank, world)
