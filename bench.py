@@ -836,11 +836,14 @@ def main():
             plan.execute_host_async(x_pin, out_pin)
         plan.host_wait()
         barrier()
+        eclocks = ClockSampler(local)
+        time.sleep(0.25)
         t0 = time.perf_counter()
         for _ in range(esteps):
             plan.execute_host_async(x_pin, out_pin)
         plan.host_wait()
         dt = rank_max(time.perf_counter() - t0)
+        eclk = eclocks.stop()
         # device time of the kernels inside those calls (per-kernel events, all four parts)
         plan.profile()
         plan.set_profiling(True)
@@ -877,7 +880,7 @@ def main():
                       "out of every step inside the timed region)",
                "model_ms_per_step": model_async,
                "model": "max(device step, copy in, copy out) + (copy in + copy out) / steps",
-               "copy_gbs": copy_gbs,
+               "copy_gbs": copy_gbs, "clocks": eclk,
                "sync": {"value": job_value(esteps, B, world, 1e3 * dt_sync), "ms_per_step": 1e3 * dt_sync / esteps,
                         "api": "ozfft_execute_host per step (returns after its copy out)",
                         "model_ms_per_step": t_out,

@@ -114,8 +114,9 @@ typedef struct {
                          must stay inside the binary32 exponent range (else OZFFT_ERR_RANGE) */
     int32_t inv_vecs; /* inverse NTT row pass with the Alg. 8 sums formed in registers (L = 1 or
                          merged schedules, N >= 2^12, row tiles up to 2^12): vectors of one prime per
-                         CTA, sharing every twiddle load.  0: 2 where it applies (or the autotuner's
-                         choice), 1 or 2 to force; results are bit-identical */
+                         CTA (2: the same group of RR and RI, or of II and IR, sharing every twiddle
+                         load).  0: 1 (or the autotuner's choice), 1 or 2 to force; results are
+                         bit-identical */
     int32_t crt_fuse; /* inverse NTT column pass fused with Garner's CRT and the exact accumulation
                          (two primes, 4..8 column stages): 0 = default (fused for plain plans,
                          separate kernels for the length classes of uneven plans, or the

@@ -523,14 +523,29 @@ __device__ __forceinline__ void inv_middle_rounds_v(uint32_t* sm, int rbase, con
     }
 }
 
-// one CTA: rows [row0, row0 + RPC) of the V vectors vbase + i P (i < V), which
-// share the prime vbase mod P; nvec is a multiple of V P
-constexpr int INV_PAIR_V = INV_ROW_VECS;
+// one product (L = 1, unmerged: the only unmerged schedules whose sums are
+// formed in registers): Z = X_s Ym_t, for a live vector
+__device__ __forceinline__ uint4 mac_one4(const MacVec& m, const MacSrc& mac, int64_t j)
+{
+    int64_t xo, yo;
+    mac_offsets<false>(m, 0, xo, yo);
+    const uint4 x = __ldg(reinterpret_cast<const uint4*>(mac.X + xo + j));
+    const uint4 y = __ldg(reinterpret_cast<const uint4*>(mac.Ym + yo + j));
+    return make_uint4(mont_mul(x.x, y.x, m.p, m.pn), mont_mul(x.y, y.y, m.p, m.pn), mont_mul(x.z, y.z, m.p, m.pn),
+                      mont_mul(x.w, y.w, m.p, m.pn));
+}
+
+// one CTA: rows [row0, row0 + RPC) of two vectors of one prime and one flush
+// group index: those of convolutions RR and RI (both products of Re x~'
+// slices) or of II and IR (Im x~'), which in the usual schedule read the same
+// X_s row, so the second vector's X loads hit L1 as its twiddles do
+constexpr int INV_PAIR_V = 2;
 template <int M2, bool MERGED>
 __global__ void __launch_bounds__(NTT_THREADS, 6) ntt_inv_row_v_kernel(NttGeom g, uint32_t* __restrict__ data,
                                                                       const uint2* __restrict__ tw_all, MacSrc mac)
 {
     constexpr int V = INV_PAIR_V;
+    static_assert(V == 2, "pairs of convolutions (RR, RI) and (II, IR)");
     constexpr int RPC = 1 << (TILE_LOG - M2);
     constexpr int TW = (RPC << M2) + ((RPC << M2) >> 5);      // words of one vector's padded tile
     using PT = Part<M2>;
@@ -538,9 +553,11 @@ __global__ void __launch_bounds__(NTT_THREADS, 6) ntt_inv_row_v_kernel(NttGeom g
     const int lg_rb = g.lgN - TILE_LOG;                     // row blocks per vector = 2^lg_rb
     const unsigned k = blockIdx.x >> lg_rb;
     const int row0 = (int)(blockIdx.x & ((1u << lg_rb) - 1)) * RPC;
-    const unsigned P = (unsigned)g.P;
-    const unsigned vbase = (k / P) * (V * P) + (k % P);
+    const unsigned P = (unsigned)g.P, GP = (unsigned)g.G * P;
+    // k enumerates (signal, pair type, group, prime); vectors are [signal][conv][group][prime]
     const int pi = (int)(k % P);
+    const unsigned grp = (k / P) % (unsigned)g.G, pt = (k / GP) & 1u, sig = k / (2 * GP);
+    const unsigned vec_of[V] = {((4 * sig + pt) * g.G + grp) * P + pi, ((4 * sig + 3 - pt) * g.G + grp) * P + pi};
     const uint32_t p = prime_of(pi);
     const uint2* tw = tw_all + (int64_t)pi * g.N;
     const int rbase = (1 << g.m1) + row0;
@@ -548,21 +565,14 @@ __global__ void __launch_bounds__(NTT_THREADS, 6) ntt_inv_row_v_kernel(NttGeom g
     MacVec mv[V];
     bool live[V];
     bool any = false;
-    const uint32_t* xrow[V];   // unmerged (one product): the rows of X_s and Ym_t this CTA reads
-    const uint32_t* yrow[V];
 #pragma unroll
     for (int i = 0; i < V; ++i) {
-        const unsigned vec = vbase + i * P;
+        const unsigned vec = vec_of[i];
         live[i] = inv_live(g, vec);
         any = any || live[i];
         mv[i] = mac_decode(g, vec, mac.ym_stride);
-        int64_t xo = 0, yo = 0;
-        if (!MERGED && mv[i].n > 0) mac_offsets<false>(mv[i], 0, xo, yo);
-        xrow[i] = mac.X + xo + j0;
-        yrow[i] = mac.Ym + yo + j0;
     }
     if (!any) return;
-    const uint32_t pn = pneg_inv_of(pi);
     {   // first round: groups of 2^RL contiguous residues, the Alg. 8 sums formed from X and Ym
         constexpr int R_ = PT::NR - 1, S0 = PT::start(R_), RL = PT::size(R_), R = 1 << RL, LOG_GPC = M2 - RL;
         static_assert(S0 + RL == M2 && RL >= 2 && RL <= 4, "first inverse round: contiguous groups");
@@ -576,14 +586,7 @@ __global__ void __launch_bounds__(NTT_THREADS, 6) ntt_inv_row_v_kernel(NttGeom g
 #pragma unroll
                 for (int q = 0; q < R; q += 4) {
                     uint4 t = make_uint4(0u, 0u, 0u, 0u);
-                    if (MERGED) {
-                        if (live[i]) t = mac_sum4<true>(mv[i], mac, j0 + base + q);
-                    } else if (live[i]) {
-                        const uint4 a = __ldg(reinterpret_cast<const uint4*>(xrow[i] + base + q));
-                        const uint4 b = __ldg(reinterpret_cast<const uint4*>(yrow[i] + base + q));
-                        t = make_uint4(mont_mul(a.x, b.x, p, pn), mont_mul(a.y, b.y, p, pn),
-                                       mont_mul(a.z, b.z, p, pn), mont_mul(a.w, b.w, p, pn));
-                    }
+                    if (live[i]) t = MERGED ? mac_sum4<true>(mv[i], mac, j0 + base + q) : mac_one4(mv[i], mac, j0 + base + q);
                     x[i][q] = t.x; x[i][q + 1] = t.y; x[i][q + 2] = t.z; x[i][q + 3] = t.w;
                 }
             radix_group_inv_v<RL, V>(x, tw, ((rbase + c) << S0) + grp, p);
@@ -614,7 +617,7 @@ __global__ void __launch_bounds__(NTT_THREADS, 6) ntt_inv_row_v_kernel(NttGeom g
 #pragma unroll
             for (int i = 0; i < V; ++i) {
                 if (!live[i]) continue;
-                uint32_t* out = data + ((int64_t)(vbase + i * P) << g.lgN) + j0 + base;
+                uint32_t* out = data + ((int64_t)vec_of[i] << g.lgN) + j0 + base;
 #pragma unroll
                 for (int u = 0; u < R; ++u) out[u * H] = x[i][u];
             }
@@ -763,7 +766,7 @@ cudaError_t launch_col_m(const NttGeom& g, uint32_t* data, const uint2* tw, cuda
 // V vectors per prime
 inline bool inv_row_v_ok(const NttGeom& g, int M2)
 {
-    return g.mac_reg && M2 >= 5 && M2 <= TILE_LOG && g.lgN >= TILE_LOG && g.nvec % (INV_PAIR_V * g.P) == 0;
+    return g.mac_reg && M2 >= 5 && M2 <= TILE_LOG && g.lgN >= TILE_LOG && g.nvec % (4 * g.G * g.P) == 0;
 }
 
 template <int M2>

@@ -61,9 +61,10 @@ bool launch_col_tma(bool inv, const NttGeom& g, const uint2* tw, cudaStream_t s,
 // barrier expects more bytes than its copy brings; *status receives the status bits
 cudaError_t col_tma_timeout_selftest(int* status_host, cudaStream_t s);
 
-// vectors of one prime per CTA of the inverse row pass with the MAC in registers
-// when the plan does not choose (the autotuner times 1 and 2)
-constexpr int INV_ROW_VECS = 2;
+// vectors per CTA of the inverse row pass with the MAC in registers when the plan
+// does not choose (the autotuner times 1 and 2; with the schedules of real
+// inputs the two are within a few percent at n = 2^18 x 64)
+constexpr int INV_ROW_VECS = 1;
 
 // Inputs of the multiply-accumulate fused into the inverse NTT's load.
 struct MacSrc {

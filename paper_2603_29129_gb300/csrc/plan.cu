@@ -806,7 +806,7 @@ static int autotune_ntt(ozfft_plan_s* p)
     if (err == cudaSuccess && p->tune_vecs) {
         NttGeom g2 = p->geom_inv;
         g2.nvec = gi.nvec; g2.P = p->P; g2.K = p->K; g2.G = p->G; g2.kcnt = p->kcnt; g2.sched = p->sched;
-        if (g2.mac_reg && g2.lgN >= 12 && g2.m2 >= 5 && g2.m2 <= 12 && g2.nvec % (2 * p->P) == 0) {
+        if (g2.mac_reg && g2.lgN >= 12 && g2.m2 >= 5 && g2.m2 <= 12 && g2.nvec % (4 * p->G * p->P) == 0) {
             float t[3] = {0.f, 0.f, 0.f};
             for (int v = 1; v <= 2; ++v) {
                 g2.inv_vecs_per_cta = v;
@@ -1475,7 +1475,7 @@ int ozfft_get_stats(ozfft_plan_t p, void* stream, ozfft_stats* out)
     {
         const NttGeom& gi = g0->geom_inv;
         const bool vk = gi.mac_reg && gi.lgN >= 12 && gi.m2 >= 5 && gi.m2 <= 12 &&
-                        (g0->chunk * 4 * g0->G * g0->P) % (2 * g0->P) == 0;
+                        (g0->chunk * 4 * g0->G * g0->P) % (4 * g0->G * g0->P) == 0;
         out->inv_vecs = vk ? gi.inv_vecs_per_cta : 1;
     }
     out->classes = p->classes.empty() ? 1 : (int32_t)p->classes.size();
