@@ -342,6 +342,37 @@ __device__ __forceinline__ long long split_level_fixed(uint64_t& a, bool& neg, i
     return q;
 }
 
+// The same level for alpha <= 30 (|q| <= 2^alpha fits 32 bits): the rounding
+// of a / 2^sh to nearest, ties to even, as one add and one shift,
+// (a + 2^(sh-1) - 1 + odd) >> sh with odd the last bit of a >> sh (a remainder
+// above half carries, one below does not, exactly half carries when the
+// quotient is odd), then the exact residual a - kq 2^sh.  Bit-identical to
+// split_level_fixed (which handles any alpha).
+__device__ __forceinline__ int32_t split_level_fixed32(uint64_t& a, bool& neg, int E, int e, int alpha)
+{
+    if (a == 0) return 0;
+    const int g = max(neg ? e - alpha : e + 1 - alpha, -1074);
+    const int sh = g - E;
+    uint32_t kq;
+    int64_t d;
+    if (sh <= 0) {                       // the grid is at least as fine as the input: all of it is kept
+        kq = (uint32_t)(a << (-sh));
+        d = 0;
+    } else if (sh >= 55) {               // a < 2^53 < 2^(sh - 2): rounds to zero
+        kq = 0;
+        d = (int64_t)a;
+    } else {
+        const uint64_t k64 = (a + ((1ull << (sh - 1)) - 1) + ((a >> sh) & 1ull)) >> sh;
+        kq = (uint32_t)k64;
+        d = (int64_t)a - (int64_t)(k64 << sh);
+    }
+    int32_t q = (int32_t)(kq << (g - (e - alpha)));
+    if (neg) q = -q;
+    neg = neg != (d < 0);
+    a = (uint64_t)(d < 0 ? -d : d);
+    return q;
+}
+
 // ceil(log2(a 2^E)) for a > 0
 __device__ __forceinline__ int ceil_log2_fixed(uint64_t a, int E)
 {
@@ -366,7 +397,7 @@ __device__ __forceinline__ uint64_t pow2_bits(int c)
 // guess, so the slices are those of Alg. 3 either way.  Residuals are not
 // written back (r keeps r^(0)).  KM bounds K at compile time (the per-level
 // maxima stay in registers).
-template <bool SD, int KM>
+template <bool SD, int KM, bool A30>
 __global__ void __launch_bounds__(SPLIT_THREADS) split_spec_kernel(const double* __restrict__ r,
                                                                    uint64_t* __restrict__ mu, int64_t N, int K,
                                                                    int alpha, const SigDesc* __restrict__ sd, int P,
@@ -401,21 +432,23 @@ __global__ void __launch_bounds__(SPLIT_THREADS) split_spec_kernel(const double*
 #pragma unroll
         for (int k = 0; k < KM; ++k) {
             if (k >= K) break;
-            const long long q = split_level_fixed(a, neg, E, e0 - k * alpha, alpha);
+            if constexpr (A30) {                  // |q| <= 2^alpha < p
+                const int32_t q = split_level_fixed32(a, neg, E, e0 - k * alpha, alpha);
 #pragma unroll
-            for (int pi = 0; pi < MAX_PRIMES; ++pi) {
-                if (pi >= P) break;
-                const uint32_t p = prime_of(pi);
-                uint32_t res;
-                if (alpha <= 30) {               // |q| <= 2^alpha < p
-                    const int32_t q32 = (int32_t)q;
-                    res = q32 < 0 ? (uint32_t)(q32 + (int32_t)p) : (uint32_t)q32;
-                } else {
-                    long long t = q % (long long)p;
-                    if (t < 0) t += p;
-                    res = (uint32_t)t;
+                for (int pi = 0; pi < MAX_PRIMES; ++pi) {
+                    if (pi >= P) break;
+                    const uint32_t p = prime_of(pi);
+                    xv[(k * P + pi) * N + j] = q < 0 ? (uint32_t)(q + (int32_t)p) : (uint32_t)q;
                 }
-                xv[(k * P + pi) * N + j] = res;
+            } else {
+                const long long q = split_level_fixed(a, neg, E, e0 - k * alpha, alpha);
+#pragma unroll
+                for (int pi = 0; pi < MAX_PRIMES; ++pi) {
+                    if (pi >= P) break;
+                    long long t = q % (long long)prime_of(pi);
+                    if (t < 0) t += prime_of(pi);
+                    xv[(k * P + pi) * N + j] = (uint32_t)t;
+                }
             }
             if (a) cmax[k] = max(cmax[k], ceil_log2_fixed(a, E));
         }
@@ -528,15 +561,20 @@ cudaError_t launch_split_spec(double* r, uint64_t* mu, int64_t N, int64_t nvec, 
                               int P, uint32_t* X, int* status, cudaStream_t s)
 {
     const unsigned grid = grid_for(nvec, N);
+    // alpha of every signal <= 30 (the plan's largest for a length class): 32-bit digits
+    const bool a30 = alpha <= 30;
+#define OZ_SPLIT_SPEC(SDV, KMV, A30V) \
+    split_spec_kernel<SDV, KMV, A30V><<<grid, SPLIT_THREADS, 0, s>>>(r, mu, N, K, alpha, sd, P, X, status)
     if (sd) {
-        if (K <= 4) split_spec_kernel<true, 4><<<grid, SPLIT_THREADS, 0, s>>>(r, mu, N, K, alpha, sd, P, X, status);
-        else split_spec_kernel<true, MAX_K><<<grid, SPLIT_THREADS, 0, s>>>(r, mu, N, K, alpha, sd, P, X, status);
+        if (K <= 4) { if (a30) OZ_SPLIT_SPEC(true, 4, true); else OZ_SPLIT_SPEC(true, 4, false); }
+        else { if (a30) OZ_SPLIT_SPEC(true, MAX_K, true); else OZ_SPLIT_SPEC(true, MAX_K, false); }
         split_fix_kernel<true><<<(unsigned)nvec, FIX_THREADS, 0, s>>>(r, mu, N, K, alpha, sd, P, X);
     } else {
-        if (K <= 4) split_spec_kernel<false, 4><<<grid, SPLIT_THREADS, 0, s>>>(r, mu, N, K, alpha, sd, P, X, status);
-        else split_spec_kernel<false, MAX_K><<<grid, SPLIT_THREADS, 0, s>>>(r, mu, N, K, alpha, sd, P, X, status);
+        if (K <= 4) { if (a30) OZ_SPLIT_SPEC(false, 4, true); else OZ_SPLIT_SPEC(false, 4, false); }
+        else { if (a30) OZ_SPLIT_SPEC(false, MAX_K, true); else OZ_SPLIT_SPEC(false, MAX_K, false); }
         split_fix_kernel<false><<<(unsigned)nvec, FIX_THREADS, 0, s>>>(r, mu, N, K, alpha, sd, P, X);
     }
+#undef OZ_SPLIT_SPEC
     return cudaGetLastError();
 }
 
