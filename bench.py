@@ -554,9 +554,16 @@ def run_uneven(a, rank, world, local):
     out = {}
     clocks = ClockSampler(local)
     for L in (3, 1):
+        # the autotuner's candidate timings per length class (OZFFT_TUNE_LOG)
+        tlog = tempfile.NamedTemporaryFile("w+", suffix=".tune", delete=False)
+        tlog.close()
+        os.environ["OZFFT_TUNE_LOG"] = tlog.name
         t0 = time.perf_counter()
         plan = ozfft.PlanMany(lens, ozfft.FORWARD, K=a.K, L=L, nprimes=a.nprimes, autotune=True)
         tplan = time.perf_counter() - t0
+        os.environ.pop("OZFFT_TUNE_LOG", None)
+        tune_rows = [ln.split() for ln in open(tlog.name).read().splitlines()]
+        os.unlink(tlog.name)
         ms = timed(lambda: plan.execute(x, y), a.steps)
         st = plan.stats()
         # whole-step roofline (the graph's kernels of every length class together): modular
@@ -588,7 +595,8 @@ def run_uneven(a, rank, world, local):
              "ntt_runtime_per_signal": (st["ntt_forward_runtime"] + st["ntt_inverse"]) / cnt,
              "gpu_launches_per_step": st["kernel_launches"],
              "tuning": {"classes": st["classes"], "crt_fused_classes": st["crt_fused_classes"],
-                        "inv_vecs_largest_class": st["inv_vecs"], "row_log_inv_largest_class": st["row_log_inv"]}}
+                        "inv_vecs_largest_class": st["inv_vecs"], "row_log_inv_largest_class": st["row_log_inv"],
+                        "candidates": [" ".join(r) for r in tune_rows]}}
         if rank == 0 and not a.skip_cpu:
             yh = y.cpu().numpy()
             xs, ys = plan.split(xh), plan.split(yh)

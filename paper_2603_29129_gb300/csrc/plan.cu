@@ -762,6 +762,14 @@ static int autotune_ntt(ozfft_plan_s* p)
                       p->status, p->sd, nullptr, p->merge, p->garner_u, 0};
     float best_f = 1e30f, best_i = 1e30f;
     int m2f = p->geom_fwd.m2, m2i = p->geom_inv.m2, fused = p->crt_fused;
+    // OZFFT_TUNE_LOG=path: every candidate's time is appended to that file (one line per
+    // candidate: N, batch, what, row-pass stages, option, ms), for tuning reports
+    FILE* tlog = nullptr;
+    if (const char* path = std::getenv("OZFFT_TUNE_LOG"))
+        if (*path) tlog = std::fopen(path, "a");
+    auto logt = [&](const char* what, int m2, int opt, float ms) {
+        if (tlog) std::fprintf(tlog, "%lld %lld %s %d %d %.4f\n", (long long)p->N, (long long)p->B, what, m2, opt, ms);
+    };
     for (int m2 : cands) {
         if (err != cudaSuccess) break;
         NttGeom gf = p->geom_fwd, gi = p->geom_inv;
@@ -773,6 +781,7 @@ static int autotune_ntt(ozfft_plan_s* p)
         gf.tmap = ntt_make_tmap(&tx, gf, p->X, gf.nvec) ? &tx : nullptr;
         gi.tmap = ntt_make_tmap(&tz, gi, p->Z, gi.nvec) ? &tz : nullptr;
         const float tf = time_ms([&] { return launch_ntt_forward(gf, p->X, p->tw, 0); });
+        logt("forward", m2, 0, tf);
         if (tf < best_f) { best_f = tf; m2f = m2; }
         const bool can_fuse = with_crt && gi.m1 > 0 && colcrt_supported(p->P, gi.m1, gi.m2, p->merge);
         for (int f = 0; f <= 1; ++f) {
@@ -793,6 +802,7 @@ static int autotune_ntt(ozfft_plan_s* p)
                 }
                 return e != cudaSuccess ? e : launch_crt_post(c, 0);
             });
+            logt(with_crt ? (f ? "inverse+crt_fused" : "inverse+crt_apart") : "inverse", m2, f, ti);
             if (ti < best_i) { best_i = ti; m2i = m2; fused = f; }
         }
     }
@@ -811,9 +821,15 @@ static int autotune_ntt(ozfft_plan_s* p)
             for (int v = 1; v <= 2; ++v) {
                 g2.inv_vecs_per_cta = v;
                 t[v] = time_ms([&] { return launch_ntt_inv_row(g2, p->Z, p->twinv, mac, 0); });
+                logt("inverse_row_vecs", g2.m2, v, t[v]);
             }
             if (err == cudaSuccess) gi.inv_vecs_per_cta = t[1] < t[2] ? 1 : 2;
         }
+    }
+    if (tlog) {
+        std::fprintf(tlog, "%lld %lld chosen %d %d %d\n", (long long)p->N, (long long)p->B, m2f, m2i,
+                     (p->crt_fused ? 1 : 0) * 10 + gi.inv_vecs_per_cta);
+        std::fclose(tlog);
     }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
