@@ -65,6 +65,9 @@ def parse(argv=None):
                     help="force 1 or 2 vectors per CTA in the inverse row pass (0: default or autotuned)")
     ap.add_argument("--crt-fuse", type=int, default=0,
                     help="force the inverse column pass fused with the CRT (1) or apart (2); 0: default or autotuned")
+    ap.add_argument("--split-fuse", type=int, default=0,
+                    help="force the Ozaki split fused with the forward column pass (1) or apart (2); "
+                         "0: default or autotuned")
     ap.add_argument("--uneven-count", type=int, default=4096, help="signals of the uneven workload")
     ap.add_argument("--plain-sample", type=int, default=256,
                     help="signals of the uneven workload timed through per-signal plans")
@@ -90,7 +93,7 @@ def workload(a):
                         f"forward, K={a.K}, L={a.L}, {a.nprimes} primes",
             "n": a.n, "batch_per_gpu": a.batch, "K": a.K, "L": a.L, "nprimes": a.nprimes, "seed": a.seed,
             "autotune": a.autotune, "merge": a.merge, "ts": a.ts, "row_log": a.row_log,
-            "inv_vecs": a.inv_vecs, "crt_fuse": a.crt_fuse,
+            "inv_vecs": a.inv_vecs, "crt_fuse": a.crt_fuse, "split_fuse": a.split_fuse,
             "l2": "inputs (batch x n x 16 B) exceed L2 each step; no flush"}
 
 
@@ -595,6 +598,7 @@ def run_uneven(a, rank, world, local):
              "ntt_runtime_per_signal": (st["ntt_forward_runtime"] + st["ntt_inverse"]) / cnt,
              "gpu_launches_per_step": st["kernel_launches"],
              "tuning": {"classes": st["classes"], "crt_fused_classes": st["crt_fused_classes"],
+                        "split_fused_classes": st["split_fused_classes"],
                         "inv_vecs_largest_class": st["inv_vecs"], "row_log_inv_largest_class": st["row_log_inv"],
                         "candidates": [" ".join(r) for r in tune_rows]}}
         if rank == 0 and not a.skip_cpu:
@@ -731,7 +735,8 @@ def main():
     y = torch.empty_like(x)
     stream = torch.cuda.current_stream(dev)
     plan = ozfft.Plan(n, B, ozfft.FORWARD, K=a.K, L=a.L, nprimes=a.nprimes, autotune=a.autotune, merge=a.merge,
-                      ts=a.ts, row_log=a.row_log, inv_vecs=a.inv_vecs, crt_fuse=a.crt_fuse)
+                      ts=a.ts, row_log=a.row_log, inv_vecs=a.inv_vecs, crt_fuse=a.crt_fuse,
+                      split_fuse=a.split_fuse)
 
     # ---- batched, device-resident (the headline value), with per-kernel events
     for _ in range(a.warmup):
@@ -763,7 +768,8 @@ def main():
     plain = None
     if not a.skip_plain:
         p1 = ozfft.Plan(n, 1, ozfft.FORWARD, K=a.K, L=a.L, nprimes=a.nprimes, autotune=a.autotune, merge=a.merge,
-                        ts=a.ts, row_log=a.row_log, inv_vecs=a.inv_vecs, crt_fuse=a.crt_fuse)
+                        ts=a.ts, row_log=a.row_log, inv_vecs=a.inv_vecs, crt_fuse=a.crt_fuse,
+                        split_fuse=a.split_fuse)
         xs = [x[i:i + 1] for i in range(B)]
         ys = [y[i:i + 1] for i in range(B)]
         for _ in range(a.warmup):
@@ -1019,7 +1025,8 @@ def main():
                 "GBps_algorithmic": total_ntt * 8 * N / (ntt_ms / 1e3) / 1e9},
         "kernel_ms_per_step": breakdown, "accuracy": acc,
         "tuning": {"row_log_fwd": stats["row_log_fwd"], "row_log_inv": stats["row_log_inv"],
-                   "inv_vecs": stats["inv_vecs"], "crt_fused": bool(stats["crt_fused_classes"])},
+                   "inv_vecs": stats["inv_vecs"], "crt_fused": bool(stats["crt_fused_classes"]),
+                   "split_fused": bool(stats["split_fused_classes"])},
     }
     print(json.dumps(line), flush=True)
     if dist:

@@ -122,6 +122,11 @@ typedef struct {
                          separate kernels for the length classes of uneven plans, or the
                          autotuner's choice per class), 1 = fused wherever supported, 2 = never
                          fused; results are bit-identical */
+    int32_t split_fuse; /* the Ozaki split fused with the forward NTT's column pass (K <= 4, K P <= 9,
+                         5..8 column stages): the slice residues are transformed on chip before they
+                         reach device memory.  0 = wherever supported (with autotune: the faster of
+                         fused and apart, timed), 1 = wherever supported, 2 = never; never for debug
+                         or TS plans; results are bit-identical */
 } ozfft_options;
 
 /* Create a plan for `batch` transforms of length n in `direction`, with default
@@ -208,6 +213,8 @@ typedef struct {
     int32_t crt_fused_classes;    /* length classes (1 for a plain plan) whose inverse column pass runs
                                      fused with the CRT */
     int32_t classes;              /* length classes (1 for a plain plan) */
+    int32_t split_fused_classes;  /* length classes (1 for a plain plan) whose Ozaki split runs fused
+                                     with the forward NTT's column pass */
 } ozfft_stats;
 int ozfft_get_stats(ozfft_plan_t plan, void* stream, ozfft_stats* out);
 

@@ -15,6 +15,7 @@
 // the grid-wide dependency Alg. 3 has between mu^(k) and sigma^(k).
 #include "oz_common.cuh"
 #include "oz_kernels.h"
+#include "ntt_impl.cuh"
 
 namespace oz {
 
@@ -470,11 +471,12 @@ template <bool SD>
 __global__ void __launch_bounds__(FIX_THREADS) split_fix_kernel(double* __restrict__ r, uint64_t* __restrict__ mu,
                                                                 int64_t N, int K, int alpha,
                                                                 const SigDesc* __restrict__ sd, int P,
-                                                                uint32_t* __restrict__ X)
+                                                                uint32_t* __restrict__ X, int32_t* __restrict__ redo)
 {
     const int64_t v = blockIdx.x;
     if (SD) alpha = sd[v >> 1].alpha;
     uint64_t* mv = mu + v * (K + 1);
+    if (redo && threadIdx.x == 0) redo[v] = 0;
     if (mv[0] == 0) return;
     const int e0 = ceil_log2_pos(__longlong_as_double((long long)mv[0]));
     if (e0 + 53 - alpha > 1023) return;                   // flagged by the speculative pass
@@ -484,6 +486,7 @@ __global__ void __launch_bounds__(FIX_THREADS) split_fix_kernel(double* __restri
         ok = ceil_log2_pos(__longlong_as_double((long long)mv[k])) == e0 - k * alpha;
     }
     if (ok) return;
+    if (redo && threadIdx.x == 0) redo[v] = 1;            // its residues are rewritten untransformed
     __syncthreads();                                      // every thread has read mu before it changes
     __shared__ uint64_t redu[32];
     uint64_t* rv = reinterpret_cast<uint64_t*>(r + v * N);
@@ -519,6 +522,124 @@ __global__ void __launch_bounds__(FIX_THREADS) split_fix_kernel(double* __restri
             mv[k + 1] = t ? pow2_bits(ceil_log2_pos(__longlong_as_double((long long)t))) : 0ull;
         }
         __syncthreads();                                  // mu[v][k + 1] and r^(k + 1) before the next level
+    }
+}
+
+// ------------------------------- split fused with the forward column pass
+// One CTA takes T = 2^(11 - m1) adjacent columns x all 2^m1 rows of one real
+// vector (2048 elements, j = row 2^m2 + col), runs every level of Alg. 3 on
+// them with the guessed exponents of split_spec_kernel (the level maxima
+// reduced into mu for split_fix_kernel's check), writes each level's residues
+// per prime into a dense shared-memory tile [row][T], transforms the columns of
+// all K P tiles (stages 0..m1-1 of the forward NTT, as the column pass does) and
+// stores them into X.  The untransformed residues never reach HBM: against
+// the split and the column pass apart, X is written once instead of written,
+// read and written again.  Consecutive lanes take consecutive columns of a
+// row, so the dense tiles need no pad words for T >= 32 (T = 16 for m1 = 7
+// leaves some 2-way conflicts).
+constexpr int SC_THREADS = 256;
+constexpr int SC_TILE_LOG = 11;
+constexpr int SC_TILE = 1 << SC_TILE_LOG;     // elements per tile
+
+template <int ML, int S0, int RL, int LOG_T>
+__device__ __forceinline__ void sc_round(uint32_t* sm, int ntiles, int P, const uint2* __restrict__ tw_all, int64_t N)
+{
+    constexpr int LOG_H = ML - S0 - RL, H = 1 << LOG_H, LOG_GPC = ML - RL, T = 1 << LOG_T;
+    constexpr int LOG_GPT = LOG_T + LOG_GPC;     // groups per tile = T 2^LOG_GPC
+    for (int gid = threadIdx.x; gid < (ntiles << LOG_GPT); gid += SC_THREADS) {
+        const int tile = gid >> LOG_GPT;
+        const int gg = gid & ((1 << LOG_GPT) - 1);
+        const int c = gg & (T - 1), grp = gg >> LOG_T;
+        const int blk = grp >> LOG_H;
+        const int l0 = (blk << (ML - S0)) + (grp & (H - 1));
+        // prime of tile k P + pi without a division (tile < 9): tile / 3 = (11 tile) >> 5
+        const int pi = P == 1 ? 0 : (P == 2 ? (tile & 1) : tile - 3 * ((tile * 11) >> 5));
+        group_bfly<false, RL, H * T, false>(sm + tile * SC_TILE + (l0 << LOG_T) + c, tw_all + pi * N, (1 << S0) + blk,
+                                            prime_of(pi));
+    }
+}
+
+template <int ML, int LOG_T, int I>
+__device__ __forceinline__ void sc_rounds(uint32_t* sm, int ntiles, int P, const uint2* tw_all, int64_t N)
+{
+    if constexpr (I < Part<ML>::NR) {
+        sc_round<ML, Part<ML>::start(I), Part<ML>::size(I), LOG_T>(sm, ntiles, P, tw_all, N);
+        __syncthreads();
+        sc_rounds<ML, LOG_T, I + 1>(sm, ntiles, P, tw_all, N);
+    }
+}
+
+template <bool SD, int M1, int KM, bool A30>
+__global__ void __launch_bounds__(SC_THREADS) split_col_kernel(const double* __restrict__ r, uint64_t* __restrict__ mu,
+                                                               int64_t N, int m2, int K, int alpha,
+                                                               const SigDesc* __restrict__ sd, int P,
+                                                               uint32_t* __restrict__ X, const uint2* __restrict__ tw_all,
+                                                               int* status)
+{
+    constexpr int LOG_T = SC_TILE_LOG - M1, T = 1 << LOG_T;
+    static_assert(T >= 8, "16-byte row segments");
+    extern __shared__ __align__(16) uint32_t sct[];      // K P tiles of SC_TILE words
+    const int lg_tpv = m2 - LOG_T;
+    const int64_t v = blockIdx.x >> lg_tpv;
+    const int c0 = (int)(blockIdx.x & ((1u << lg_tpv) - 1)) << LOG_T;
+    if (SD) alpha = sd[v >> 1].alpha;
+    const uint64_t mub = mu[v * (K + 1)];
+    if (mub == 0) return;                                 // every level empty
+    const int e0 = ceil_log2_pos(__longlong_as_double((long long)mub));
+    if (e0 + 53 - alpha > 1023) {
+        if (threadIdx.x == 0) atomicOr(status, ST_RANGE);
+        return;
+    }
+    const uint64_t* rv = reinterpret_cast<const uint64_t*>(r + v * N);
+    int cmax[KM];
+#pragma unroll
+    for (int k = 0; k < KM; ++k) cmax[k] = -2000;
+#pragma unroll 2
+    for (int e = threadIdx.x; e < SC_TILE; e += SC_THREADS) {
+        const uint64_t rb = rv[((int64_t)(e >> LOG_T) << m2) + c0 + (e & (T - 1))];
+        bool neg = (rb >> 63) != 0;
+        const int Eb = (int)((rb >> 52) & 0x7ff);
+        uint64_t a = rb & ((1ull << 52) - 1);
+        int E = -1074;
+        if (Eb) { a |= 1ull << 52; E = Eb - 1075; }
+#pragma unroll
+        for (int k = 0; k < KM; ++k) {
+            if (k >= K) break;
+            if constexpr (A30) {                          // |q| <= 2^alpha < p
+                const int32_t q = split_level_fixed32(a, neg, E, e0 - k * alpha, alpha);
+#pragma unroll
+                for (int pi = 0; pi < MAX_PRIMES; ++pi) {
+                    if (pi >= P) break;
+                    const uint32_t p = prime_of(pi);
+                    sct[(k * P + pi) * SC_TILE + e] = q < 0 ? (uint32_t)(q + (int32_t)p) : (uint32_t)q;
+                }
+            } else {
+                const long long q = split_level_fixed(a, neg, E, e0 - k * alpha, alpha);
+#pragma unroll
+                for (int pi = 0; pi < MAX_PRIMES; ++pi) {
+                    if (pi >= P) break;
+                    long long t = q % (long long)prime_of(pi);
+                    if (t < 0) t += prime_of(pi);
+                    sct[(k * P + pi) * SC_TILE + e] = (uint32_t)t;
+                }
+            }
+            if (a) cmax[k] = max(cmax[k], ceil_log2_fixed(a, E));
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < KM; ++k) {
+        if (k >= K) break;
+        block_umax_to(&mu[v * (K + 1) + k + 1], cmax[k] > -2000 ? pow2_bits(cmax[k]) : 0ull);
+        __syncthreads();                                  // also: every residue tile is complete
+    }
+    sc_rounds<M1, LOG_T, 0>(sct, K * P, P, tw_all, N);
+    // store: 16-byte row segments of each tile (vector (v K + k) P + pi of X)
+    constexpr int Q = SC_TILE / 4;
+    for (int q = threadIdx.x; q < K * P * Q; q += SC_THREADS) {
+        const int tile = q / Q, w = q - tile * Q;
+        const int row = w >> (LOG_T - 2), c = (w & ((T >> 2) - 1)) << 2;
+        const uint4 val = *reinterpret_cast<const uint4*>(sct + tile * SC_TILE + (row << LOG_T) + c);
+        *reinterpret_cast<uint4*>(X + (v * K * P + tile) * N + ((int64_t)row << m2) + c0 + c) = val;
     }
 }
 
@@ -568,13 +689,63 @@ cudaError_t launch_split_spec(double* r, uint64_t* mu, int64_t N, int64_t nvec, 
     if (sd) {
         if (K <= 4) { if (a30) OZ_SPLIT_SPEC(true, 4, true); else OZ_SPLIT_SPEC(true, 4, false); }
         else { if (a30) OZ_SPLIT_SPEC(true, MAX_K, true); else OZ_SPLIT_SPEC(true, MAX_K, false); }
-        split_fix_kernel<true><<<(unsigned)nvec, FIX_THREADS, 0, s>>>(r, mu, N, K, alpha, sd, P, X);
+        split_fix_kernel<true><<<(unsigned)nvec, FIX_THREADS, 0, s>>>(r, mu, N, K, alpha, sd, P, X, nullptr);
     } else {
         if (K <= 4) { if (a30) OZ_SPLIT_SPEC(false, 4, true); else OZ_SPLIT_SPEC(false, 4, false); }
         else { if (a30) OZ_SPLIT_SPEC(false, MAX_K, true); else OZ_SPLIT_SPEC(false, MAX_K, false); }
-        split_fix_kernel<false><<<(unsigned)nvec, FIX_THREADS, 0, s>>>(r, mu, N, K, alpha, sd, P, X);
+        split_fix_kernel<false><<<(unsigned)nvec, FIX_THREADS, 0, s>>>(r, mu, N, K, alpha, sd, P, X, nullptr);
     }
 #undef OZ_SPLIT_SPEC
+    return cudaGetLastError();
+}
+
+bool split_col_supported(int K, int P, int m1, int m2)
+{
+    return K >= 1 && K <= 4 && K * P <= 9 && m1 >= 5 && m1 <= 8 && m2 >= SC_TILE_LOG - m1;
+}
+
+template <bool SD, int M1>
+static cudaError_t launch_split_col_m(double* r, uint64_t* mu, int64_t N, int m2, int64_t nvec, int K, int alpha,
+                                      const SigDesc* sd, int P, uint32_t* X, const uint2* tw, int* status,
+                                      cudaStream_t s)
+{
+    const size_t smem = (size_t)K * P * SC_TILE * sizeof(uint32_t);
+    const unsigned grid = (unsigned)(nvec << (m2 - (SC_TILE_LOG - M1)));
+    cudaError_t e;
+    if (alpha <= 30) {
+        e = cudaFuncSetAttribute(split_col_kernel<SD, M1, 4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        split_col_kernel<SD, M1, 4, true><<<grid, SC_THREADS, smem, s>>>(r, mu, N, m2, K, alpha, sd, P, X, tw, status);
+    } else {
+        e = cudaFuncSetAttribute(split_col_kernel<SD, M1, 4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        split_col_kernel<SD, M1, 4, false><<<grid, SC_THREADS, smem, s>>>(r, mu, N, m2, K, alpha, sd, P, X, tw, status);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_split_col(double* r, uint64_t* mu, int64_t N, int m1, int m2, int64_t nvec, int K, int alpha,
+                             const SigDesc* sd, int P, uint32_t* X, const uint2* tw, int32_t* redo, int* status,
+                             cudaStream_t s)
+{
+    if (!split_col_supported(K, P, m1, m2)) return cudaErrorInvalidValue;
+    cudaError_t e = cudaErrorInvalidValue;
+    switch (m1) {
+    case 5: e = sd ? launch_split_col_m<true, 5>(r, mu, N, m2, nvec, K, alpha, sd, P, X, tw, status, s)
+                   : launch_split_col_m<false, 5>(r, mu, N, m2, nvec, K, alpha, sd, P, X, tw, status, s); break;
+    case 6: e = sd ? launch_split_col_m<true, 6>(r, mu, N, m2, nvec, K, alpha, sd, P, X, tw, status, s)
+                   : launch_split_col_m<false, 6>(r, mu, N, m2, nvec, K, alpha, sd, P, X, tw, status, s); break;
+    case 7: e = sd ? launch_split_col_m<true, 7>(r, mu, N, m2, nvec, K, alpha, sd, P, X, tw, status, s)
+                   : launch_split_col_m<false, 7>(r, mu, N, m2, nvec, K, alpha, sd, P, X, tw, status, s); break;
+    case 8: e = sd ? launch_split_col_m<true, 8>(r, mu, N, m2, nvec, K, alpha, sd, P, X, tw, status, s)
+                   : launch_split_col_m<false, 8>(r, mu, N, m2, nvec, K, alpha, sd, P, X, tw, status, s); break;
+    default: break;
+    }
+    if (e != cudaSuccess) return e;
+    // the check: vectors whose guessed exponents fail are redone level by level,
+    // untransformed, and flagged for the column pass
+    if (sd) split_fix_kernel<true><<<(unsigned)nvec, FIX_THREADS, 0, s>>>(r, mu, N, K, alpha, sd, P, X, redo);
+    else split_fix_kernel<false><<<(unsigned)nvec, FIX_THREADS, 0, s>>>(r, mu, N, K, alpha, sd, P, X, redo);
     return cudaGetLastError();
 }
 

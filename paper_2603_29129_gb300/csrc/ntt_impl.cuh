@@ -204,6 +204,7 @@ __device__ __forceinline__ bool fwd_live(const NttGeom& g, unsigned vec)
 {
     const unsigned bv = vec / (unsigned)(g.P * g.K);
     const int k = (int)((vec / (unsigned)g.P) % (unsigned)g.K);
+    if (g.redo && !g.redo[bv]) return false;   // transformed already by the fused split
     return k < g.kcnt[bv];
 }
 __device__ __forceinline__ bool inv_live(const NttGeom& g, unsigned vec)

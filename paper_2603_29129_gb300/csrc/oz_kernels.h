@@ -49,6 +49,8 @@ struct NttGeom {
     int64_t vec0;          // index of the launch's first vector in that map
     int* status;           // status word for bounded waits that give up
     uint32_t extra_tx;     // self-test only: bytes the barrier expects beyond the tile (0)
+    const int32_t* redo;   // forward column pass after the fused split: [B][2] nonzero for the real
+                           // vectors split_fix_kernel redid (only those are transformed); null: all
 };
 
 // tensor map of a buffer of nvec vectors of 2^m1 x 2^m2 residues, box = one
@@ -104,6 +106,15 @@ cudaError_t launch_split_level(int k, double* r, const uint64_t* mu_in, uint64_t
 cudaError_t launch_split_spec(double* r, uint64_t* mu, int64_t N, int64_t nvec, int K, int alpha, const SigDesc* sd,
                               int P, uint32_t* X, int* status, cudaStream_t s);
 constexpr int SPLIT_SPEC_LAUNCHES = 2;
+// the same split fused with the forward NTT's column pass (stages 0..m1-1, table
+// tw): every level's residues are transformed on chip before they reach X.
+// Vectors whose guessed level exponents fail are redone untransformed by the
+// check kernel, which sets redo[v]; a column pass with NttGeom.redo = redo must
+// follow (after the schedule).  split_col_supported tells where it applies.
+bool split_col_supported(int K, int P, int m1, int m2);
+cudaError_t launch_split_col(double* r, uint64_t* mu, int64_t N, int m1, int m2, int64_t nvec, int K, int alpha,
+                             const SigDesc* sd, int P, uint32_t* X, const uint2* tw, int32_t* redo, int* status,
+                             cudaStream_t s);
 cudaError_t launch_set_io(IoPtrs* io, const void* in, void* out, cudaStream_t s);
 
 // k_crt.cu

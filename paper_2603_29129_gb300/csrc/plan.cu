@@ -133,8 +133,10 @@ struct ozfft_plan_s {
     int direction = -1, K = 3, L = 1, P = 2, alpha = 0, G = 9, debug = 0, merge = 0, ts = 0;
     int kinf = 0;                // K = infinity: K holds the level cap MAX_K
     int crt_fused = 1;           // inverse column pass fused with the CRT where colcrt_supported
+    int split_fused = 1;         // the split fused with the forward column pass where split_col_supported
     int tune_vecs = 1;           // the autotuner may choose the inverse row pass's vectors per CTA
     int tune_fuse = 1;           // ... and whether the inverse column pass is fused with the CRT
+    int tune_sfuse = 1;          // ... and whether the split is fused with the forward column pass
     int garner_u = 0;            // every convolution value |z| < p0 p1 / 2 - p0 (CRT without centering z0)
     int64_t chunk = 1;           // signals per inverse-stage chunk (Z holds one chunk)
     int device = 0;
@@ -155,6 +157,7 @@ struct ozfft_plan_s {
     int32_t* kcnt = nullptr;
     Sched* sched = nullptr;
     int32_t* span = nullptr;     // [B][3] scale span of each signal's flush groups
+    int32_t* redo = nullptr;     // [B][2] vectors the split's check redid (fused split + column pass)
     uint32_t* Z = nullptr;
     int* status = nullptr;
     double* dbg_r = nullptr;     // [B][2][N] (debug plans)
@@ -426,11 +429,24 @@ __global__ void ymont_kernel(uint32_t* Y, int64_t N, int64_t total, int P, uint3
     }
 }
 
+// autotuner input of the split: r uniform in (-1, 1) from a counter hash, every
+// vector's mu[v][0] = 1 (e_0 = 0) and the level maxima cleared
+__global__ void tune_fill_kernel(double* r, uint64_t* mu, int64_t N, int64_t nvec, int K)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nvec * N; i += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t z = (uint64_t)i * 0x9e3779b97f4a7c15ull + 0x632be59bd9b4e019ull;
+        z = (z ^ (z >> 29)) * 0xbf58476d1ce4e5b9ull;
+        z ^= z >> 32;
+        r[i] = ((double)(z >> 11) * 0x1.0p-53) * 2.0 - 1.0;
+        if (i < nvec * (K + 1)) mu[i] = i % (K + 1) == 0 ? 0x3ff0000000000000ull : 0ull;
+    }
+}
+
 // ------------------------------------------------------------ plan lifetime
 static void plan_free(ozfft_plan_s* p)
 {
     void* ptrs[] = {p->chirp, p->tw, p->twinv, p->Ym, p->wk, p->wsexp, p->r, p->mu, p->X, p->kcnt, p->sched,
-                    p->span, p->Z, p->status, p->dbg_r, p->dbg_X, p->stage_in, p->stage_out, p->sd, p->io};
+                    p->span, p->Z, p->status, p->dbg_r, p->dbg_X, p->stage_in, p->stage_out, p->sd, p->io, p->redo};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     for (ozfft_plan_s* c : p->classes) plan_free(c);
@@ -567,6 +583,7 @@ static int plan_build(ozfft_plan_s* p)
     if ((rc = dalloc(p, &p->span, (size_t)B * 3))) return rc;
     if ((rc = dalloc(p, &p->Z, (size_t)p->chunk * 4 * p->G * P * N))) return rc;
     if ((rc = dalloc(p, &p->status, 1))) return rc;
+    if ((rc = dalloc(p, &p->redo, (size_t)B * 2))) return rc;
     if (p->debug) {
         if ((rc = dalloc(p, &p->dbg_r, (size_t)B * 2 * N))) return rc;
         if ((rc = dalloc(p, &p->dbg_X, (size_t)B * 2 * K * P * N))) return rc;
@@ -697,7 +714,9 @@ static int force_split(ozfft_plan_s* p, int m2)
 // The inverse side is timed with what follows it: the inverse column pass
 // fused with the CRT or the column pass and the CRT apart (each where allowed),
 // so the split and the fusion are chosen together; then, at that choice, one
-// or two vectors per CTA in the inverse row pass.  Each choice changes only
+// or two vectors per CTA in the inverse row pass.  The forward side is timed
+// with the Ozaki split before it (on uniform synthetic input), fused with the
+// column pass or apart, so its split and fusion are chosen together too.  Each choice changes only
 // the order in which the same operations run, so results are bit-identical.
 static int autotune_ntt(ozfft_plan_s* p)
 {
@@ -757,11 +776,19 @@ static int autotune_ntt(ozfft_plan_s* p)
         }
         return best;
     };
+    // the forward side with its split: synthetic split input in r and mu
+    const bool with_split = !p->ts && !p->debug;
+    if (with_split && err == cudaSuccess) {
+        const int64_t nv = B * 2;
+        tune_fill_kernel<<<(unsigned)std::min<int64_t>((nv * p->N + 255) / 256, 65535), 256>>>(p->r, p->mu, p->N, nv,
+                                                                                             (int)K);
+        err = cudaGetLastError();
+    }
     const MacSrc mac{p->X, p->Ym, p->ym_stride};
     const CrtArgs ca0{p->Z, p->sched, p->span, p->chirp, tout, p->n, p->N, p->chunk, p->P, p->G, p->direction,
                       p->status, p->sd, nullptr, p->merge, p->garner_u, 0};
     float best_f = 1e30f, best_i = 1e30f;
-    int m2f = p->geom_fwd.m2, m2i = p->geom_inv.m2, fused = p->crt_fused;
+    int m2f = p->geom_fwd.m2, m2i = p->geom_inv.m2, fused = p->crt_fused, sfused = p->split_fused;
     // OZFFT_TUNE_LOG=path: every candidate's time is appended to that file (one line per
     // candidate: N, batch, what, row-pass stages, option, ms), for tuning reports
     FILE* tlog = nullptr;
@@ -780,9 +807,27 @@ static int autotune_ntt(ozfft_plan_s* p)
         CUtensorMap tx{}, tz{};   // this split's tensor maps, so the candidates run the kernels they would use
         gf.tmap = ntt_make_tmap(&tx, gf, p->X, gf.nvec) ? &tx : nullptr;
         gi.tmap = ntt_make_tmap(&tz, gi, p->Z, gi.nvec) ? &tz : nullptr;
-        const float tf = time_ms([&] { return launch_ntt_forward(gf, p->X, p->tw, 0); });
-        logt("forward", m2, 0, tf);
-        if (tf < best_f) { best_f = tf; m2f = m2; }
+        const bool can_sfuse = with_split && gf.m1 > 0 && split_col_supported((int)K, p->P, gf.m1, gf.m2);
+        for (int f = 0; f <= 1; ++f) {
+            if (f && !(can_sfuse && (p->tune_sfuse || p->split_fused))) continue;
+            if (!f && !p->tune_sfuse && p->split_fused && can_sfuse) continue;   // fusion forced where it applies
+            const float tf = time_ms([&] {
+                if (!with_split) return launch_ntt_forward(gf, p->X, p->tw, 0);
+                cudaError_t e;
+                NttGeom gc = gf;
+                if (f) {
+                    e = launch_split_col(p->r, p->mu, p->N, gf.m1, gf.m2, B * 2, (int)K, p->alpha, p->sd, p->P, p->X,
+                                         p->tw, p->redo, p->status, 0);
+                    gc.redo = p->redo;
+                } else {
+                    e = launch_split_spec(p->r, p->mu, p->N, B * 2, (int)K, p->alpha, p->sd, p->P, p->X, p->status, 0);
+                }
+                if (e == cudaSuccess && gc.m1 > 0) e = launch_ntt_fwd_col(gc, p->X, p->tw, 0);
+                return e != cudaSuccess ? e : launch_ntt_fwd_row(gf, p->X, p->tw, 0);
+            });
+            logt(with_split ? (f ? "split+forward_fused" : "split+forward_apart") : "forward", m2, f, tf);
+            if (tf < best_f) { best_f = tf; m2f = m2; sfused = f; }
+        }
         const bool can_fuse = with_crt && gi.m1 > 0 && colcrt_supported(p->P, gi.m1, gi.m2, p->merge);
         for (int f = 0; f <= 1; ++f) {
             if (f && !(can_fuse && (p->tune_fuse || p->crt_fused))) continue;
@@ -811,6 +856,7 @@ static int autotune_ntt(ozfft_plan_s* p)
         ntt_configure_split(p->geom_fwd, p->N, m2f);
         ntt_configure_split(p->geom_inv, p->N, m2i);
         if (p->tune_fuse && with_crt) p->crt_fused = fused;
+        if (p->tune_sfuse && with_split) p->split_fused = sfused;
     }
     // at the chosen split and fusion: one or two vectors per CTA in the inverse row pass
     if (err == cudaSuccess && p->tune_vecs) {
@@ -828,7 +874,7 @@ static int autotune_ntt(ozfft_plan_s* p)
     }
     if (tlog) {
         std::fprintf(tlog, "%lld %lld chosen %d %d %d\n", (long long)p->N, (long long)p->B, m2f, m2i,
-                     (p->crt_fused ? 1 : 0) * 10 + gi.inv_vecs_per_cta);
+                     (p->split_fused ? 1 : 0) * 100 + (p->crt_fused ? 1 : 0) * 10 + gi.inv_vecs_per_cta);
         std::fclose(tlog);
     }
     if (e0) cudaEventDestroy(e0);
@@ -839,6 +885,7 @@ static int autotune_ntt(ozfft_plan_s* p)
     CUDA_TRY(cudaMemset(p->sched, 0, sizeof(Sched) * B * 4));
     CUDA_TRY(cudaMemset(p->span, 0, sizeof(int32_t) * B * 3));
     CUDA_TRY(cudaMemset(p->status, 0, sizeof(int)));
+    CUDA_TRY(cudaMemset(p->redo, 0, sizeof(int32_t) * B * 2));
     p->geom_fwd.nvec = gf.nvec; p->geom_fwd.P = gf.P; p->geom_fwd.K = gf.K; p->geom_fwd.G = gf.G;
     p->geom_fwd.kcnt = gf.kcnt; p->geom_fwd.sched = gf.sched;
     p->geom_inv.nvec = gi.nvec; p->geom_inv.P = gi.P; p->geom_inv.K = gi.K; p->geom_inv.G = gi.G;
@@ -867,6 +914,11 @@ static int run_plan_range(ozfft_plan_s* p, const void* in, void* out, cudaStream
     const SigDesc* sd = p->sd ? p->sd + sb0 : nullptr;
     const uint32_t* Ym = p->Ym + sb0 * p->ym_stride;
     const bool whole = sb0 == 0 && B == p->B;
+    int32_t* redo = p->redo + sb0 * 2;
+    // the split fused with the forward column pass (the residues are transformed on
+    // chip), unless the stage dumps need the untransformed residues or the plan is TS
+    const bool fuse_fwd = !p->ts && !p->debug && p->split_fused && p->geom_fwd.m1 > 0 &&
+                          split_col_supported(K, P, p->geom_fwd.m1, p->geom_fwd.m2);
     CUDA_TRY(cudaMemsetAsync(mu, 0, sizeof(uint64_t) * B * 2 * (K + 1), s));
     p->cur = nullptr;
     if (p->profiling) {
@@ -897,6 +949,10 @@ static int run_plan_range(ozfft_plan_s* p, const void* in, void* out, cudaStream
                 CUDA_TRY(launch_ts_split_level(k, (float*)r, mu, N, B * 2, K, p->alpha, P, X, k + 1 < K, p->status, s));
                 mark(p, OZFFT_PROF_SPLIT, s);
             }
+        } else if (fuse_fwd) {
+            CUDA_TRY(launch_split_col(r, mu, N, p->geom_fwd.m1, p->geom_fwd.m2, B * 2, K, p->alpha, sd, P, X, p->tw,
+                                      redo, p->status, s));
+            mark(p, OZFFT_PROF_SPLIT, s);
         } else {
             CUDA_TRY(launch_split_spec(r, mu, N, B * 2, K, p->alpha, sd, P, X, p->status, s));
             mark(p, OZFFT_PROF_SPLIT, s);
@@ -915,7 +971,9 @@ static int run_plan_range(ozfft_plan_s* p, const void* in, void* out, cudaStream
     gf.vec0 = sb0 * 2 * K * P;   // the launch's first vector in the tensor map of X
     StageRange range_fwd("forward NTTs");
     if (gf.m1 > 0) {
-        CUDA_TRY(launch_ntt_fwd_col(gf, X, p->tw, s));
+        NttGeom gc = gf;
+        if (fuse_fwd) gc.redo = redo;   // only the vectors the split's check redid
+        CUDA_TRY(launch_ntt_fwd_col(gc, X, p->tw, s));
         mark(p, OZFFT_PROF_NTT_FWD_COL, s);
     }
     CUDA_TRY(launch_ntt_fwd_row(gf, X, p->tw, s));
@@ -1019,8 +1077,9 @@ ozfft_plan_t ozfft_plan_ex(int64_t n, int64_t batch, int direction, const ozfft_
         fail(OZFFT_ERR_LENGTH, "ozfft_plan: convolution length must be a power of two <= 2^24, equal to n or >= 2n-1");
         return nullptr;
     }
-    if (o.inv_vecs < 0 || o.inv_vecs > 2 || o.crt_fuse < 0 || o.crt_fuse > 2) {
-        fail(OZFFT_ERR_ARG, "ozfft_plan: inv_vecs must be 0..2 and crt_fuse 0..2");
+    if (o.inv_vecs < 0 || o.inv_vecs > 2 || o.crt_fuse < 0 || o.crt_fuse > 2 || o.split_fuse < 0 ||
+        o.split_fuse > 2) {
+        fail(OZFFT_ERR_ARG, "ozfft_plan: inv_vecs, crt_fuse and split_fuse must be 0..2");
         return nullptr;
     }
     if (o.ts && (P != 2 || o.merge || kinf)) {
@@ -1062,6 +1121,8 @@ ozfft_plan_t ozfft_plan_ex(int64_t n, int64_t batch, int direction, const ozfft_
     }
     p->total = n * batch;
     p->crt_fused = o.crt_fuse != 2;
+    p->split_fused = o.split_fuse != 2;
+    p->tune_sfuse = o.split_fuse == 0;
     p->tune_fuse = o.crt_fuse == 0;
     p->tune_vecs = o.inv_vecs == 0;
     if (plan_build(p) != OZFFT_OK) {
@@ -1096,7 +1157,8 @@ ozfft_plan_t ozfft_plan_many(const int64_t* lengths, int64_t count, int directio
     if (!lengths || count < 1 || (direction != OZFFT_FORWARD && direction != OZFFT_INVERSE &&
                                   direction != OZFFT_ADJOINT && direction != OZFFT_INVERSE_ADJOINT) ||
         K < 1 || K > MAX_K || L < 1 || L > MAX_L || P < 2 || P > 3 || o.conv_len != 0 || o.debug != 0 || o.chunk < 0 ||
-        o.ts != 0 || o.inv_vecs < 0 || o.inv_vecs > 2 || o.crt_fuse < 0 || o.crt_fuse > 2) {
+        o.ts != 0 || o.inv_vecs < 0 || o.inv_vecs > 2 || o.crt_fuse < 0 || o.crt_fuse > 2 || o.split_fuse < 0 ||
+        o.split_fuse > 2) {
         fail(OZFFT_ERR_ARG, "ozfft_plan_many: argument out of range");
         return nullptr;
     }
@@ -1190,6 +1252,8 @@ ozfft_plan_t ozfft_plan_many(const int64_t* lengths, int64_t count, int directio
         q->chunk = o.chunk > 0 ? std::min<int64_t>(o.chunk, q->B)
                                : std::max<int64_t>(1, std::min<int64_t>(q->B, (int64_t)(q->B * frac)));
         q->crt_fused = o.crt_fuse == 1;   // length classes keep the CRT apart unless forced or tuned
+        q->split_fused = o.split_fuse != 2;
+        q->tune_sfuse = o.split_fuse == 0;
         q->tune_fuse = o.crt_fuse == 0;
         q->tune_vecs = o.inv_vecs == 0;
         if (plan_build(q) != OZFFT_OK) return bail(0, "");
@@ -1499,6 +1563,9 @@ int ozfft_get_stats(ozfft_plan_t p, void* stream, ozfft_stats* out)
         const NttGeom& gi = q->geom_inv;
         out->crt_fused_classes += !q->ts && !q->debug && q->crt_fused && gi.m1 > 0 &&
                                   colcrt_supported(q->P, gi.m1, gi.m2, q->merge);
+        const NttGeom& gf = q->geom_fwd;
+        out->split_fused_classes += !q->ts && !q->debug && q->split_fused && gf.m1 > 0 &&
+                                    split_col_supported(q->K, q->P, gf.m1, gf.m2);
     }
     std::vector<ozfft_plan_s*> parts = p->classes;
     if (parts.empty()) parts.push_back(p);

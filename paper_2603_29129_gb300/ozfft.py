@@ -35,7 +35,7 @@ class Options(C.Structure):
     _fields_ = [("K", C.c_int32), ("L", C.c_int32), ("nprimes", C.c_int32), ("conv_len", C.c_int64),
                 ("debug", C.c_int32), ("chunk", C.c_int32), ("autotune", C.c_int32), ("no_graph", C.c_int32),
                 ("merge", C.c_int32), ("row_log", C.c_int32), ("ts", C.c_int32), ("inv_vecs", C.c_int32),
-                ("crt_fuse", C.c_int32)]
+                ("crt_fuse", C.c_int32), ("split_fuse", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -45,7 +45,7 @@ class Stats(C.Structure):
                 ("ntt_forward_runtime", C.c_int64), ("ntt_forward_plan", C.c_int64), ("ntt_inverse", C.c_int64),
                 ("kernel_launches", C.c_int64), ("workspace_bytes", C.c_int64),
                 ("row_log_fwd", C.c_int32), ("row_log_inv", C.c_int32), ("inv_vecs", C.c_int32),
-                ("crt_fused_classes", C.c_int32), ("classes", C.c_int32)]
+                ("crt_fused_classes", C.c_int32), ("classes", C.c_int32), ("split_fused_classes", C.c_int32)]
 
 
 class Profile(C.Structure):
@@ -116,13 +116,13 @@ class Plan:
     """A plan for `batch` transforms of length n (see ozfft_plan_ex)."""
 
     def __init__(self, n, batch=1, direction=FORWARD, K=3, L=1, nprimes=2, conv_len=0, debug=False, chunk=0,
-                 autotune=False, merge=False, ts=False, row_log=0, inv_vecs=0, crt_fuse=0):
+                 autotune=False, merge=False, ts=False, row_log=0, inv_vecs=0, crt_fuse=0, split_fuse=0):
         lib = load()
         self.n, self.batch, self.direction = int(n), int(batch), int(direction)
         self.K, self.L, self.nprimes, self.merge, self.ts = int(K), int(L), int(nprimes), bool(merge), bool(ts)
         self.levels = K_INF_CAP if self.K == K_INF else self.K   # level dimension of the buffers
         opt = Options(self.K, self.L, self.nprimes, int(conv_len), int(bool(debug)), int(chunk), int(bool(autotune)), 0,
-                      int(self.merge), int(row_log), int(self.ts), int(inv_vecs), int(crt_fuse))
+                      int(self.merge), int(row_log), int(self.ts), int(inv_vecs), int(crt_fuse), int(split_fuse))
         self._h = lib.ozfft_plan_ex(self.n, self.batch, self.direction, C.byref(opt))
         if not self._h:
             raise OzfftError(-1, lib.ozfft_last_error().decode())
@@ -251,7 +251,7 @@ class PlanMany(Plan):
     output are packed, signal i at elements [offsets[i], offsets[i+1])."""
 
     def __init__(self, lengths, direction=FORWARD, K=3, L=1, nprimes=2, chunk=0, autotune=False, graph=True,
-                 merge=False, row_log=0, inv_vecs=0, crt_fuse=0):
+                 merge=False, row_log=0, inv_vecs=0, crt_fuse=0, split_fuse=0):
         lib = load()
         lens = np.ascontiguousarray(np.asarray(lengths, dtype=np.int64))
         self.lengths = lens
@@ -260,7 +260,7 @@ class PlanMany(Plan):
         self.levels = K_INF_CAP if self.K == K_INF else self.K
         self.merge = bool(merge)
         opt = Options(self.K, self.L, self.nprimes, 0, 0, int(chunk), int(bool(autotune)), int(not graph),
-                      int(self.merge), int(row_log), 0, int(inv_vecs), int(crt_fuse))
+                      int(self.merge), int(row_log), 0, int(inv_vecs), int(crt_fuse), int(split_fuse))
         self._h = lib.ozfft_plan_many(lens.ctypes.data_as(C.POINTER(C.c_int64)), lens.size, self.direction,
                                       C.byref(opt))
         if not self._h:

@@ -43,10 +43,10 @@ def _plan_bit_exact(oz, n=4096, seed=92):
         assert np.array_equal(y[b].view(np.uint64), oracle.ozfft(x[b])[0].view(np.uint64)), b
 
 
-@pytest.mark.parametrize("spec", ["alloc", "alloc:1", "alloc:4", "alloc:9", "alloc:14"])
+@pytest.mark.parametrize("spec", ["alloc", "alloc:1", "alloc:4", "alloc:9", "alloc:15"])
 def test_injected_allocation_failure_in_plan_creation(oz, monkeypatch, spec):
     """OZFFT_FAULT=alloc[:N] fails a device allocation while the plan is built
-    (the first, middle ones, the last of the 14 a plain plan makes); creation
+    (the first, middle ones, the last of the 15 a plain plan makes); creation
     reports it and frees what it had allocated, and the next plan on the same
     context is bit-exact."""
     monkeypatch.setenv("OZFFT_FAULT", spec)
