@@ -388,6 +388,82 @@ __device__ __forceinline__ void inv_middle_rounds(uint32_t* sm, const PassArgs& 
     }
 }
 
+// Twiddles of the inverse row pass's middle and last rounds staged in shared
+// memory (one row per CTA and three rounds): the 2^S0 blocks of the middle
+// round take 2^RL - 1 table entries each, the last round's single block
+// 2^RL0 - 1, laid out per block in radix_group's order w[1], w[2..3], w[4..7],
+// w[8..15]; the CTA copies them while its first round forms the Alg. 8 sums.
+#ifndef OZ_TW_STAGE
+#define OZ_TW_STAGE 1
+#endif
+template <int ML>
+struct InvTw {
+    static constexpr int NR = Part<ML>::NR;
+    static constexpr bool ON = OZ_TW_STAGE && NR == 3;
+    static constexpr int S0M = Part<ML>::start(1), RLM = Part<ML>::size(1), RL0 = Part<ML>::size(0);
+    static constexpr int PER = (1 << RLM) - 1, MID = (1 << S0M) * PER, TOTAL = MID + (1 << RL0) - 1;
+};
+
+template <int ML>
+__device__ __forceinline__ void stage_inv_tw(uint2* tws, const uint2* __restrict__ tw, int rbase)
+{
+    using T = InvTw<ML>;
+    for (int e = threadIdx.x; e < T::TOTAL; e += NTT_THREADS) {
+        const bool mid = e < T::MID;
+        const int blk = mid ? e / T::PER : 0;
+        const int k = (mid ? e - blk * T::PER : e - T::MID) + 1;   // radix_group's index (1 << j) + q
+        const int j = 31 - __clz(k);
+        const int B0 = mid ? (rbase << T::S0M) + blk : rbase;
+        tws[e] = __ldg(tw + (B0 << j) + (k - (1 << j)));
+    }
+}
+
+template <int RL>
+__device__ __forceinline__ void radix_group_inv_staged(uint32_t (&v)[1 << RL], const uint2* tws, uint32_t p)
+{
+    constexpr int R = 1 << RL;
+    uint2 w[R];
+#pragma unroll
+    for (int k = 1; k < R; ++k) w[k] = tws[k - 1];
+#pragma unroll
+    for (int j = RL - 1; j >= 0; --j) {
+        const int half = R >> (j + 1);
+#pragma unroll
+        for (int u = 0; u < R; ++u) {
+            if (u & half) continue;
+            bfly_gs(v[u], v[u + half], w[(1 << j) + (u >> (RL - j))], p);
+        }
+    }
+}
+
+// the middle round of a one-row tile with staged twiddles (row_round's map)
+template <int ML>
+__device__ __forceinline__ void inv_middle_round_staged(uint32_t* sm, const uint2* tws, uint32_t p)
+{
+    using T = InvTw<ML>;
+    constexpr int S0 = T::S0M, RL = T::RLM, R = 1 << RL;
+    constexpr int LOG_H = ML - S0 - RL, H = 1 << LOG_H, LOG_GPC = ML - RL;
+    constexpr bool PERM = LOG_H == 4 && ML - S0 >= 6 && ML - S0 <= 8;
+    constexpr int D = 9 - (ML - S0);
+#pragma unroll 1
+    for (int gid = threadIdx.x; gid < (1 << LOG_GPC); gid += NTT_THREADS) {
+        int grp = gid;
+        if constexpr (PERM) {
+            const int b = grp >> 4;
+            const int sw = (b ^ (b >> D)) & 1;
+            grp ^= (sw | (sw << D)) << 4;
+        }
+        const int blk = grp >> LOG_H;
+        uint32_t* smp = sm + pad_idx((blk << (ML - S0)) + (grp & (H - 1)));
+        uint32_t v[R];
+#pragma unroll
+        for (int u = 0; u < R; ++u) v[u] = smp[u * H + (u * H) / 32];
+        radix_group_inv_staged<RL>(v, tws + blk * T::PER, p);
+#pragma unroll
+        for (int u = 0; u < R; ++u) smp[u * H + (u * H) / 32] = v[u];
+    }
+}
+
 // The inverse row pass of a full tile of ROWS rows of one vector with the MAC
 // in registers: the first round's groups are 2^RL contiguous residues, so each
 // thread forms their Alg. 8 sums straight from X and Ym; the last round (the
@@ -402,6 +478,9 @@ __device__ __forceinline__ void row_inv_mac(uint32_t* sm, uint32_t* __restrict__
     using PT = Part<ML>;
     const uint2* tw = tw_all + (int64_t)pi * tw_stride;
     const uint32_t p = prime_of(pi);
+    constexpr bool STAGED = ROWS == 1 && InvTw<ML>::ON;
+    __shared__ uint2 tws[STAGED ? InvTw<ML>::TOTAL : 1];
+    if constexpr (STAGED) stage_inv_tw<ML>(tws, tw, rbase);   // visible after the first round's barrier
     {
         constexpr int R_ = PT::NR - 1, S0 = PT::start(R_), RL = PT::size(R_), R = 1 << RL, LOG_GPC = ML - RL;
         static_assert(S0 + RL == ML && RL >= 2 && RL <= 4, "first inverse round: contiguous groups");
@@ -423,8 +502,13 @@ __device__ __forceinline__ void row_inv_mac(uint32_t* sm, uint32_t* __restrict__
         }
     }
     __syncthreads();
-    const PassArgs a{ROWS, rbase, 1, tw_all, tw_stride, pi, 1, false};
-    inv_middle_rounds<ML, 1>(sm, a);
+    if constexpr (STAGED) {
+        inv_middle_round_staged<ML>(sm, tws, p);
+        __syncthreads();
+    } else {
+        const PassArgs a{ROWS, rbase, 1, tw_all, tw_stride, pi, 1, false};
+        inv_middle_rounds<ML, 1>(sm, a);
+    }
     {
         constexpr int RL = PT::size(0), R = 1 << RL, LOG_H = ML - RL, H = 1 << LOG_H;
         constexpr int NG = ROWS << LOG_H;
@@ -436,7 +520,8 @@ __device__ __forceinline__ void row_inv_mac(uint32_t* sm, uint32_t* __restrict__
             const uint32_t* smp = sm + pad_idx(base);
 #pragma unroll
             for (int u = 0; u < R; ++u) v[u] = smp[u * H + (u * H) / 32];
-            radix_group<true, RL>(v, tw, rbase + c, p);
+            if constexpr (STAGED) radix_group_inv_staged<RL>(v, tws + InvTw<ML>::MID, p);
+            else radix_group<true, RL>(v, tw, rbase + c, p);
 #pragma unroll
             for (int u = 0; u < R; ++u) out[base + u * H] = v[u];
         }
@@ -477,9 +562,30 @@ __device__ __forceinline__ void radix_group_inv_v(uint32_t (&x)[V][1 << RL], con
     }
 }
 
+// the same with the twiddles from shared memory (stage_inv_tw's layout)
+template <int RL, int V>
+__device__ __forceinline__ void radix_group_inv_v_staged(uint32_t (&x)[V][1 << RL], const uint2* tws, uint32_t p)
+{
+    constexpr int R = 1 << RL;
+    uint2 w[R];
+#pragma unroll
+    for (int k = 1; k < R; ++k) w[k] = tws[k - 1];
+#pragma unroll
+    for (int j = RL - 1; j >= 0; --j) {
+        const int half = R >> (j + 1);
+#pragma unroll
+        for (int u = 0; u < R; ++u) {
+            if (u & half) continue;
+#pragma unroll
+            for (int i = 0; i < V; ++i) bfly_gs(x[i][u], x[i][u + half], w[(1 << j) + (u >> (RL - j))], p);
+        }
+    }
+}
+
 // middle round of the inverse row pass on V tiles (the row_round index map)
-template <int ML, int S0, int RL, int V, int TW, int ROWS>
-__device__ __forceinline__ void row_round_inv_v(uint32_t* sm, int rbase, const uint2* __restrict__ tw, uint32_t p)
+template <int ML, int S0, int RL, int V, int TW, int ROWS, bool STG = false>
+__device__ __forceinline__ void row_round_inv_v(uint32_t* sm, int rbase, const uint2* __restrict__ tw, uint32_t p,
+                                                const uint2* tws = nullptr)
 {
     constexpr int LOG_H = ML - S0 - RL, H = 1 << LOG_H, LOG_GPC = ML - RL, R = 1 << RL;
     constexpr bool PERM = LOG_H == 4 && ML - S0 >= 6 && ML - S0 <= 8;
@@ -503,7 +609,8 @@ __device__ __forceinline__ void row_round_inv_v(uint32_t* sm, int rbase, const u
 #pragma unroll
             for (int u = 0; u < R; ++u) x[i][u] = s[u * H + (u * H) / 32];
         }
-        radix_group_inv_v<RL, V>(x, tw, ((rbase + c) << S0) + blk, p);
+        if constexpr (STG) radix_group_inv_v_staged<RL, V>(x, tws + blk * ((1 << RL) - 1), p);
+        else radix_group_inv_v<RL, V>(x, tw, ((rbase + c) << S0) + blk, p);
 #pragma unroll
         for (int i = 0; i < V; ++i) {
             uint32_t* s = sm + i * TW + pad_idx(base);
@@ -574,6 +681,9 @@ __global__ void __launch_bounds__(NTT_THREADS, 6) ntt_inv_row_v_kernel(NttGeom g
         mv[i] = mac_decode(g, vec, mac.ym_stride);
     }
     if (!any) return;
+    constexpr bool STAGED = RPC == 1 && InvTw<M2>::ON;
+    __shared__ uint2 tws[STAGED ? InvTw<M2>::TOTAL : 1];
+    if constexpr (STAGED) stage_inv_tw<M2>(tws, tw, rbase);   // visible after the first round's barrier
     {   // first round: groups of 2^RL contiguous residues, the Alg. 8 sums formed from X and Ym
         constexpr int R_ = PT::NR - 1, S0 = PT::start(R_), RL = PT::size(R_), R = 1 << RL, LOG_GPC = M2 - RL;
         static_assert(S0 + RL == M2 && RL >= 2 && RL <= 4, "first inverse round: contiguous groups");
@@ -600,7 +710,12 @@ __global__ void __launch_bounds__(NTT_THREADS, 6) ntt_inv_row_v_kernel(NttGeom g
         }
     }
     __syncthreads();
-    inv_middle_rounds_v<M2, V, TW, RPC, 1>(sm, rbase, tw, p);
+    if constexpr (STAGED) {
+        row_round_inv_v<M2, InvTw<M2>::S0M, InvTw<M2>::RLM, V, TW, RPC, true>(sm, rbase, tw, p, tws);
+        __syncthreads();
+    } else {
+        inv_middle_rounds_v<M2, V, TW, RPC, 1>(sm, rbase, tw, p);
+    }
     {   // last round: stride 2^(M2 - RL), stored straight to HBM
         constexpr int RL = PT::size(0), R = 1 << RL, LOG_H = M2 - RL, H = 1 << LOG_H;
 #pragma unroll 1
@@ -614,7 +729,8 @@ __global__ void __launch_bounds__(NTT_THREADS, 6) ntt_inv_row_v_kernel(NttGeom g
 #pragma unroll
                 for (int u = 0; u < R; ++u) x[i][u] = s[u * H + (u * H) / 32];
             }
-            radix_group_inv_v<RL, V>(x, tw, rbase + c, p);
+            if constexpr (STAGED) radix_group_inv_v_staged<RL, V>(x, tws + InvTw<M2>::MID, p);
+            else radix_group_inv_v<RL, V>(x, tw, rbase + c, p);
 #pragma unroll
             for (int i = 0; i < V; ++i) {
                 if (!live[i]) continue;

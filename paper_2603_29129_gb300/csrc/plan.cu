@@ -917,7 +917,7 @@ static int run_plan_range(ozfft_plan_s* p, const void* in, void* out, cudaStream
     int32_t* redo = p->redo + sb0 * 2;
     // the split fused with the forward column pass (the residues are transformed on
     // chip), unless the stage dumps need the untransformed residues or the plan is TS
-    const bool fuse_fwd = !p->ts && !p->debug && p->split_fused && p->geom_fwd.m1 > 0 &&
+    const bool fuse_fwd = !p->ts && !p->debug && p->split_fused && p->redo && p->geom_fwd.m1 > 0 &&
                           split_col_supported(K, P, p->geom_fwd.m1, p->geom_fwd.m2);
     CUDA_TRY(cudaMemsetAsync(mu, 0, sizeof(uint64_t) * B * 2 * (K + 1), s));
     p->cur = nullptr;
@@ -1763,6 +1763,7 @@ static int noalloc_setup(NoallocState& st, int dev, int64_t n, int64_t N, int al
     p.n = n; p.N = N; p.B = 1; p.K = K; p.L = 1; p.P = P; p.G = K * K; p.alpha = alpha; p.debug = 0; p.chunk = 1;
     p.garner_u = garner_u_ok(n, 1, alpha);
     p.device = dev; p.profiling = false; p.bytes = 0;
+    p.split_fused = 0;   // no redo flags in the static workspace (and N <= 2^13: one column stage at most)
     unsigned char* cur = st.base;
     p.chirp = (double2*)noalloc_take(cur, sizeof(double2) * NM);
     p.tw = (uint2*)noalloc_take(cur, sizeof(uint2) * P * NM);
