@@ -823,8 +823,9 @@ __device__ __forceinline__ int fc_pad(int i) { return LOG_T < 5 ? i + ((i >> (LO
 // tiles prime 1): 2^RL-point groups of stride H rows; element u of a group
 // sits at the group's base plus the compile-time offset u H T + T floor(u H /
 // 16) (a group never straddles a 16-row bucket except at multiples of H)
-template <int ML, int S0, int RL, int LOG_T, int NT>
-__device__ __forceinline__ void fc_round(uint32_t* st, const uint2* __restrict__ tw0, const uint2* __restrict__ tw1)
+template <int ML, int S0, int RL, int LOG_T, int NT, bool STG = false>
+__device__ __forceinline__ void fc_round(uint32_t* st, const uint2* __restrict__ tw0, const uint2* __restrict__ tw1,
+                                         const uint2* stw = nullptr)
 {
     constexpr int LOG_H = ML - S0 - RL, H = 1 << LOG_H, LOG_GPC = ML - RL, T = 1 << LOG_T, R = 1 << RL;
     constexpr int GPT = T << LOG_GPC, PW = fc_words<LOG_T>();
@@ -838,7 +839,10 @@ __device__ __forceinline__ void fc_round(uint32_t* st, const uint2* __restrict__
         uint32_t v[R];
 #pragma unroll
         for (int u = 0; u < R; ++u) v[u] = base[u * H * T + (LOG_T < 5 ? ((u * H) >> 4) << LOG_T : 0)];
-        radix_group<true, RL>(v, pr ? tw1 : tw0, (1 << S0) + blk, pr ? P1 : P0);
+        if constexpr (STG)   // staged: [prime][block][2^RL - 1] in radix_group's order
+            radix_group_inv_staged<RL>(v, stw + (pr << S0) * (R - 1) + blk * (R - 1), pr ? P1 : P0);
+        else
+            radix_group<true, RL>(v, pr ? tw1 : tw0, (1 << S0) + blk, pr ? P1 : P0);
 #pragma unroll
         for (int u = 0; u < R; ++u) base[u * H * T + (LOG_T < 5 ? ((u * H) >> 4) << LOG_T : 0)] = v[u];
     }
@@ -858,11 +862,30 @@ __device__ __forceinline__ void fc_rounds(uint32_t* st, const uint2* tw0, const 
 // the column rounds for stages 2 .. ML-1 in one round (ML <= 6); stages 0 and
 // 1 then run in registers in colcrt_kernel
 template <int ML, int LOG_T, int NT>
-__device__ __forceinline__ void fc_rounds_hi(uint32_t* st, const uint2* tw0, const uint2* tw1)
+__device__ __forceinline__ void fc_rounds_hi(uint32_t* st, const uint2* tw0, const uint2* tw1, const uint2* stw)
 {
     static_assert(ML - 2 >= 1 && ML - 2 <= 4, "one shared-memory round");
-    fc_round<ML, 2, ML - 2, LOG_T, NT>(st, tw0, tw1);
+    fc_round<ML, 2, ML - 2, LOG_T, NT, true>(st, tw0, tw1, stw);
     __syncthreads();
+}
+
+// the twiddles of that round (4 blocks of stage 2's table rows, 2^(ML-2) - 1
+// entries each, both primes) copied once per CTA: every flush group of the CTA
+// uses the same ones
+template <int ML>
+struct FcTw {
+    static constexpr int PER = (1 << (ML - 2)) - 1, TOTAL = 2 * 4 * PER;
+};
+template <int ML>
+__device__ __forceinline__ void fc_stage_tw(uint2* stw, const uint2* __restrict__ tw0, const uint2* __restrict__ tw1)
+{
+    constexpr int PER = FcTw<ML>::PER;
+    for (int e = threadIdx.x; e < FcTw<ML>::TOTAL; e += FC_THREADS) {
+        const int pr = e / (4 * PER), rest = e - pr * 4 * PER;
+        const int blk = rest / PER, k = rest - blk * PER + 1;     // radix_group's index (1 << j) + q
+        const int j = 31 - __clz(k);
+        stw[e] = __ldg((pr ? tw1 : tw0) + ((4 + blk) << j) + (k - (1 << j)));
+    }
 }
 
 struct FcTerm {
@@ -948,6 +971,8 @@ __global__ void __launch_bounds__(FC_THREADS, 4) colcrt_kernel(CrtArgs a, int m2
     };
     static_assert(FC_STAGES == 2, "the copies of step i + 1 go to the buffer step i - 1 used");
     issue(0);
+    __shared__ uint2 fc_tw[REG01 ? FcTw<(M1 < 3 ? 3 : M1)>::TOTAL : 1];
+    if constexpr (REG01) fc_stage_tw<M1>(fc_tw, tw0, tw1);   // visible after the first step's barrier
     // stages 1 and 0 (the register round): table entries 1 and 2 are 1 (block 0
     // of stages 0 and 1), entry 3 is w^(N/4), the same for every step
     const uint2 w3_0 = __ldg(tw0 + 3), w3_1 = __ldg(tw1 + 3);
@@ -964,7 +989,7 @@ __global__ void __launch_bounds__(FC_THREADS, 4) colcrt_kernel(CrtArgs a, int m2
                                                           // thread is done with step i - 1's buffer
         issue(i + 1);                                     // into that buffer, during this step's arithmetic
         uint32_t* st = fc_sm + (i % FC_STAGES) * SW;
-        if constexpr (REG01) fc_rounds_hi<M1, LOG_T, 2 * TB>(st, tw0, tw1);   // ends with a barrier
+        if constexpr (REG01) fc_rounds_hi<M1, LOG_T, 2 * TB>(st, tw0, tw1, fc_tw);   // ends with a barrier
         else fc_rounds<M1, LOG_T, 2 * TB, 0>(st, tw0, tw1);
 #pragma unroll
         for (int tb = 0; tb < TB; ++tb) {
