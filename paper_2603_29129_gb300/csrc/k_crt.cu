@@ -823,7 +823,9 @@ __device__ __forceinline__ int fc_pad(int i) { return LOG_T < 5 ? i + ((i >> (LO
 // tiles prime 1): 2^RL-point groups of stride H rows; element u of a group
 // sits at the group's base plus the compile-time offset u H T + T floor(u H /
 // 16) (a group never straddles a 16-row bucket except at multiples of H)
-template <int ML, int S0, int RL, int LOG_T, int NT, bool STG = false>
+// STG: 0 the table from global memory, 1 the REG01 round's staged layout (stw),
+// 2 tw0 / tw1 are copies of the table's first 2^ML entries in shared memory
+template <int ML, int S0, int RL, int LOG_T, int NT, int STG = 0>
 __device__ __forceinline__ void fc_round(uint32_t* st, const uint2* __restrict__ tw0, const uint2* __restrict__ tw1,
                                          const uint2* stw = nullptr)
 {
@@ -839,8 +841,10 @@ __device__ __forceinline__ void fc_round(uint32_t* st, const uint2* __restrict__
         uint32_t v[R];
 #pragma unroll
         for (int u = 0; u < R; ++u) v[u] = base[u * H * T + (LOG_T < 5 ? ((u * H) >> 4) << LOG_T : 0)];
-        if constexpr (STG)   // staged: [prime][block][2^RL - 1] in radix_group's order
+        if constexpr (STG == 1)   // staged: [prime][block][2^RL - 1] in radix_group's order
             radix_group_inv_staged<RL>(v, stw + (pr << S0) * (R - 1) + blk * (R - 1), pr ? P1 : P0);
+        else if constexpr (STG == 2)
+            radix_group_tab<true, RL>(v, pr ? tw1 : tw0, (1 << S0) + blk, pr ? P1 : P0);
         else
             radix_group<true, RL>(v, pr ? tw1 : tw0, (1 << S0) + blk, pr ? P1 : P0);
 #pragma unroll
@@ -853,7 +857,7 @@ __device__ __forceinline__ void fc_rounds(uint32_t* st, const uint2* tw0, const 
 {
     if constexpr (I < Part<ML>::NR) {
         constexpr int R_ = Part<ML>::NR - 1 - I;   // the inverse takes the rounds last to first
-        fc_round<ML, Part<ML>::start(R_), Part<ML>::size(R_), LOG_T, NT>(st, tw0, tw1);
+        fc_round<ML, Part<ML>::start(R_), Part<ML>::size(R_), LOG_T, NT, 2>(st, tw0, tw1);
         __syncthreads();
         fc_rounds<ML, LOG_T, NT, I + 1>(st, tw0, tw1);
     }
@@ -865,7 +869,7 @@ template <int ML, int LOG_T, int NT>
 __device__ __forceinline__ void fc_rounds_hi(uint32_t* st, const uint2* tw0, const uint2* tw1, const uint2* stw)
 {
     static_assert(ML - 2 >= 1 && ML - 2 <= 4, "one shared-memory round");
-    fc_round<ML, 2, ML - 2, LOG_T, NT, true>(st, tw0, tw1, stw);
+    fc_round<ML, 2, ML - 2, LOG_T, NT, 1>(st, tw0, tw1, stw);
     __syncthreads();
 }
 
@@ -971,8 +975,16 @@ __global__ void __launch_bounds__(FC_THREADS, 4) colcrt_kernel(CrtArgs a, int m2
     };
     static_assert(FC_STAGES == 2, "the copies of step i + 1 go to the buffer step i - 1 used");
     issue(0);
-    __shared__ uint2 fc_tw[REG01 ? FcTw<(M1 < 3 ? 3 : M1)>::TOTAL : 1];
-    if constexpr (REG01) fc_stage_tw<M1>(fc_tw, tw0, tw1);   // visible after the first step's barrier
+    // the twiddles of the shared-memory rounds, copied once per CTA (every flush
+    // group uses the same ones): the REG01 round's entries, or the first 2^M1
+    // entries of both primes' tables (the column transform's whole table)
+    __shared__ __align__(16) uint2 fc_tw[REG01 ? FcTw<(M1 < 3 ? 3 : M1)>::TOTAL : 2 << M1];
+    if constexpr (REG01) {
+        fc_stage_tw<M1>(fc_tw, tw0, tw1);   // visible after the first step's barrier
+    } else {
+        for (int e = threadIdx.x; e < (2 << M1); e += FC_THREADS)
+            fc_tw[e] = __ldg((e >> M1 ? tw1 : tw0) + (e & ((1 << M1) - 1)));
+    }
     // stages 1 and 0 (the register round): table entries 1 and 2 are 1 (block 0
     // of stages 0 and 1), entry 3 is w^(N/4), the same for every step
     const uint2 w3_0 = __ldg(tw0 + 3), w3_1 = __ldg(tw1 + 3);
@@ -990,7 +1002,7 @@ __global__ void __launch_bounds__(FC_THREADS, 4) colcrt_kernel(CrtArgs a, int m2
         issue(i + 1);                                     // into that buffer, during this step's arithmetic
         uint32_t* st = fc_sm + (i % FC_STAGES) * SW;
         if constexpr (REG01) fc_rounds_hi<M1, LOG_T, 2 * TB>(st, tw0, tw1, fc_tw);   // ends with a barrier
-        else fc_rounds<M1, LOG_T, 2 * TB, 0>(st, tw0, tw1);
+        else fc_rounds<M1, LOG_T, 2 * TB, 0>(st, fc_tw, fc_tw + (1 << M1));
 #pragma unroll
         for (int tb = 0; tb < TB; ++tb) {
             const int ti = i * TB + tb;

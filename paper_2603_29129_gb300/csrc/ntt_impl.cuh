@@ -96,6 +96,36 @@ __device__ __forceinline__ void radix_group(uint32_t (&v)[1 << RL], const uint2*
     }
 }
 
+// radix_group with the table read by plain loads from any address space (a
+// copy of the table's first rows in shared memory, 16-byte aligned)
+template <bool INV, int RL>
+__device__ __forceinline__ void radix_group_tab(uint32_t (&v)[1 << RL], const uint2* tab, int B0, uint32_t p)
+{
+    constexpr int R = 1 << RL;
+    uint2 w[R];
+    w[1] = tab[B0];
+#pragma unroll
+    for (int j = 1; j < RL; ++j)
+#pragma unroll
+        for (int q = 0; q < (1 << j); q += 2) {
+            const uint4 t = *reinterpret_cast<const uint4*>(tab + (B0 << j) + q);
+            w[(1 << j) + q] = make_uint2(t.x, t.y);
+            w[(1 << j) + q + 1] = make_uint2(t.z, t.w);
+        }
+#pragma unroll
+    for (int jj = 0; jj < RL; ++jj) {
+        const int j = INV ? RL - 1 - jj : jj;
+        const int half = R >> (j + 1);
+#pragma unroll
+        for (int u = 0; u < R; ++u) {
+            if (u & half) continue;
+            const int q = u >> (RL - j);
+            if (INV) bfly_gs(v[u], v[u + half], w[(1 << j) + q], p);
+            else bfly_ct(v[u], v[u + half], w[(1 << j) + q], p);
+        }
+    }
+}
+
 // load, transform and store one group whose elements are S words apart
 // (PAD = false: a dense tile without the pad words, as the tensor-memory-access
 // column pass keeps it)
