@@ -124,9 +124,9 @@ typedef struct {
                          fused; results are bit-identical */
     int32_t split_fuse; /* the Ozaki split fused with the forward NTT's column pass (K <= 4, K P <= 9,
                          5..8 column stages): the slice residues are transformed on chip before they
-                         reach device memory.  0 = wherever supported (with autotune: the faster of
-                         fused and apart, timed), 1 = wherever supported, 2 = never; never for debug
-                         or TS plans; results are bit-identical */
+                         reach device memory.  0 = apart (with autotune: the faster of fused and
+                         apart, timed), 1 = wherever supported, 2 = never; never for debug or TS
+                         plans; results are bit-identical */
 } ozfft_options;
 
 /* Create a plan for `batch` transforms of length n in `direction`, with default

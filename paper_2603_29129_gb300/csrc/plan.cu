@@ -133,7 +133,7 @@ struct ozfft_plan_s {
     int direction = -1, K = 3, L = 1, P = 2, alpha = 0, G = 9, debug = 0, merge = 0, ts = 0;
     int kinf = 0;                // K = infinity: K holds the level cap MAX_K
     int crt_fused = 1;           // inverse column pass fused with the CRT where colcrt_supported
-    int split_fused = 1;         // the split fused with the forward column pass where split_col_supported
+    int split_fused = 0;         // the split fused with the forward column pass where split_col_supported
     int tune_vecs = 1;           // the autotuner may choose the inverse row pass's vectors per CTA
     int tune_fuse = 1;           // ... and whether the inverse column pass is fused with the CRT
     int tune_sfuse = 1;          // ... and whether the split is fused with the forward column pass
@@ -1121,7 +1121,7 @@ ozfft_plan_t ozfft_plan_ex(int64_t n, int64_t batch, int direction, const ozfft_
     }
     p->total = n * batch;
     p->crt_fused = o.crt_fuse != 2;
-    p->split_fused = o.split_fuse != 2;
+    p->split_fused = o.split_fuse == 1;   // apart unless forced or tuned (apart measured faster at N = 2^17 .. 2^20)
     p->tune_sfuse = o.split_fuse == 0;
     p->tune_fuse = o.crt_fuse == 0;
     p->tune_vecs = o.inv_vecs == 0;
@@ -1252,7 +1252,7 @@ ozfft_plan_t ozfft_plan_many(const int64_t* lengths, int64_t count, int directio
         q->chunk = o.chunk > 0 ? std::min<int64_t>(o.chunk, q->B)
                                : std::max<int64_t>(1, std::min<int64_t>(q->B, (int64_t)(q->B * frac)));
         q->crt_fused = o.crt_fuse == 1;   // length classes keep the CRT apart unless forced or tuned
-        q->split_fused = o.split_fuse != 2;
+        q->split_fused = o.split_fuse == 1;
         q->tune_sfuse = o.split_fuse == 0;
         q->tune_fuse = o.crt_fuse == 0;
         q->tune_vecs = o.inv_vecs == 0;

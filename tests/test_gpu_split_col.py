@@ -133,8 +133,9 @@ def test_fused_split_autotuned(oz):
 
 
 def test_fused_split_uneven_lengths(oz):
-    """A plan over uneven lengths (length classes with N = 2^17 .. 2^18 fuse by
-    default, smaller ones do not): fused and apart give the same bits."""
+    """A plan over uneven lengths with the fusion forced (the classes with N = 2^17
+    .. 2^18 fuse, the smaller ones have too few column stages) and with it off:
+    the same bits, and each signal bit-exact against the oracle."""
     lens = [70000, 100000, 3000, 131072, 65537, 5000]
     xh = synth.complex_signal("phi", int(np.sum(lens)), 87, phi=4.0)[0]
     x = torch.from_numpy(xh).cuda()
