@@ -431,6 +431,19 @@ __device__ __forceinline__ void acc192_add64(Acc192& A, long long z)   // A += z
         : "r"(lo), "r"(hi), "r"(ext));
 }
 
+__device__ __forceinline__ void acc192_sub64(Acc192& A, long long z)   // A -= z, z sign-extended
+{
+    const uint32_t lo = (uint32_t)z, hi = (uint32_t)((unsigned long long)z >> 32), ext = (uint32_t)(z >> 63);
+    asm("sub.cc.u32 %0, %0, %6;\n\t"
+        "subc.cc.u32 %1, %1, %7;\n\t"
+        "subc.cc.u32 %2, %2, %8;\n\t"
+        "subc.cc.u32 %3, %3, %8;\n\t"
+        "subc.cc.u32 %4, %4, %8;\n\t"
+        "subc.u32 %5, %5, %8;"
+        : "+r"(A.w[0]), "+r"(A.w[1]), "+r"(A.w[2]), "+r"(A.w[3]), "+r"(A.w[4]), "+r"(A.w[5])
+        : "r"(lo), "r"(hi), "r"(ext));
+}
+
 __device__ __forceinline__ void acc192_add(Acc192& A, const Acc192& B)   // A += B
 {
     asm("add.cc.u32 %0, %0, %6;\n\t"
@@ -900,7 +913,7 @@ struct FcTerm {
 
 // TB flush groups per step (their 2 TB tiles transformed between the same
 // barriers)
-template <bool SD, int M1, int TB>
+template <bool SD, int M1, int TB, bool UC>
 __global__ void __launch_bounds__(FC_THREADS, 4) colcrt_kernel(CrtArgs a, int m2, const uint2* __restrict__ tw_all)
 {
     constexpr int LOG_T = 10 - M1, T = 1 << LOG_T;
@@ -1033,12 +1046,16 @@ __global__ void __launch_bounds__(FC_THREADS, 4) colcrt_kernel(CrtArgs a, int m2
                 }
             }
             if (fast) {
+                if (t.sh) {                               // the same shift for every position
 #pragma unroll
-                for (int e = 0; e < FC_E; ++e) {
-                    long long z = a.garner_u ? garner2u(v0[e], v1[e]) : garner2(v0[e], v1[e]);
-                    if (t.neg) z = -z;
-                    if (t.sh) acc192_shl(acc[e], t.sh);
-                    acc192_add64(acc[e], z);
+                    for (int e = 0; e < FC_E; ++e) acc192_shl(acc[e], t.sh);
+                }
+                if (t.neg) {                              // II: subtracted (uniform branch)
+#pragma unroll
+                    for (int e = 0; e < FC_E; ++e) acc192_sub64(acc[e], garner2x<UC>(v0[e], v1[e]));
+                } else {
+#pragma unroll
+                    for (int e = 0; e < FC_E; ++e) acc192_add64(acc[e], garner2x<UC>(v0[e], v1[e]));
                 }
                 if (ti + 1 == s_pstart[1]) {              // the real part is complete
 #pragma unroll
@@ -1090,11 +1107,12 @@ static cudaError_t launch_colcrt_m(const CrtArgs& a, int m2, const uint2* tw, cu
 {
     constexpr int LOG_T = 10 - M1;
     const size_t smem = (size_t)FC_STAGES * 2 * FC_TB * fc_words<LOG_T>() * sizeof(uint32_t);
-    cudaError_t e = cudaFuncSetAttribute(colcrt_kernel<SD, M1, FC_TB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
     const int64_t grid = a.B * ((int64_t(1) << m2) >> LOG_T);
-    colcrt_kernel<SD, M1, FC_TB><<<(unsigned)grid, FC_THREADS, smem, s>>>(a, m2, tw);
+    // Garner without centering z0 (garner_u: every signal's values within the bound) or with it
+    auto kern = a.garner_u ? colcrt_kernel<SD, M1, FC_TB, true> : colcrt_kernel<SD, M1, FC_TB, false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)grid, FC_THREADS, smem, s>>>(a, m2, tw);
     return cudaGetLastError();
 }
 
