@@ -388,6 +388,18 @@ __device__ __forceinline__ uint4 mac_load4(const MacVec& m, const MacSrc& mac, i
     return m.merged ? mac_sum4<true>(m, mac, j) : mac_sum4<false>(m, mac, j);
 }
 
+// one product (L = 1, unmerged: the only unmerged schedules whose sums are
+// formed in registers): Z = X_s Ym_t, for a live vector
+__device__ __forceinline__ uint4 mac_one4(const MacVec& m, const MacSrc& mac, int64_t j)
+{
+    int64_t xo, yo;
+    mac_offsets<false>(m, 0, xo, yo);
+    const uint4 x = __ldg(reinterpret_cast<const uint4*>(mac.X + xo + j));
+    const uint4 y = __ldg(reinterpret_cast<const uint4*>(mac.Ym + yo + j));
+    return make_uint4(mont_mul(x.x, y.x, m.p, m.pn), mont_mul(x.y, y.y, m.p, m.pn), mont_mul(x.z, y.z, m.p, m.pn),
+                      mont_mul(x.w, y.w, m.p, m.pn));
+}
+
 template <bool MERGED>
 __device__ __forceinline__ uint32_t mac_sum1(const MacVec& m, const MacSrc& mac, int64_t j)
 {
@@ -500,16 +512,15 @@ __device__ __forceinline__ void inv_middle_round_staged(uint32_t* sm, const uint
 // stages of stride H = 2^(ML - RL)) stores straight to global memory, with
 // consecutive lanes on consecutive addresses.  Two shared-memory passes and two
 // barriers fewer than loading, transforming and storing separately.
-template <int ML, int ROWS>
+template <int ML, int ROWS, bool ONE>
 __device__ __forceinline__ void row_inv_mac(uint32_t* sm, uint32_t* __restrict__ out, const uint2* __restrict__ tw_all,
                                             int pi, int64_t tw_stride, int rbase, const MacVec& mv, const MacSrc& mac,
-                                            int64_t j0)
+                                            int64_t j0, uint2* tws)
 {
     using PT = Part<ML>;
     const uint2* tw = tw_all + (int64_t)pi * tw_stride;
     const uint32_t p = prime_of(pi);
-    constexpr bool STAGED = ROWS == 1 && InvTw<ML>::ON;
-    __shared__ uint2 tws[STAGED ? InvTw<ML>::TOTAL : 1];
+    constexpr bool STAGED = ROWS == 1 && InvTw<ML>::ON;   // tws: InvTw<ML>::TOTAL entries
     if constexpr (STAGED) stage_inv_tw<ML>(tws, tw, rbase);   // visible after the first round's barrier
     {
         constexpr int R_ = PT::NR - 1, S0 = PT::start(R_), RL = PT::size(R_), R = 1 << RL, LOG_GPC = ML - RL;
@@ -522,7 +533,7 @@ __device__ __forceinline__ void row_inv_mac(uint32_t* sm, uint32_t* __restrict__
             uint32_t v[R];
 #pragma unroll
             for (int q = 0; q < R; q += 4) {
-                const uint4 t = mac_load4(mv, mac, j0 + base + q);
+                const uint4 t = ONE ? mac_one4(mv, mac, j0 + base + q) : mac_load4(mv, mac, j0 + base + q);
                 v[q] = t.x; v[q + 1] = t.y; v[q + 2] = t.z; v[q + 3] = t.w;
             }
             radix_group<true, RL>(v, tw, ((rbase + c) << S0) + grp, p);
@@ -661,18 +672,6 @@ __device__ __forceinline__ void inv_middle_rounds_v(uint32_t* sm, int rbase, con
     }
 }
 
-// one product (L = 1, unmerged: the only unmerged schedules whose sums are
-// formed in registers): Z = X_s Ym_t, for a live vector
-__device__ __forceinline__ uint4 mac_one4(const MacVec& m, const MacSrc& mac, int64_t j)
-{
-    int64_t xo, yo;
-    mac_offsets<false>(m, 0, xo, yo);
-    const uint4 x = __ldg(reinterpret_cast<const uint4*>(mac.X + xo + j));
-    const uint4 y = __ldg(reinterpret_cast<const uint4*>(mac.Ym + yo + j));
-    return make_uint4(mont_mul(x.x, y.x, m.p, m.pn), mont_mul(x.y, y.y, m.p, m.pn), mont_mul(x.z, y.z, m.p, m.pn),
-                      mont_mul(x.w, y.w, m.p, m.pn));
-}
-
 // one CTA: rows [row0, row0 + RPC) of two vectors of one prime and one flush
 // group index: those of convolutions RR and RI (both products of Re x~'
 // slices) or of II and IR (Im x~'), which in the usual schedule read the same
@@ -797,7 +796,15 @@ __global__ void __launch_bounds__(NTT_THREADS, (INV && MAC) ? 9 : 10) ntt_row_ke
             if (rows == RPC && g.mac_reg) {   // groups of several products keep the coalesced staged loads
                 const MacVec mv = mac_decode(g, vec, mac.ym_stride);
                 const int rin0 = (int)(row0 & ((int64_t(1) << lg_rpv) - 1));
-                row_inv_mac<M2, RPC>(sm, data + gbase, tw_all, pi, g.N, (1 << g.m1) + rin0, mv, mac, j0);
+                __shared__ uint2 tws[RPC == 1 && InvTw<M2>::ON ? InvTw<M2>::TOTAL : 1];
+                // one unmerged product per group (L = 1): the MAC without the product loop
+                // (one-row tiles; with several rows per CTA the second variant spills)
+                if (RPC == 1 && !mv.merged && mv.n == 1)
+                    row_inv_mac<M2, RPC, RPC == 1>(sm, data + gbase, tw_all, pi, g.N, (1 << g.m1) + rin0, mv, mac,
+                                                   j0, tws);
+                else
+                    row_inv_mac<M2, RPC, false>(sm, data + gbase, tw_all, pi, g.N, (1 << g.m1) + rin0, mv, mac, j0,
+                                                tws);
                 return;
             }
         }
