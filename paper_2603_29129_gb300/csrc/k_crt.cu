@@ -905,6 +905,11 @@ __device__ __forceinline__ void fc_stage_tw(uint2* stw, const uint2* __restrict_
     }
 }
 
+template <bool B>
+struct FcBool {
+    static constexpr bool value = B;
+};
+
 struct FcTerm {
     int64_t off;     // Z offset of the group's prime-0 vector
     int16_t sh;      // left shift of the running sum before the term
@@ -1008,6 +1013,10 @@ __global__ void __launch_bounds__(FC_THREADS, 4) colcrt_kernel(CrtArgs a, int m2
         acc[e] = Acc192{{0u, 0u, 0u, 0u, 0u, 0u}};
         s_yr[e][threadIdx.x] = 0.0;
     }
+    // the step loop, instantiated for signals on the Horner path and for the others
+    // (column pass only), so that neither carries the other's code and registers
+    auto run_steps = [&](auto fast_c) {
+    constexpr bool FAST = decltype(fast_c)::value;
     for (int i = 0; i < nsteps; ++i) {
         asm volatile("cp.async.wait_group 0;" ::: "memory");
         __syncthreads();                                  // step i's tiles are in shared memory, and every
@@ -1045,7 +1054,7 @@ __global__ void __launch_bounds__(FC_THREADS, 4) colcrt_kernel(CrtArgs a, int m2
                     v1[e] = sp[PW + p];
                 }
             }
-            if (fast) {
+            if constexpr (FAST) {
                 if (t.sh) {                               // the same shift for every position
 #pragma unroll
                     for (int e = 0; e < FC_E; ++e) acc192_shl(acc[e], t.sh);
@@ -1078,6 +1087,9 @@ __global__ void __launch_bounds__(FC_THREADS, 4) colcrt_kernel(CrtArgs a, int m2
             }
         }
     }
+    };
+    if (fast) run_steps(FcBool<true>{});
+    else run_steps(FcBool<false>{});
     asm volatile("cp.async.wait_group 0;" ::: "memory");
     if (!fast) return;
     double yi[FC_E];

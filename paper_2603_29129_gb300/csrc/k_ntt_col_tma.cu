@@ -56,7 +56,7 @@ __global__ void __launch_bounds__(NTT_THREADS, 8) ntt_col_tma_kernel(const __gri
     const unsigned vec = blockIdx.x >> lg_tpv;
     const int col0 = (int)(blockIdx.x & ((1u << lg_tpv) - 1)) << LOG_T;
     if (INV ? !inv_live(g, vec) : !fwd_live(g, vec)) return;
-    const int pi = (int)(vec % (unsigned)g.P);
+    const int pi = (int)(vec - udiv_small(vec, (unsigned)g.P) * (unsigned)g.P);
     const int zc = (int)(vec + g.vec0);
     const uint32_t sma = smem_addr(sm), bara = smem_addr(&bar);
     const uint64_t map = reinterpret_cast<uint64_t>(&tmap);

@@ -232,8 +232,9 @@ __device__ __forceinline__ void run_rounds(uint32_t* sm, const PassArgs& a)
 // inverse vectors [B][4][G][P] when g < ngroups of (b, conv).
 __device__ __forceinline__ bool fwd_live(const NttGeom& g, unsigned vec)
 {
-    const unsigned bv = vec / (unsigned)(g.P * g.K);
-    const int k = (int)((vec / (unsigned)g.P) % (unsigned)g.K);
+    const unsigned vp = udiv_small(vec, (unsigned)g.P);       // vec / P
+    const unsigned bv = udiv_small(vp, (unsigned)g.K);        // vec / (P K)
+    const int k = (int)(vp - bv * (unsigned)g.K);
     if (g.redo && !g.redo[bv]) return false;   // transformed already by the fused split
     return k < g.kcnt[bv];
 }
@@ -259,7 +260,7 @@ __global__ void __launch_bounds__(NTT_THREADS, 8) ntt_col_kernel(NttGeom g, uint
     const unsigned vec = blockIdx.x >> lg_tpv;
     const int col0 = (int)(blockIdx.x & ((1u << lg_tpv) - 1)) << LOG_T;
     if (INV ? !inv_live(g, vec) : !fwd_live(g, vec)) return;
-    const int pi = (int)(vec % (unsigned)g.P);
+    const int pi = (int)(vec - udiv_small(vec, (unsigned)g.P) * (unsigned)g.P);
     uint32_t* v = data + (int64_t)vec * g.N + col0;
     constexpr int TILE4 = (T << M1) >> 2;
     static_assert(TILE4 % (8 * NTT_THREADS) == 0, "column tile");

@@ -54,6 +54,35 @@ __host__ __device__ __forceinline__ uint32_t pneg_inv_of(int pi)
     return pi == 0 ? PRIME0 - 2u : (pi == 1 ? PRIME1 - 2u : PRIME2 - 2u);
 }
 
+// ------------------------------------------------ division by small divisors
+// x / d for a divisor 1 <= d <= SMALL_DIV_MAX that is the same in every thread (the
+// number of primes, levels or flush groups of a vector index) and any 32-bit x,
+// by multiplication with a precomputed reciprocal (division by invariant integers,
+// Granlund and Montgomery 1994): M = floor(2^64 / d) + 1 (2^64 / d for a power
+// of two), floor(x M / 2^64) = floor(x / d) since x (M d - 2^64) < 2^64.  A few
+// integer instructions instead of the generic division sequence.
+constexpr int SMALL_DIV_MAX = 512;
+struct SmallRcp {
+    unsigned long long v[SMALL_DIV_MAX + 1];
+};
+constexpr SmallRcp make_small_rcp()
+{
+    SmallRcp t{};
+    for (int d = 2; d <= SMALL_DIV_MAX; ++d) t.v[d] = 0xffffffffffffffffull / (unsigned)d + 1ull;
+    return t;
+}
+static __constant__ SmallRcp c_small_rcp = make_small_rcp();
+
+__device__ __forceinline__ uint32_t udiv_small(uint32_t x, uint32_t d)
+{
+    if (d <= 1u) return x;
+    if (d > (uint32_t)SMALL_DIV_MAX) return x / d;   // not reached: primes, levels and groups are below it
+    const unsigned long long m = c_small_rcp.v[d];
+    // the high word of x * m without the 64 x 64 product: x m_hi + high(x m_lo)
+    const unsigned long long t = (unsigned long long)x * (uint32_t)(m >> 32) + __umulhi(x, (uint32_t)m);
+    return (uint32_t)(t >> 32);
+}
+
 // ---------------------------------------------------------------- modular ops
 __device__ __forceinline__ uint32_t mod_add(uint32_t a, uint32_t b, uint32_t p)
 {
